@@ -1,0 +1,103 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Sec. 6.1.1).
+
+This module holds no step of the NMF method: it only draws matrices.  Both the
+tests (for the CUDA path and the FP64 oracle) and ``bench.py`` take their
+inputs from here, so each side sees identical data.
+
+Recipes (the design notes list them with their sizes):
+
+* ``dense_lowrank``: A = W* H* + |N(0, sigma^2)| with W* (m x r) and H* (r x n)
+  uniform on [0, 1) and sigma = 0.01 (standard deviation, absolute value taken
+  entrywise).  The paper's dense synthetic matrix is the noise-free product of
+  two uniform factors (Sec. 6.1.1); the noise makes the residual nonzero.
+* ``init_factors``: W0 (m x k) and H0 (k x n) uniform on [0, 1) -- the same
+  seed gives the same H0 for every algorithm, as in Sec. 6.1.3.
+* ``sparse_uniform``: CSR with entries nonzero at uniformly random positions
+  (Erdos-Renyi, as the paper's sparse synthetic matrix, Sec. 6.1.1) with
+  values uniform on (0, 1].
+* ``dense_lowrank_torch``: the dense recipe drawn on a torch device in FP32,
+  row block by row block, for sizes too large to draw on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def dense_lowrank(m: int, n: int, r: int, seed: int, sigma: float = 0.01, noise: bool = True):
+    """Returns (A, W*, H*) in float64."""
+    g = _rng(seed)
+    Ws = g.random((m, r))
+    Hs = g.random((r, n))
+    A = Ws @ Hs
+    if noise and sigma > 0:
+        A += np.abs(g.normal(0.0, sigma, size=(m, n)))
+    return A, Ws, Hs
+
+
+def init_factors(m: int, n: int, k: int, seed: int):
+    """(W0, H0) uniform on [0, 1), float64; H0 is drawn first so that it does not
+    depend on m."""
+    g = _rng(seed + 7919)
+    H0 = g.random((k, n))
+    W0 = g.random((m, k))
+    return W0, H0
+
+
+def sparse_uniform(m: int, n: int, density: float, seed: int):
+    """CSR (indptr int64, indices int32, data float64) with each row holding a
+    Binomial(n, density) number of distinct, uniformly placed columns; values
+    uniform on (0, 1].  Returns (indptr, indices, data)."""
+    g = _rng(seed)
+    counts = g.binomial(n, density, size=m).astype(np.int64)
+    nnz = int(counts.sum())
+    rows = np.repeat(np.arange(m, dtype=np.int64), counts)
+    cols = g.integers(0, n, size=nnz, dtype=np.int64)
+    key = np.unique(rows * n + cols)  # sorted by (row, col); drops rare repeats
+    rows = key // n
+    cols = (key % n).astype(np.int32)
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=indptr[1:])
+    data = 1.0 - g.random(key.shape[0])  # (0, 1]
+    return indptr, cols, data
+
+
+def dense_lowrank_torch(m: int, n: int, r: int, seed: int, device, sigma: float = 0.01,
+                        out=None, block_rows: int = 8192):
+    """FP32 A = W* H* + |N(0, sigma^2)| drawn on ``device`` with torch's
+    generator (a different stream of numbers than ``dense_lowrank``).
+    Returns (A, W*, H*); ``out`` (m x n, float32) is filled when given."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    Ws = torch.rand((m, r), generator=g, device=device, dtype=torch.float32)
+    Hs = torch.rand((r, n), generator=g, device=device, dtype=torch.float32)
+    A = out if out is not None else torch.empty((m, n), device=device, dtype=torch.float32)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for r0 in range(0, m, block_rows):
+            r1 = min(m, r0 + block_rows)
+            blk = A[r0:r1]
+            torch.matmul(Ws[r0:r1], Hs, out=blk)
+            if sigma > 0:
+                blk.add_(torch.randn((r1 - r0, n), generator=g, device=device,
+                                     dtype=torch.float32).abs_().mul_(sigma))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return A, Ws, Hs
+
+
+def init_factors_torch(m: int, n: int, k: int, seed: int, device):
+    """(W0, H0) uniform on [0, 1), float32, drawn on ``device``."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + 7919)
+    H0 = torch.rand((k, n), generator=g, device=device, dtype=torch.float32)
+    W0 = torch.rand((m, k), generator=g, device=device, dtype=torch.float32)
+    return W0, H0
