@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""AU-NMF throughput on one GB300 (or N replicas): iterations/s of Alg. 1 on a
+dense 96,000 x 64,000 FP32 matrix (planted rank 50 + |N(0, 0.01^2)| noise),
+k = 50, through the library's C ABI.
+
+One step = one AU-NMF iteration (both products with A, both Gram matrices,
+both local updates, the relative residual).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--algo hals] [--prec tf32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NMF iters/s & TFLOP/s (MU/HALS/ABPP), mixed vs FP32 at matched rel. residual"
+M_FULL, N_FULL, K_FULL, RANK_FULL, SEED = 96_000, 64_000, 50, 50, 1609
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SMS, FP32_LANES = 152, 128
+
+
+def peaks():
+    try:
+        d = json.load(open(PEAKS))
+        return d, "measured"
+    except Exception:
+        return FALLBACK, "fallback"
+
+
+def flops_per_iter(m, n, k, algo):
+    """Sec. 5.2.1: 4mnk + (m+n)k^2 for the products and Grams; MU/HALS local
+    updates add 2(m+n)k^2 (Secs. 4.1, 4.2).  BPP's local work is data
+    dependent and not counted."""
+    f = 4.0 * m * n * k + (m + n) * k * k
+    if algo in ("mu", "hals"):
+        f += 2.0 * (m + n) * k * k
+    return f
+
+
+def product_bytes(m, n, k, prec):
+    """Algorithmic bytes of one product launch: A once (4 B FP32/TF32, 2 B for
+    the BF16 copy), the fixed factor once, the output once."""
+    ea = 2 if prec == "bf16" else 4
+    return ea * m * n + 4 * (n * k + m * k)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(algo, A_slice, k, iters=1):
+    """Runs the FP64 oracle on a slice of the workload; returns (seconds per
+    iteration, threads)."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_1609_09154_gb300 import synth
+
+    ms, ns = A_slice.shape
+    W0, H0 = synth.init_factors(ms, ns, k, seed=SEED)
+    t0 = time.perf_counter()
+    out = orc.nmf_run(A_slice, k, algo, iters, W0, H0)
+    dt = (time.perf_counter() - t0) / iters
+    assert out["rc"] in (0, -5) and np.isfinite(out["relres"]).all()
+    return dt, orc.num_threads()
+
+
+def make_slice(ms, ns):
+    """A slice with the workload's recipe (rank-50 uniform factors + noise),
+    drawn on the host in FP64 and rounded to FP32."""
+    import numpy as np
+
+    from paper_1609_09154_gb300 import synth
+
+    A, _, _ = synth.dense_lowrank(ms, ns, RANK_FULL, seed=SEED)
+    return A.astype(np.float32).astype(np.float64)
+
+
+SLICE = (19_200, 12_800)  # 1/25 of the rows x 1/5 of the columns: 4% of the entries
+
+
+def cpu_baseline(algo, k, iters=1):
+    ms, ns = SLICE
+    A = make_slice(ms, ns)
+    dt, threads = oracle_sample(algo, A, k, iters)
+    scale = (M_FULL * N_FULL) / (ms * ns)  # the products dominate: cost ~ m n k
+    return {
+        "value": 1.0 / (dt * scale), "unit": "iters/s", "cores": threads, "kind": "oracle",
+        "sample": (f"{iters} {algo.upper()} iteration(s) of the FP64 oracle on a {ms}x{ns} "
+                   f"slice (k={k}, same recipe), {dt:.2f} s/iteration, scaled by the "
+                   f"entry ratio {scale:.0f} to the {M_FULL}x{N_FULL} workload"),
+    }
+
+
+def run_reference(args):
+    world, rank, _ = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+
+    orc.build()
+    ms, ns = SLICE
+    A = make_slice(ms, ns)
+    scale = (M_FULL * N_FULL) / (ms * ns)
+    for _ in range(args.warmup):
+        oracle_sample(args.algo, A[:ms // 8], args.k, 1)  # short untimed warm-up
+    t0 = time.perf_counter()
+    threads = 1
+    for _ in range(args.steps):
+        _, threads = oracle_sample(args.algo, A, args.k, 1)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / (dt * scale)
+    cfg = config_dict(args)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                         "sample": f"each step: one {args.algo.upper()} iteration of the FP64 "
+                                   f"oracle on a {ms}x{ns} slice, scaled by {scale:.0f}"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(args):
+    return {"workload": f"dense {M_FULL}x{N_FULL} FP32, planted rank {RANK_FULL} + |N(0,0.01^2)|, "
+                        f"k={args.k}, {args.algo.upper()}, products in {args.prec.upper()}",
+            "m": M_FULL, "n": N_FULL, "k": args.k, "algo": args.algo, "prec": args.prec,
+            "l2": "inputs larger than L2 (A is 24.6 GB), no flush needed",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1609_09154_gb300 import aunmf, synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n, k = M_FULL, N_FULL, args.k
+    A, _, _ = synth.dense_lowrank_torch(m, n, RANK_FULL, seed=SEED + rank, device=dev)
+    W0, H0 = synth.init_factors_torch(m, n, k, seed=SEED + rank, device=dev)
+    torch.cuda.synchronize()
+    h = aunmf.Handle()
+    W = torch.empty_like(W0)
+    H = torch.empty_like(H0)
+    # warm-up (untimed), then the timed K iterations in profile mode so the
+    # library records per-phase CUDA events on its stream
+    h.run(A, k, args.algo, args.warmup, W0, H0, prec=args.prec, out=(W, H),
+          allow_noconverge=True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, _, rel, info = h.run(A, k, args.algo, args.steps, W0, H0, prec=args.prec, out=(W, H),
+                            profile=True, allow_noconverge=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_total = max_over_ranks(ms_total, world)
+    value = world * args.steps / (ms_total / 1e3)
+
+    # dominant kernel: the product launch with the larger summed time
+    pk, pks = peaks()
+    kern = {
+        "aht": {"ms_avg": info["ms_aht"] / max(1, info["n_aht"]), "launches": info["n_aht"]},
+        "wta": {"ms_avg": info["ms_wta"] / max(1, info["n_wta"]), "launches": info["n_wta"]},
+    }
+    dom = max(kern, key=lambda x: kern[x]["ms_avg"] * kern[x]["launches"])
+    t_launch = kern[dom]["ms_avg"] / 1e3
+    if args.prec == "fp32":
+        sm_mhz = (clk or {}).get("sm_mhz") or 1485.0
+        peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        ach = 2.0 * m * n * k / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": f"{dom} (FP32 FMA products)",
+                "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM "
+                             f"clock sampled during the timed region)"}
+    else:
+        by = product_bytes(m, n, k, args.prec)
+        ach = by / t_launch / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "kernel": dom,
+                "peak_note": f"hbm_gbs of {pks} peaks"}
+    for kk in kern.values():
+        kk["ms_avg"] = round(kk["ms_avg"], 4)
+
+    # end to end through the host-buffer entry point: H2D of A, W0, H0 and the
+    # D2H of W, H, relres inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        Ah.copy_(A)
+        W0h = W0.cpu().pin_memory()
+        H0h = H0.cpu().pin_memory()
+        Wh = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
+        Hh = torch.empty((k, n), dtype=torch.float32, pin_memory=True)
+        del A
+        torch.cuda.empty_cache()
+        barrier(world)
+        t0 = time.perf_counter()
+        h.run_host(Ah.numpy(), k, args.algo, args.steps, W0h.numpy(), H0h.numpy(),
+                   prec=args.prec, W=Wh.numpy(), H=Hh.numpy())
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * args.steps / t_e2e, "unit": "iters/s",
+               "h2d_bytes_per_step": (4 * m * n + 4 * m * k + 4 * k * n) / args.steps,
+               "d2h_bytes_per_step": (4 * m * k + 4 * k * n + 8 * args.steps) / args.steps,
+               "note": f"one aunmf_run_host call of {args.steps} iterations; copies of "
+                       f"the whole input/output amortised over its steps"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.algo, k)
+
+    if rank == 0:
+        f_it = flops_per_iter(m, n, k, args.algo)
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[args.prec],
+            "data": "synthetic", "config": config_dict(args),
+            "tflops": f_it * value / 1e12,
+            "relres_last": float(rel[-1]) if len(rel) else None,
+            "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(info["launches"]), "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="hals", choices=["mu", "hals", "abpp"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--k", type=int, default=K_FULL)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * aunmf.h -- C ABI of the GB300 (sm_103a) alternating-updating NMF library.
+ *
+ * Problem (Kannan, Ballard, Park, arXiv:1609.09154, Eq. "original NMF"):
+ *     min_{W >= 0, H >= 0} || A - W H ||_F,   A m x n,  W m x k,  H k x n.
+ * Solved by Alg. 1 (AU-NMF): repeat { update W from H H^T and A H^T;
+ * update H from W^T W and W^T A } with one of three local updates:
+ * MU (Sec. 4.1, Eq. muupdate), HALS (Sec. 4.2, Eq. halsupdate) or ANLS with
+ * block principal pivoting (Sec. 4.3, SolveBPP).
+ *
+ * Conventions for every entry point:
+ *   - All matrices are row-major float32 unless stated; W is m x k, H is k x n
+ *     (the paper's shapes).  Pointers marked [device] must be CUDA device (or
+ *     managed) memory on the handle's device; [host] pointers are host memory.
+ *   - The caller owns every buffer it passes; the library never frees them.
+ *     The handle owns its workspace (grown on demand, freed by
+ *     aunmf_destroy).  Nothing is retained past a call except the workspace.
+ *   - All work is enqueued on the handle's stream.  Entry points that return
+ *     host results (relres, info, loss) synchronise that stream before
+ *     returning; the step-level entry points (aunmf_gram_*, aunmf_aht, ...)
+ *     do not synchronise.
+ *   - Every call returns AUNMF_OK (0) or a negative status code; no C++
+ *     exception crosses this boundary.  aunmf_strerror() names a code.
+ *   - Rank limits: 1 <= k <= AUNMF_K_MAX; ABPP needs k <= AUNMF_BPP_K_MAX.
+ */
+#ifndef AUNMF_H
+#define AUNMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AUNMF_OK 0
+#define AUNMF_E_INVAL -1       /* bad argument: null pointer, k out of range, bad sizes */
+#define AUNMF_E_NOMEM -2       /* workspace allocation failed */
+#define AUNMF_E_CUDA -3        /* a CUDA runtime call failed (see aunmf_last_cuda_error) */
+#define AUNMF_E_NUMERIC -4     /* non-finite value, or a non-positive Cholesky pivot in BPP */
+#define AUNMF_E_NOCONVERGE -5  /* BPP hit its pivot cap on some right-hand side (results written) */
+#define AUNMF_E_TIMEOUT -6     /* a bounded device-side wait expired */
+#define AUNMF_E_UNSUPPORTED -7 /* valid request that this build does not implement */
+
+/* ---- algorithms and precisions ---------------------------------------- */
+#define AUNMF_MU 0   /* Sec. 4.1, Eq. muupdate */
+#define AUNMF_HALS 1 /* Sec. 4.2, Eq. halsupdate */
+#define AUNMF_ABPP 2 /* Sec. 4.3, SolveBPP on each row of W / column of H */
+
+#define AUNMF_FP32 0 /* products with A on FP32 CUDA cores (FMA), FP32 accumulation */
+#define AUNMF_TF32 1 /* products with A on tensor cores (tcgen05 kind::tf32), FP32 accumulation */
+#define AUNMF_BF16 2 /* products with A on tensor cores from a BF16 copy of A, FP32 accumulation */
+
+#define AUNMF_K_MAX 256
+#define AUNMF_BPP_K_MAX 64
+
+typedef struct aunmf_handle aunmf_handle;
+
+/* Input matrix A (nonnegative, Eq. original NMF).  Exactly one form is set:
+ *   dense: dense != NULL, row-major m x n, leading dimension lda >= n
+ *          (elements), 16-byte aligned base and lda % 4 == 0 for the tensor
+ *          paths.  [device]
+ *   CSR:   dense == NULL; rowptr[m+1] (int64), colidx[nnz] (int32, sorted
+ *          within a row), val[nnz] (float32).  [device]
+ * Sizes use int64 throughout (the dense configurations exceed 2^31 entries). */
+typedef struct {
+  int64_t m, n;
+  const float *dense;
+  int64_t lda;
+  const int64_t *rowptr;
+  const int32_t *colidx;
+  const float *val;
+  int64_t nnz;
+} aunmf_matrix;
+
+/* Options (zero-initialised struct = defaults). */
+typedef struct {
+  int prec;           /* AUNMF_FP32 (default) / AUNMF_TF32 / AUNMF_BF16 */
+  double mu_eps;      /* MU: added to the denominator of Eq. muupdate; 0 -> 1e-16 */
+  int bpp_max_pivots; /* ABPP: exchange cap per right-hand side; 0 -> 10*k */
+  int use_graph;      /* 1: capture one iteration as a CUDA graph and replay it */
+  int profile;        /* 1: time product / update / Gram phases with CUDA events */
+} aunmf_options;
+
+/* Per-call report, filled when the pointer is non-NULL. */
+typedef struct {
+  int64_t bpp_pivots;       /* total BPP exchanges over all right-hand sides and iterations */
+  int64_t bpp_nonconverged; /* right-hand sides that hit the pivot cap */
+  int64_t bpp_numeric;      /* right-hand sides with a non-positive Cholesky pivot */
+  int iters_done;
+  float ms_total;           /* device time of the whole call (CUDA events) */
+  /* profile == 1 only: summed device time and launch count per phase */
+  float ms_aht, ms_wta, ms_update, ms_gram, ms_other;
+  int n_aht, n_wta;
+  int64_t launches;         /* kernels this call launched (graph replays counted per kernel) */
+} aunmf_info;
+
+/* ---- handle -------------------------------------------------------------- */
+
+/* Creates a handle bound to the current CUDA device and `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *h receives the handle. */
+int aunmf_create(aunmf_handle **h, void *stream);
+/* Rebinds the handle to another stream of the same device. */
+int aunmf_set_stream(aunmf_handle *h, void *stream);
+/* Frees the workspace and the handle (synchronises its stream first). */
+int aunmf_destroy(aunmf_handle *h);
+
+const char *aunmf_strerror(int code);
+/* The last CUDA error string seen by this handle ("" if none). */
+const char *aunmf_last_cuda_error(aunmf_handle *h);
+
+/* ---- whole runs ---------------------------------------------------------- */
+
+/* Alg. 1: `iters` iterations of AU-NMF with local update `algo` from (W0, H0).
+ *   A        input matrix (dense or CSR) [device]
+ *   W0, H0   initial factors, m x k and k x n [device]; W0 is read by MU and
+ *            HALS only (ABPP starts from H0, as Alg. 1 initialises only H)
+ *   W, H     outputs, m x k and k x n [device]; may alias W0, H0
+ *   relres   [host] array of `iters` doubles (may be NULL): after iteration t's
+ *            two updates, ||A - W H||_F / ||A||_F (Sec. 6.2), evaluated as
+ *            sqrt(||A||^2 - 2 <W^T A, H> + <W^T W, H H^T>) / ||A|| with FP64
+ *            reductions
+ *   opt      options (NULL = defaults); info: report (may be NULL)
+ * HALS takes each column step as the exact coordinate minimiser (the
+ * correction divided by the Gram diagonal) and normalises W's columns after
+ * the sweep while scaling H's rows by the same norms, which leaves W H
+ * unchanged (Eq. halsupdate).  Synchronises the stream. */
+int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
+              const float *W0, const float *H0, float *W, float *H, double *relres,
+              const aunmf_options *opt, aunmf_info *info);
+
+/* Same as aunmf_run with every array in HOST memory (A dense only): copies A,
+ * W0, H0 to the device, runs, copies W, H back.  The device copies live in
+ * the handle's workspace.  Host buffers registered as pinned transfer faster. */
+int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_t lda, int k,
+                   int algo, int iters, const float *W0, const float *H0, float *W, float *H,
+                   double *relres, const aunmf_options *opt, aunmf_info *info);
+
+/* ---- single steps of Alg. 1 (for step-by-step checks and custom drivers) -- */
+
+/* G = W^T W (k x k) for W m x k [device in/out] (Alg. 1 line 4; Alg. 3 X). */
+int aunmf_gram_w(aunmf_handle *h, const float *W, int64_t m, int k, float *G);
+/* G = H H^T (k x k) for H k x n [device in/out] (Alg. 1 line 3; Alg. 3 U). */
+int aunmf_gram_h(aunmf_handle *h, const float *H, int k, int64_t n, float *G);
+/* P = A H^T (m x k) [device] (Alg. 1 line 3; Alg. 3 V), in precision `prec`. */
+int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int prec, float *P);
+/* P = W^T A (k x n) [device] (Alg. 1 line 4; Alg. 3 Y), in precision `prec`. */
+int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int prec, float *P);
+
+/* Local update of W (Alg. 1 line 3) in place: W m x k, PW = A H^T (m x k),
+ * GH = H H^T (k x k) [device].  MU: Eq. muupdate with eps; HALS: the
+ * column sweep of Eq. halsupdate, then unit-normalised columns with H's rows
+ * (H k x n, may be NULL) scaled by the norms; ABPP: each row of W solves
+ * SolveBPP(GH, row of PW) in FP64.  eps <= 0 selects 1e-16. */
+int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const float *GH,
+                   int64_t m, int k, float *H, int64_t n, double eps);
+/* Local update of H (Alg. 1 line 4) in place: H k x n, PH = W^T A (k x n),
+ * GW = W^T W [device].  MU / HALS row sweep / ABPP on each column. */
+int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const float *GW,
+                   int k, int64_t n, double eps);
+
+/* Batched NLS (Sec. 4.3, Eqs. single NLS and KKT): for each of `nrhs` rows r
+ * of R (nrhs x k, float32 [device]) solves x = argmin_{x>=0} ||C x - b|| given
+ * G = C^T C (k x k float32 [device]) and r = C^T b, in FP64; writes x as row r
+ * of X (nrhs x k float32 [device]).  pivots/nonconv (may be NULL) [host]
+ * receive the total exchanges and the number of right-hand sides that hit
+ * max_pivots (0 -> 10*k).  Returns AUNMF_E_NOCONVERGE / AUNMF_E_NUMERIC if
+ * any right-hand side failed (X still written).  Synchronises. */
+int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs, int k, float *X,
+                  int max_pivots, int64_t *pivots, int64_t *nonconv);
+
+/* ||A - W H||_F / ||A||_F (Sec. 6.2) by the trace expansion with FP64
+ * reductions; W m x k, H k x n [device]; *relres [host].  Synchronises. */
+int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const float *H, int k,
+                 double *relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AUNMF_H */

@@ -1,0 +1,614 @@
+// aunmf_api.cu -- the C ABI (include/aunmf.h): handle, workspace, argument
+// checks, and the AU-NMF driver of Alg. 1 that enqueues the hot-path kernels.
+//
+// One iteration (Alg. 1 lines 3-4, with H held as Ht = H^T, n x k):
+//   P_W  = A Ht                       (product, Alg. 1 line 3)
+//   W    = LUC(W, P_W, G_H)           (MU / HALS sweep / BPP)
+//   G_W  = W^T W                      (Gram, Alg. 1 line 4)
+//   HALS: W(:,i) /= s_i, Ht(:,i) *= s_i, G_W <- D^-1 G_W D^-1, s_i = sqrt(G_W,ii)
+//   P_Ht = A^T W                      (product, Alg. 1 line 4)
+//   Ht   = LUC(Ht, P_Ht, G_W)
+//   G_H  = Ht^T Ht                    (Gram for the next iteration)
+//   relres[t] = sqrt(||A||^2 - 2 <P_Ht, Ht> + <G_W, G_H>) / ||A||   (Sec. 6.2)
+// Every step is a kernel of this library; the host only enqueues them.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+using namespace aunmf;
+
+thread_local long long aunmf::g_launches = 0;
+
+struct Buf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct aunmf_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  std::string cuda_err;
+  // workspace
+  Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last, Abf, Wbf, Htbf;
+  Buf hA, hW, hH;  // device copies for aunmf_run_host
+  int max_gram_blocks = 4 * 152;
+  int n_dparts = 2 * 152;
+};
+
+namespace {
+
+int fail_cuda(aunmf_handle *h, cudaError_t e, const char *what) {
+  if (h) {
+    h->cuda_err = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return AUNMF_E_CUDA;
+}
+
+#define CK(h, call)                                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return fail_cuda(h, e_, #call); \
+  } while (0)
+
+int ensure(aunmf_handle *h, Buf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return AUNMF_OK;
+  if (b.p) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->cuda_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return AUNMF_E_NOMEM;
+  }
+  b.cap = bytes;
+  return AUNMF_OK;
+}
+
+#define ENS(h, buf, bytes)                 \
+  do {                                     \
+    int rc_ = ensure(h, buf, (bytes));     \
+    if (rc_ != AUNMF_OK) return rc_;       \
+  } while (0)
+
+template <class T>
+T *P(Buf &b) {
+  return reinterpret_cast<T *>(b.p);
+}
+
+bool valid_matrix(const aunmf_matrix *A) {
+  if (!A || A->m < 1 || A->n < 1) return false;
+  if (A->dense) return A->lda >= A->n;
+  return A->rowptr && (A->nnz == 0 || (A->colidx && A->val));
+}
+
+struct RunCtx {
+  const aunmf_matrix *A;
+  int k, algo, prec;
+  float mu_eps;
+  int max_piv;
+  float *W, *Ht, *PW, *PHt, *GH, *GW, *gpart;
+  double *dpart, *n2a, *relres_dev, *last;
+  DevCounters *ctr;
+  const uint16_t *Abf;  // BF16 copy of A (prec == BF16)
+  uint16_t *Wbf, *Htbf; // BF16 copies of the factors
+  bool profile;
+  std::vector<cudaEvent_t> *ev;          // profile events (pairs)
+  std::vector<int> *ev_phase;            // phase index per pair
+};
+
+enum Phase { kPhAht = 0, kPhWta = 1, kPhUpdate = 2, kPhGram = 3, kPhOther = 4 };
+
+struct PhaseTimer {
+  RunCtx &c;
+  cudaStream_t s;
+  int phase;
+  cudaEvent_t b = nullptr;
+  PhaseTimer(RunCtx &c_, cudaStream_t s_, int ph) : c(c_), s(s_), phase(ph) {
+    if (!c.profile) return;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    c.ev->push_back(e0);
+    c.ev->push_back(e1);
+    c.ev_phase->push_back(ph);
+    cudaEventRecord(e0, s);
+    b = e1;
+  }
+  ~PhaseTimer() {
+    if (b) cudaEventRecord(b, s);
+  }
+};
+
+cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
+  const aunmf_matrix *A = c.A;
+  if (!A->dense)
+    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, s);
+  if (c.prec == AUNMF_FP32) return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
+  (void)h;
+  return tc::launch_aht_tc(A->dense, c.Abf, A->m, A->n, A->lda, c.Ht, c.Htbf, c.k, c.prec, c.PW, s);
+}
+
+cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
+  const aunmf_matrix *A = c.A;
+  if (!A->dense)
+    return launch_wta_csr(A->rowptr, A->colidx, A->val, A->m, A->n, c.W, c.k, c.PHt, s);
+  if (c.prec == AUNMF_FP32) return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
+  (void)h;
+  return tc::launch_wta_tc(A->dense, c.Abf, A->m, A->n, A->lda, c.W, c.Wbf, c.k, c.prec, c.PHt, s);
+}
+
+cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, int64_t rows,
+                   cudaStream_t s) {
+  switch (c.algo) {
+    case AUNMF_MU: return launch_mu(X, Pm, G, rows, c.k, c.mu_eps, s);
+    case AUNMF_HALS: return launch_hals(X, Pm, G, rows, c.k, s);
+    default: return launch_bpp(G, Pm, rows, c.k, X, c.max_piv, c.ctr, nullptr, s);
+  }
+}
+
+// One AU-NMF iteration (see the file header).
+cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
+  const int64_t m = c.A->m, n = c.A->n;
+  const int k = c.k;
+  cudaError_t e;
+  { PhaseTimer t(c, s, kPhAht); if ((e = product_aht(h, c, s)) != cudaSuccess) return e; }
+  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.W, c.PW, c.GH, m, s)) != cudaSuccess) return e; }
+  {
+    PhaseTimer t(c, s, kPhGram);
+    if ((e = launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s)) != cudaSuccess) return e;
+  }
+  if (c.algo == AUNMF_HALS) {
+    PhaseTimer t(c, s, kPhUpdate);
+    if ((e = launch_hals_normalise(c.W, m, c.Ht, n, c.GW, k, s)) != cudaSuccess) return e;
+  }
+  { PhaseTimer t(c, s, kPhWta); if ((e = product_wta(h, c, s)) != cudaSuccess) return e; }
+  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.Ht, c.PHt, c.GW, n, s)) != cudaSuccess) return e; }
+  {
+    PhaseTimer t(c, s, kPhGram);
+    if ((e = launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s)) != cudaSuccess) return e;
+  }
+  {
+    PhaseTimer t(c, s, kPhOther);
+    e = launch_relres(c.PHt, c.Ht, n * (int64_t)k, c.GW, c.GH, k, c.n2a, c.dpart, h->n_dparts,
+                      c.relres_dev, c.ctr, c.last, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int check_run_args(const aunmf_matrix *A, int k, int algo, int iters, const float *W0,
+                   const float *H0, const float *W, const float *H, const aunmf_options *o) {
+  if (!valid_matrix(A)) return AUNMF_E_INVAL;
+  if (!A->dense) return AUNMF_E_UNSUPPORTED;
+  if (k < 1 || k > AUNMF_K_MAX || iters < 0) return AUNMF_E_INVAL;
+  if (algo < AUNMF_MU || algo > AUNMF_ABPP) return AUNMF_E_INVAL;
+  if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
+  if (!H0 || !W || !H || (algo != AUNMF_ABPP && !W0)) return AUNMF_E_INVAL;
+  const int prec = o ? o->prec : AUNMF_FP32;
+  if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (prec != AUNMF_FP32) {
+    if (!A->dense) return AUNMF_E_UNSUPPORTED;
+    int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
+    if (rc != AUNMF_OK) return rc;
+  }
+  return AUNMF_OK;
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+const char *aunmf_strerror(int code) {
+  switch (code) {
+    case AUNMF_OK: return "ok";
+    case AUNMF_E_INVAL: return "invalid argument";
+    case AUNMF_E_NOMEM: return "out of device memory";
+    case AUNMF_E_CUDA: return "CUDA error";
+    case AUNMF_E_NUMERIC: return "numerical failure (non-finite value or non-positive pivot)";
+    case AUNMF_E_NOCONVERGE: return "BPP reached its pivot cap";
+    case AUNMF_E_TIMEOUT: return "device wait timed out";
+    case AUNMF_E_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+int aunmf_create(aunmf_handle **out, void *stream) {
+  if (!out) return AUNMF_E_INVAL;
+  *out = nullptr;
+  aunmf_handle *h = new (std::nothrow) aunmf_handle();
+  if (!h) return AUNMF_E_NOMEM;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { int rc = fail_cuda(h, e, "cudaGetDevice"); delete h; return rc; }
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { int rc = fail_cuda(h, e, "cudaStreamCreate"); delete h; return rc; }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->max_gram_blocks = 4 * sms;
+  h->n_dparts = 2 * sms;
+  *out = h;
+  return AUNMF_OK;
+}
+
+int aunmf_set_stream(aunmf_handle *h, void *stream) {
+  if (!h) return AUNMF_E_INVAL;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return AUNMF_OK;
+}
+
+int aunmf_destroy(aunmf_handle *h) {
+  if (!h) return AUNMF_E_INVAL;
+  cudaStreamSynchronize(h->stream);
+  Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
+                 &h->ctr, &h->relres, &h->last, &h->Abf, &h->Wbf, &h->Htbf, &h->hA, &h->hW,
+                 &h->hH};
+  for (Buf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return AUNMF_OK;
+}
+
+const char *aunmf_last_cuda_error(aunmf_handle *h) { return h ? h->cuda_err.c_str() : ""; }
+
+int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
+              const float *W0, const float *H0, float *W, float *H, double *relres,
+              const aunmf_options *opt, aunmf_info *info) {
+  if (!h) return AUNMF_E_INVAL;
+  int rc = check_run_args(A, k, algo, iters, W0, H0, W, H, opt);
+  if (rc != AUNMF_OK) return rc;
+  aunmf_options o{};
+  if (opt) o = *opt;
+  const int64_t m = A->m, n = A->n;
+  cudaStream_t s = h->stream;
+
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  ENS(h, h->PW, sizeof(float) * m * k);
+  ENS(h, h->PHt, sizeof(float) * n * k);
+  ENS(h, h->GH, sizeof(float) * k * k);
+  ENS(h, h->GW, sizeof(float) * k * k);
+  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  ENS(h, h->dpart, sizeof(double) * (h->n_dparts + 8));
+  ENS(h, h->n2a, sizeof(double));
+  ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->relres, sizeof(double) * (iters > 0 ? iters : 1));
+  ENS(h, h->last, sizeof(double));
+
+  RunCtx c{};
+  c.A = A;
+  c.k = k;
+  c.algo = algo;
+  c.prec = o.prec;
+  c.mu_eps = (float)(o.mu_eps > 0 ? o.mu_eps : 1e-16);
+  c.max_piv = o.bpp_max_pivots > 0 ? o.bpp_max_pivots : 10 * k;
+  c.W = W;
+  c.Ht = P<float>(h->Ht);
+  c.PW = P<float>(h->PW);
+  c.PHt = P<float>(h->PHt);
+  c.GH = P<float>(h->GH);
+  c.GW = P<float>(h->GW);
+  c.gpart = P<float>(h->gpart);
+  c.dpart = P<double>(h->dpart);
+  c.n2a = P<double>(h->n2a);
+  c.relres_dev = P<double>(h->relres);
+  c.last = P<double>(h->last);
+  c.ctr = P<DevCounters>(h->ctr);
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_phase;
+  c.ev = &ev;
+  c.ev_phase = &ev_phase;
+  c.profile = o.profile != 0;
+  if (o.prec != AUNMF_FP32) {
+    if (o.prec == AUNMF_BF16) {
+      ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
+      ENS(h, h->Wbf, sizeof(uint16_t) * tc::factor_elems(m, k));
+      ENS(h, h->Htbf, sizeof(uint16_t) * tc::factor_elems(n, k));
+      c.Abf = P<uint16_t>(h->Abf);
+      c.Wbf = P<uint16_t>(h->Wbf);
+      c.Htbf = P<uint16_t>(h->Htbf);
+    }
+  }
+
+  const long long launches0 = g_launches;
+  long long graph_launches = 0;
+  cudaEvent_t t0, t1;
+  CK(h, cudaEventCreate(&t0));
+  CK(h, cudaEventCreate(&t1));
+  CK(h, cudaEventRecord(t0, s));
+  CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
+  // setup (a0): W0 -> W, H0 -> Ht, ||A||^2, BF16 copy of A, initial G_H
+  if (algo != AUNMF_ABPP) {
+    if (W != W0) CK(h, cudaMemcpyAsync(W, W0, sizeof(float) * m * k, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(h, cudaMemsetAsync(W, 0, sizeof(float) * m * k, s));
+  }
+  CK(h, launch_transpose(H0, k, n, c.Ht, s));
+  if (A->dense) {
+    CK(h, launch_norm2(A->dense, m, n, A->lda, c.dpart, h->n_dparts, c.n2a, s));
+  } else {
+    CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
+  }
+  if (o.prec == AUNMF_BF16) CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), s));
+  CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  const bool use_graph = o.use_graph && !o.profile && iters > 1;
+  if (use_graph) {
+    // capture one iteration on the private stream, replay on the caller's
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long lc0 = g_launches;
+    cudaError_t ce = iterate(h, c, h->cap_stream);
+    const long long per_iter = g_launches - lc0;
+    g_launches = lc0;  // captured, not launched: counted per replay below
+    graph_launches = per_iter * iters;
+    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (ce != cudaSuccess) return fail_cuda(h, ce, "iterate (capture)");
+    if (ee != cudaSuccess) return fail_cuda(h, ee, "cudaStreamEndCapture");
+    CK(h, cudaGraphInstantiate(&gexec, graph, 0));
+    for (int t = 0; t < iters; ++t) CK(h, cudaGraphLaunch(gexec, s));
+  } else {
+    for (int t = 0; t < iters; ++t) {
+      cudaError_t e = iterate(h, c, s);
+      if (e != cudaSuccess) return fail_cuda(h, e, "iterate");
+    }
+  }
+  CK(h, launch_transpose(c.Ht, n, k, H, s));
+  CK(h, cudaEventRecord(t1, s));
+  DevCounters hc{};
+  CK(h, cudaMemcpyAsync(&hc, c.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+  if (relres && iters > 0)
+    CK(h, cudaMemcpyAsync(relres, c.relres_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->bpp_pivots = hc.bpp_pivots;
+    info->bpp_nonconverged = hc.bpp_nonconv;
+    info->bpp_numeric = hc.bpp_numeric;
+    info->iters_done = iters;
+    info->launches = g_launches - launches0 + graph_launches;
+    cudaEventElapsedTime(&info->ms_total, t0, t1);
+    for (size_t p = 0; p < ev_phase.size(); ++p) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * p], ev[2 * p + 1]);
+      switch (ev_phase[p]) {
+        case kPhAht: info->ms_aht += ms; info->n_aht += 1; break;
+        case kPhWta: info->ms_wta += ms; info->n_wta += 1; break;
+        case kPhUpdate: info->ms_update += ms; break;
+        case kPhGram: info->ms_gram += ms; break;
+        default: info->ms_other += ms; break;
+      }
+    }
+  }
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (hc.nonfinite) return AUNMF_E_NUMERIC;
+  if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
+  if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;
+  return AUNMF_OK;
+}
+
+int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_t lda, int k,
+                   int algo, int iters, const float *W0, const float *H0, float *W, float *H,
+                   double *relres, const aunmf_options *opt, aunmf_info *info) {
+  if (!h || !A || m < 1 || n < 1 || lda < n || !H0 || !W || !H) return AUNMF_E_INVAL;
+  if (algo != AUNMF_ABPP && !W0) return AUNMF_E_INVAL;
+  cudaStream_t s = h->stream;
+  ENS(h, h->hA, sizeof(float) * m * n);
+  ENS(h, h->hW, sizeof(float) * m * k);
+  ENS(h, h->hH, sizeof(float) * k * n);
+  float *dA = P<float>(h->hA), *dW = P<float>(h->hW), *dH = P<float>(h->hH);
+  CK(h, cudaMemcpy2DAsync(dA, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
+                          cudaMemcpyHostToDevice, s));
+  if (algo != AUNMF_ABPP) CK(h, cudaMemcpyAsync(dW, W0, sizeof(float) * m * k, cudaMemcpyHostToDevice, s));
+  CK(h, cudaMemcpyAsync(dH, H0, sizeof(float) * k * n, cudaMemcpyHostToDevice, s));
+  aunmf_matrix M{};
+  M.m = m;
+  M.n = n;
+  M.dense = dA;
+  M.lda = n;
+  int rc = aunmf_run(h, &M, k, algo, iters, dW, dH, dW, dH, relres, opt, info);
+  if (rc != AUNMF_OK && rc != AUNMF_E_NOCONVERGE) return rc;
+  CK(h, cudaMemcpyAsync(W, dW, sizeof(float) * m * k, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(H, dH, sizeof(float) * k * n, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  return rc;
+}
+
+// ------------------------------------------------------------ single steps
+int aunmf_gram_w(aunmf_handle *h, const float *W, int64_t m, int k, float *G) {
+  if (!h || !W || !G || m < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  CK(h, launch_gram(W, m, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream));
+  return AUNMF_OK;
+}
+
+int aunmf_gram_h(aunmf_handle *h, const float *H, int k, int64_t n, float *G) {
+  if (!h || !H || !G || n < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  CK(h, launch_transpose(H, k, n, P<float>(h->Ht), h->stream));
+  CK(h, launch_gram(P<float>(h->Ht), n, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream));
+  return AUNMF_OK;
+}
+
+int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int prec, float *Pout) {
+  if (!h || !valid_matrix(A) || !H || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (prec != AUNMF_FP32) {
+    if (!A->dense) return AUNMF_E_UNSUPPORTED;
+    int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
+    if (rc != AUNMF_OK) return rc;
+  }
+  const int64_t n = A->n, m = A->m;
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  RunCtx c{};
+  c.A = A;
+  c.k = k;
+  c.prec = prec;
+  c.Ht = P<float>(h->Ht);
+  c.PW = Pout;
+  CK(h, launch_transpose(H, k, n, c.Ht, h->stream));
+  if (prec == AUNMF_BF16) {
+    ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
+    ENS(h, h->Htbf, sizeof(uint16_t) * tc::factor_elems(n, k));
+    c.Abf = P<uint16_t>(h->Abf);
+    c.Htbf = P<uint16_t>(h->Htbf);
+    CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), h->stream));
+  }
+  CK(h, product_aht(h, c, h->stream));
+  return AUNMF_OK;
+}
+
+int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int prec, float *Pout) {
+  if (!h || !valid_matrix(A) || !W || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (prec != AUNMF_FP32) {
+    if (!A->dense) return AUNMF_E_UNSUPPORTED;
+    int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
+    if (rc != AUNMF_OK) return rc;
+  }
+  const int64_t n = A->n, m = A->m;
+  ENS(h, h->PHt, sizeof(float) * n * k);
+  RunCtx c{};
+  c.A = A;
+  c.k = k;
+  c.prec = prec;
+  c.W = const_cast<float *>(W);
+  c.PHt = P<float>(h->PHt);
+  if (prec == AUNMF_BF16) {
+    ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
+    ENS(h, h->Wbf, sizeof(uint16_t) * tc::factor_elems(m, k));
+    c.Abf = P<uint16_t>(h->Abf);
+    c.Wbf = P<uint16_t>(h->Wbf);
+    CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), h->stream));
+  }
+  CK(h, product_wta(h, c, h->stream));
+  CK(h, launch_transpose(c.PHt, n, k, Pout, h->stream));
+  return AUNMF_OK;
+}
+
+int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const float *GH,
+                   int64_t m, int k, float *H, int64_t n, double eps) {
+  if (!h || !W || !PW || !GH || m < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (algo < AUNMF_MU || algo > AUNMF_ABPP) return AUNMF_E_INVAL;
+  if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
+  cudaStream_t s = h->stream;
+  ENS(h, h->ctr, sizeof(DevCounters));
+  RunCtx c{};
+  c.k = k;
+  c.algo = algo;
+  c.mu_eps = (float)(eps > 0 ? eps : 1e-16);
+  c.max_piv = 10 * k;
+  c.ctr = P<DevCounters>(h->ctr);
+  CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
+  CK(h, update(c, W, PW, GH, m, s));
+  if (algo == AUNMF_HALS) {
+    ENS(h, h->GW, sizeof(float) * k * k);
+    ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+    CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
+    if (H && n > 0) {
+      ENS(h, h->Ht, sizeof(float) * n * k);
+      CK(h, launch_transpose(H, k, n, P<float>(h->Ht), s));
+      CK(h, launch_hals_normalise(W, m, P<float>(h->Ht), n, P<float>(h->GW), k, s));
+      CK(h, launch_transpose(P<float>(h->Ht), n, k, H, s));
+    } else {
+      CK(h, launch_hals_normalise(W, m, nullptr, 0, P<float>(h->GW), k, s));
+    }
+  }
+  return AUNMF_OK;
+}
+
+int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const float *GW, int k,
+                   int64_t n, double eps) {
+  if (!h || !H || !PH || !GW || n < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (algo < AUNMF_MU || algo > AUNMF_ABPP) return AUNMF_E_INVAL;
+  if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
+  cudaStream_t s = h->stream;
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  ENS(h, h->PHt, sizeof(float) * n * k);
+  ENS(h, h->ctr, sizeof(DevCounters));
+  RunCtx c{};
+  c.k = k;
+  c.algo = algo;
+  c.mu_eps = (float)(eps > 0 ? eps : 1e-16);
+  c.max_piv = 10 * k;
+  c.ctr = P<DevCounters>(h->ctr);
+  CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
+  CK(h, launch_transpose(H, k, n, P<float>(h->Ht), s));
+  CK(h, launch_transpose(PH, k, n, P<float>(h->PHt), s));
+  CK(h, update(c, P<float>(h->Ht), P<float>(h->PHt), GW, n, s));
+  CK(h, launch_transpose(P<float>(h->Ht), n, k, H, s));
+  return AUNMF_OK;
+}
+
+int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs, int k, float *X,
+                  int max_pivots, int64_t *pivots, int64_t *nonconv) {
+  if (!h || !G || !R || !X || nrhs < 0 || k < 1 || k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
+  cudaStream_t s = h->stream;
+  ENS(h, h->ctr, sizeof(DevCounters));
+  DevCounters *ctr = P<DevCounters>(h->ctr);
+  CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+  CK(h, launch_bpp(G, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, ctr, nullptr, s));
+  DevCounters hc{};
+  CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (pivots) *pivots = hc.bpp_pivots;
+  if (nonconv) *nonconv = hc.bpp_nonconv;
+  if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
+  if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;
+  return AUNMF_OK;
+}
+
+int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const float *H, int k,
+                 double *relres) {
+  if (!h || !valid_matrix(A) || !W || !H || !relres || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  const int64_t m = A->m, n = A->n;
+  cudaStream_t s = h->stream;
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  ENS(h, h->PHt, sizeof(float) * n * k);
+  ENS(h, h->GH, sizeof(float) * k * k);
+  ENS(h, h->GW, sizeof(float) * k * k);
+  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  ENS(h, h->dpart, sizeof(double) * (h->n_dparts + 8));
+  ENS(h, h->n2a, sizeof(double));
+  ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->last, sizeof(double));
+  float *Ht = P<float>(h->Ht), *PHt = P<float>(h->PHt);
+  double *dp = P<double>(h->dpart);
+  CK(h, cudaMemsetAsync(h->ctr.p, 0, sizeof(DevCounters), s));
+  CK(h, launch_transpose(H, k, n, Ht, s));
+  if (A->dense) {
+    CK(h, launch_norm2(A->dense, m, n, A->lda, dp, h->n_dparts, P<double>(h->n2a), s));
+    CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, s));
+  } else {
+    CK(h, launch_norm2_vec(A->val, A->nnz, dp, h->n_dparts, P<double>(h->n2a), s));
+    CK(h, launch_wta_csr(A->rowptr, A->colidx, A->val, m, n, W, k, PHt, s));
+  }
+  CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
+  CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s));
+  CK(h, launch_relres(PHt, Ht, n * (int64_t)k, P<float>(h->GW), P<float>(h->GH), k,
+                      P<double>(h->n2a), dp, h->n_dparts, nullptr, P<DevCounters>(h->ctr),
+                      P<double>(h->last), s));
+  CK(h, cudaMemcpyAsync(relres, h->last.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  return AUNMF_OK;
+}
+
+}  // extern "C"

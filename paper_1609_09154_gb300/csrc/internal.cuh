@@ -1,0 +1,86 @@
+// internal.cuh -- declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (that is include/aunmf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/aunmf.h"
+
+namespace aunmf {
+
+constexpr int kWarp = 32;
+
+// Kernels enqueued by this thread since the counter was last read; every
+// launcher adds the number of kernels it launches.
+extern thread_local long long g_launches;
+
+// Device-side error/diagnostic counters, one block of int64 in the workspace.
+struct DevCounters {
+  long long bpp_pivots;
+  long long bpp_nonconv;
+  long long bpp_numeric;
+  long long nonfinite;
+  long long iter;  // index of the next relres slot
+  long long pad[3];
+};
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `s` and return cudaGetLastError().
+
+// Gram: partial[b] = sum over rows of block b of X^T X (X rows x k, row-major,
+// leading dimension ldx); then G = sum_b partial[b] in FP64, fixed order.
+cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
+                        float *partials, int max_blocks, cudaStream_t s);
+int gram_partial_blocks(int64_t rows, int max_blocks);
+
+// SIMT FP32 products.
+//   aht: P_W (m x k, ld k) = A (m x n, lda) * Ht (n x k, ld k)
+//   wta: P_Ht (n x k, ld k) = A^T (n x m) * W (m x k, ld k)
+cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *Ht,
+                            int k, float *P, cudaStream_t s);
+cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
+                            int k, float *P, cudaStream_t s);
+
+// Sparse CSR products (FP32).
+cudaError_t launch_aht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                           int64_t m, const float *Ht, int k, float *P, cudaStream_t s);
+cudaError_t launch_wta_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                           int64_t m, int64_t n, const float *W, int k, float *P,
+                           cudaStream_t s);
+
+// Transpose: out (cols x rows) = in (rows x cols)^T, both row-major, dense ld.
+cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, float *out,
+                             cudaStream_t s);
+
+// Local updates on row-major X (rows x k) given P (rows x k) and G (k x k).
+cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
+                      cudaStream_t s);
+cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, int k,
+                        cudaStream_t s);
+// HALS normalisation: s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i (Y = Ht,
+// may be null, rows_y rows); GW_ij /= s_i s_j.  Zero norms leave column i as is.
+cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t rows_y, float *GW,
+                                  int k, cudaStream_t s);
+// BPP: X(r, :) = argmin_{x>=0} given G, R(r, :) in FP64.
+cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
+                       int max_pivots, DevCounters *ctr, double *Gd, cudaStream_t s);
+
+// Reductions for the relative residual.
+// sum of squares of A (dense) or of val (CSR) into *out (device double).
+cudaError_t launch_norm2(const float *A, int64_t m, int64_t n, int64_t lda, double *partials,
+                         int nparts, double *out, cudaStream_t s);
+cudaError_t launch_norm2_vec(const float *v, int64_t len, double *partials, int nparts,
+                             double *out, cudaStream_t s);
+// relres[ctr->iter++] = sqrt(max(0, n2a - 2 <P, Ht> + <GW, GH>) / n2a); also
+// copies the value to *last.
+cudaError_t launch_relres(const float *P, const float *Ht, int64_t len, const float *GW,
+                          const float *GH, int k, const double *n2a, double *partials,
+                          int nparts, double *relres_dev, DevCounters *ctr, double *last,
+                          cudaStream_t s);
+
+// Copy with a different leading dimension (rows x cols).
+cudaError_t launch_copy2d(const float *in, int64_t ld_in, float *out, int64_t ld_out,
+                          int64_t rows, int64_t cols, cudaStream_t s);
+
+}  // namespace aunmf

@@ -1,0 +1,218 @@
+// k_luc.cu -- local update computations (LUC) for MU and HALS.
+//
+// Both factors are held as row-major "rows x k" matrices (W, and H^T for H),
+// so one kernel serves both updates.  One warp owns one row; lane l holds
+// the entries j = l, l + 32, ... (KT = ceil(k / 32) per lane, k <= 256).
+// The k x k Gram matrix is staged in shared memory when it fits.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace aunmf {
+namespace {
+
+constexpr int kLucThreads = 256;
+constexpr int kLucWarps = kLucThreads / kWarp;
+constexpr int kSmemGramMaxK = 108;  // 108*108*4 B < 48 KB default dynamic limit
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool SMEM>
+__device__ __forceinline__ const float *stage_gram(const float *G, int k, float *sG) {
+  if constexpr (!SMEM) {
+    return G;
+  } else {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) sG[e] = G[e];
+    __syncthreads();
+    return sG;
+  }
+}
+
+// MU (Sec. 4.1, Eq. muupdate) on each row x of X with p the row of P:
+//   x_j <- x_j p_j / ((x G)_j + eps), all j at once (old x on the right).
+template <int KT, bool SMEM>
+__global__ void __launch_bounds__(kLucThreads)
+    k_mu(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ Gg,
+         int64_t rows, int k, float eps) {
+  extern __shared__ float sG[];
+  const float *G = stage_gram<SMEM>(Gg, k, sG);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
+  const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
+  for (int64_t r = w0; r < rows; r += wstride) {
+    float x[KT], den[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      x[t] = j < k ? X[r * k + j] : 0.f;
+      den[t] = 0.f;
+    }
+#pragma unroll
+    for (int tl = 0; tl < KT; ++tl) {
+      for (int ll = 0; ll < 32; ++ll) {
+        const int l = 32 * tl + ll;
+        if (l >= k) break;
+        const float xl = __shfl_sync(0xffffffffu, x[tl], ll);
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) den[t] = fmaf(xl, G[l * k + j], den[t]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) X[r * k + j] = x[t] * P[r * k + j] / (den[t] + eps);
+    }
+  }
+}
+
+// HALS column sweep (Sec. 4.2, Eq. halsupdate, exact coordinate steps):
+//   for i = 0..k-1:  x_i <- max(0, x_i + (p_i - (x G)_i) / G_ii)
+// with the current x (earlier entries already updated); G_ii <= 0 skips i.
+template <int KT, bool SMEM>
+__global__ void __launch_bounds__(kLucThreads)
+    k_hals(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ Gg,
+           int64_t rows, int k) {
+  extern __shared__ float sG[];
+  const float *G = stage_gram<SMEM>(Gg, k, sG);
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
+  const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
+  for (int64_t r = w0; r < rows; r += wstride) {
+    float x[KT], p[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      x[t] = j < k ? X[r * k + j] : 0.f;
+      p[t] = j < k ? P[r * k + j] : 0.f;
+    }
+#pragma unroll
+    for (int ti = 0; ti < KT; ++ti) {
+      for (int ii = 0; ii < 32; ++ii) {
+        const int i = 32 * ti + ii;
+        if (i >= k) break;
+        const float* Gi = G + i * k;  // G is symmetric: row i = column i
+        float part = 0.f;
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) part = fmaf(x[t], Gi[j], part);
+        }
+        const float dot = warp_sum(part);
+        const float gii = Gi[i];
+        if (lane == ii && gii > 0.f) {
+          const float v = x[ti] + (p[ti] - dot) / gii;
+          x[ti] = v > 0.f ? v : 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) X[r * k + j] = x[t];
+    }
+  }
+}
+
+// HALS normalisation (Eq. halsupdate, w^i / ||w^i||, compensated in H):
+// s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i; GW_ij /= s_i s_j.
+__global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
+                                  const float *__restrict__ GW, bool divide) {
+  const int64_t total = rows * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % k);
+    const float g = GW[i * k + i];
+    if (g > 0.f) {
+      const float s = sqrtf(g);
+      X[e] = divide ? X[e] / s : X[e] * s;
+    }
+  }
+}
+
+__global__ void k_hals_scale_gram(float *__restrict__ GW, int k) {
+  // one block: read the diagonal first, then rescale
+  __shared__ float sd[AUNMF_K_MAX];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const float g = GW[i * k + i];
+    sd[i] = g > 0.f ? sqrtf(g) : 1.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e % k;
+    GW[e] = GW[e] / (sd[i] * sd[j]);
+  }
+}
+
+int luc_blocks(int64_t rows) {
+  int64_t nb = (rows + kLucWarps - 1) / kLucWarps;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+#define AUNMF_KT_SWITCH(KT_VAL, CALL) \
+  switch (KT_VAL) {                   \
+    case 1: CALL(1); break;           \
+    case 2: CALL(2); break;           \
+    case 3: CALL(3); break;           \
+    case 4: CALL(4); break;           \
+    case 5: CALL(5); break;           \
+    case 6: CALL(6); break;           \
+    case 7: CALL(7); break;           \
+    default: CALL(8); break;          \
+  }
+
+}  // namespace
+
+cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
+                      cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  const int kt = (k + 31) / 32, nb = luc_blocks(rows);
+  const bool sm = k <= kSmemGramMaxK;
+  const size_t smem = sm ? sizeof(float) * k * k : 0;
+#define AUNMF_CALL_MU(KT)                                                          \
+  if (sm) k_mu<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k, eps);     \
+  else k_mu<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k, eps);
+  AUNMF_KT_SWITCH(kt, AUNMF_CALL_MU)
+#undef AUNMF_CALL_MU
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, int k,
+                        cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  const int kt = (k + 31) / 32, nb = luc_blocks(rows);
+  const bool sm = k <= kSmemGramMaxK;
+  const size_t smem = sm ? sizeof(float) * k * k : 0;
+#define AUNMF_CALL_HALS(KT)                                                    \
+  if (sm) k_hals<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k);    \
+  else k_hals<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k);
+  AUNMF_KT_SWITCH(kt, AUNMF_CALL_HALS)
+#undef AUNMF_CALL_HALS
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t rows_y, float *GW,
+                                  int k, cudaStream_t s) {
+  auto nb = [](int64_t total) {
+    int64_t b = (total + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+  };
+  if (rows_x > 0) k_hals_scale_rows<<<nb(rows_x * k), 256, 0, s>>>(X, rows_x, k, GW, true);
+  if (Y && rows_y > 0) k_hals_scale_rows<<<nb(rows_y * k), 256, 0, s>>>(Y, rows_y, k, GW, false);
+  k_hals_scale_gram<<<1, 256, 0, s>>>(GW, k);
+  g_launches += 1 + (rows_x > 0) + (Y && rows_y > 0);
+  return cudaGetLastError();
+}
+
+}  // namespace aunmf

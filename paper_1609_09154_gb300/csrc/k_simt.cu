@@ -1,0 +1,400 @@
+// k_simt.cu -- FP32/FP64 CUDA-core kernels of the AU-NMF hot path:
+//   * Gram matrices X^T X (Alg. 1 lines 3-4: H H^T, W^T W; the all-reduce of
+//     Alg. 3 becomes a fixed-order FP64 reduction of per-block partials)
+//   * the two products with A on CUDA cores (Alg. 1: A H^T, W^T A)
+//   * transposes, ||A||^2 and the relative residual of Sec. 6.2 from the
+//     expansion ||A||^2 - 2 <W^T A, H> + <W^T W, H H^T>.
+// Internally H is held transposed (Ht, n x k) so that both factors are
+// row-major "rows x k" and share the same update kernels.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace aunmf {
+
+// ------------------------------------------------------------------ Gram
+// Block b accumulates X^T X over rows [b*chunk, (b+1)*chunk) into
+// partials[b] (k x k).  Each thread owns a 4x4 tile of G; rows are staged in
+// shared memory 32 at a time.
+namespace {
+constexpr int kGramRows = 32;
+constexpr int kGramThreads = 256;
+
+__global__ void __launch_bounds__(kGramThreads)
+    k_gram_partial(const float *__restrict__ X, int64_t rows, int k, int64_t ldx, int64_t chunk,
+                   float *__restrict__ partials) {
+  extern __shared__ float sX[];  // [kGramRows][kp]
+  const int kp = (k + 3) & ~3;
+  const int nt = kp / 4, ntiles = nt * nt;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(rows, r0 + chunk);
+  float *out = partials + (int64_t)blockIdx.x * k * k;
+  for (int tb = 0; tb < ntiles; tb += kGramThreads) {
+    const int t = tb + threadIdx.x;
+    const bool act = t < ntiles;
+    const int ti = act ? t / nt : 0, tj = act ? t % nt : 0;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int64_t c0 = r0; c0 < r1; c0 += kGramRows) {
+      const int nr = (int)min((int64_t)kGramRows, r1 - c0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kGramRows * kp; idx += kGramThreads) {
+        const int rr = idx / kp, cc = idx % kp;
+        sX[idx] = (rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+      }
+      __syncthreads();
+      if (act) {
+        for (int rr = 0; rr < nr; ++rr) {
+          const float4 a = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * ti]);
+          const float4 b = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * tj]);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+        }
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * ti + p, j = 4 * tj + q;
+          if (i < k && j < k) out[i * k + j] = acc[p][q];
+        }
+    }
+  }
+}
+
+// G_ij = sum_b partials[b]_ij, in FP64, b ascending.
+__global__ void k_gram_reduce(const float *__restrict__ partials, int nb, int k,
+                              float *__restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += (double)partials[(int64_t)b * k * k + e];
+  G[e] = (float)s;
+}
+}  // namespace
+
+int gram_partial_blocks(int64_t rows, int max_blocks) {
+  int64_t nb = (rows + 127) / 128;  // at least 128 rows per block
+  if (nb > max_blocks) nb = max_blocks;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
+                        float *partials, int max_blocks, cudaStream_t s) {
+  const int nb = gram_partial_blocks(rows, max_blocks);
+  const int64_t chunk = (rows + nb - 1) / nb;
+  const int kp = (k + 3) & ~3;
+  const size_t smem = sizeof(float) * kGramRows * kp;
+  k_gram_partial<<<nb, kGramThreads, smem, s>>>(X, rows, k, ldx, chunk, partials);
+  k_gram_reduce<<<(k * k + 255) / 256, 256, 0, s>>>(partials, nb, k, G);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ SIMT GEMM
+// C (M x N, ld ldc) = Aop (M x K) * B (K x N, ld ldb), FP32 FMA.
+//   AK = true : Aop(mm, kk) = A[mm * lda + kk]   (A H^T: A is K-contiguous)
+//   AK = false: Aop(mm, kk) = A[kk * lda + mm]   (W^T A as (A^T W): M-contiguous)
+// 256 threads as 16 x 16; each owns a (BM/16) x (BN/16) tile; register
+// prefetch of the next K-slab while the current one is consumed from shared
+// memory.
+namespace {
+template <int BM, int BN, int BK, bool AK>
+__global__ void __launch_bounds__(256)
+    k_gemm_simt(const float *__restrict__ A, int64_t lda, int64_t M, int64_t K,
+                const float *__restrict__ B, int ldb, int N, float *__restrict__ C, int ldc) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  constexpr int LA = BM * BK / 256, LB = BK * BN / 256;
+  static_assert(LA >= 1 && LB >= 1, "tile too small");
+  __shared__ float sA[2][BK][BM];
+  __shared__ float sB[2][BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+
+  float ra[LA], rb[LB];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int idx = tid + 256 * q;
+      int mm, kk;
+      if (AK) { kk = idx % BK; mm = idx / BK; } else { mm = idx % BM; kk = idx / BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < M && gk < K) v = AK ? __ldg(&A[gm * lda + gk]) : __ldg(&A[gk * lda + gm]);
+      ra[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int idx = tid + 256 * q;
+      const int nn = idx % BN, kk = idx / BN;
+      const int64_t gk = k0 + kk;
+      const int gn = n0 + nn;
+      rb[q] = (gk < K && gn < N) ? __ldg(&B[gk * ldb + gn]) : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int idx = tid + 256 * q;
+      int mm, kk;
+      if (AK) { kk = idx % BK; mm = idx / BK; } else { mm = idx % BM; kk = idx / BM; }
+      sA[buf][kk][mm] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int idx = tid + 256 * q;
+      sB[buf][idx / BN][idx % BN] = rb[q];
+    }
+  };
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) load(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = sA[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = sB[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn < N) C[gm * ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+template <bool AK>
+cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const float *B, int N,
+                      float *C, cudaStream_t s) {
+  constexpr int BM = 128, BK = 16;
+  const unsigned gx = (unsigned)((M + BM - 1) / BM);
+  if (N <= 16) {
+    k_gemm_simt<BM, 16, BK, AK><<<dim3(gx, 1), 256, 0, s>>>(A, lda, M, K, B, N, N, C, N);
+  } else if (N <= 32) {
+    k_gemm_simt<BM, 32, BK, AK><<<dim3(gx, 1), 256, 0, s>>>(A, lda, M, K, B, N, N, C, N);
+  } else {
+    k_gemm_simt<BM, 64, BK, AK><<<dim3(gx, (N + 63) / 64), 256, 0, s>>>(A, lda, M, K, B, N, N,
+                                                                          C, N);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *Ht,
+                            int k, float *P, cudaStream_t s) {
+  return gemm_simt<true>(A, lda, m, n, Ht, k, P, s);
+}
+
+cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
+                            int k, float *P, cudaStream_t s) {
+  return gemm_simt<false>(A, lda, n, m, W, k, P, s);
+}
+
+// ------------------------------------------------------------------ transpose
+namespace {
+__global__ void k_transpose(const float *__restrict__ in, int64_t rows, int64_t cols,
+                            float *__restrict__ out) {
+  __shared__ float t[32][33];
+  const int64_t tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < tr * tc; tile += gridDim.x) {
+    const int64_t r0 = (tile / tc) * 32, c0 = (tile % tc) * 32;
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t r = r0 + y, c = c0 + threadIdx.x;
+      if (r < rows && c < cols) t[y][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t c = c0 + y, r = r0 + threadIdx.x;
+      if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][y];
+    }
+  }
+}
+
+__global__ void k_copy2d(const float *__restrict__ in, int64_t ld_in, float *__restrict__ out,
+                         int64_t ld_out, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    out[r * ld_out + c] = in[r * ld_in + c];
+  }
+}
+}  // namespace
+
+cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, float *out,
+                             cudaStream_t s) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+  if (tiles > 152 * 64) tiles = 152 * 64;
+  k_transpose<<<(unsigned)tiles, dim3(32, 8), 0, s>>>(in, rows, cols, out);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(const float *in, int64_t ld_in, float *out, int64_t ld_out,
+                          int64_t rows, int64_t cols, cudaStream_t s) {
+  if (rows * cols == 0) return cudaSuccess;
+  int64_t nb = (rows * cols + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  k_copy2d<<<(unsigned)nb, 256, 0, s>>>(in, ld_in, out, ld_out, rows, cols);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ reductions
+namespace {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide FP64 sum in a fixed tree order; result valid in thread 0.
+__device__ double block_sum_d(double v) {
+  __shared__ double sw[32];
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sw[lane] : 0.0;
+    r = warp_sum_d(r);
+  }
+  return r;
+}
+
+// partials[b] = sum of squares over rows r = b, b + nb, ... of A (m x n, lda)
+__global__ void k_norm2_partial(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                double *__restrict__ partials) {
+  double s = 0.0;
+  for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+    const float *row = A + r * lda;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      const double v = (double)row[c];
+      s = fma(v, v, s);
+    }
+  }
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_norm2_vec_partial(const float *__restrict__ v, int64_t len,
+                                    double *__restrict__ partials) {
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (double)v[e];
+    s = fma(x, x, s);
+  }
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_sum_partials(const double *__restrict__ partials, int nparts,
+                               double *__restrict__ out) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += partials[b];
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_dot_partial(const float *__restrict__ P, const float *__restrict__ Q,
+                              int64_t len, double *__restrict__ partials) {
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    s = fma((double)P[e], (double)Q[e], s);
+  s = block_sum_d(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_relres_final(const double *__restrict__ partials, int nparts,
+                               const float *__restrict__ GW, const float *__restrict__ GH, int k,
+                               const double *__restrict__ n2a, double *__restrict__ relres,
+                               DevCounters *ctr, double *last) {
+  double cross = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) cross += partials[b];
+  cross = block_sum_d(cross);
+  double quad = 0.0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
+  quad = block_sum_d(quad);
+  if (threadIdx.x == 0) {
+    const double a2 = *n2a;
+    double r2 = a2 - 2.0 * cross + quad;
+    if (r2 < 0.0) r2 = 0.0;
+    const double rr = a2 > 0.0 ? sqrt(r2 / a2) : 0.0;
+    if (!isfinite(rr)) ctr->nonfinite += 1;
+    if (relres) relres[ctr->iter] = rr;
+    ctr->iter += 1;
+    if (last) *last = rr;
+  }
+}
+}  // namespace
+
+cudaError_t launch_norm2(const float *A, int64_t m, int64_t n, int64_t lda, double *partials,
+                         int nparts, double *out, cudaStream_t s) {
+  k_norm2_partial<<<nparts, 256, 0, s>>>(A, m, n, lda, partials);
+  k_sum_partials<<<1, 256, 0, s>>>(partials, nparts, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2_vec(const float *v, int64_t len, double *partials, int nparts,
+                             double *out, cudaStream_t s) {
+  k_norm2_vec_partial<<<nparts, 256, 0, s>>>(v, len, partials);
+  k_sum_partials<<<1, 256, 0, s>>>(partials, nparts, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relres(const float *P, const float *Ht, int64_t len, const float *GW,
+                          const float *GH, int k, const double *n2a, double *partials,
+                          int nparts, double *relres_dev, DevCounters *ctr, double *last,
+                          cudaStream_t s) {
+  k_dot_partial<<<nparts, 256, 0, s>>>(P, Ht, len, partials);
+  k_relres_final<<<1, 256, 0, s>>>(partials, nparts, GW, GH, k, n2a, relres_dev, ctr, last);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace aunmf

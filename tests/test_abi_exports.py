@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a and exports every function that
+include/aunmf.h declares (no GPU needed: nothing is called)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aunmf.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(aunmf_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("aunmf_create", "aunmf_destroy", "aunmf_run", "aunmf_run_host", "aunmf_strerror",
+                 "aunmf_gram_w", "aunmf_gram_h", "aunmf_aht", "aunmf_wta", "aunmf_update_w",
+                 "aunmf_update_h", "aunmf_nls_bpp", "aunmf_relres"):
+        assert must in names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1609_09154_gb300 import build
+
+    if shutil_which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    return build.build()
+
+
+def shutil_which(x):
+    import shutil
+
+    return shutil.which(x)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(aunmf_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_1609_09154_gb300 import aunmf
+
+    assert set(declared_functions()) <= set(aunmf.SIGNATURES), (
+        set(declared_functions()) - set(aunmf.SIGNATURES))
+
+
+def test_library_loads_without_gpu(libpath):
+    import ctypes
+
+    L = ctypes.CDLL(libpath)
+    L.aunmf_strerror.restype = ctypes.c_char_p
+    L.aunmf_strerror.argtypes = [ctypes.c_int]
+    assert L.aunmf_strerror(-1) == b"invalid argument"
+    assert L.aunmf_strerror(0) == b"ok"
