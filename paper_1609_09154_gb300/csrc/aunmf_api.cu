@@ -36,7 +36,8 @@ struct aunmf_handle {
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   std::string cuda_err;
   // workspace
-  Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last, Abf, Wbf, Htbf;
+  Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last;
+  Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
@@ -101,8 +102,15 @@ struct RunCtx {
   float *W, *Ht, *PW, *PHt, *GH, *GW, *gpart;
   double *dpart, *n2a, *relres_dev, *last;
   DevCounters *ctr;
-  const uint16_t *Abf;  // BF16 copy of A (prec == BF16)
-  uint16_t *Wbf, *Htbf; // BF16 copies of the factors
+  // tensor-core path (prec != FP32): X operands of the two products (A or its
+  // BF16 copy, m x n; A^T copy, n x m), K-major factor copies (H as k x n,
+  // W^T as k x m), split-K partials and the device error flag
+  const void *Ax, *At;
+  int64_t ldx, ldat;
+  void *Hk, *Wt;
+  int64_t ldh, ldw;
+  float *parts;
+  int *err;
   bool profile;
   std::vector<cudaEvent_t> *ev;          // profile events (pairs)
   std::vector<int> *ev_phase;            // phase index per pair
@@ -133,21 +141,70 @@ struct PhaseTimer {
 
 cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const aunmf_matrix *A = c.A;
-  if (!A->dense)
-    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, s);
-  if (c.prec == AUNMF_FP32) return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
   (void)h;
-  return tc::launch_aht_tc(A->dense, c.Abf, A->m, A->n, A->lda, c.Ht, c.Htbf, c.k, c.prec, c.PW, s);
+  if (!A->dense) {
+    PhaseTimer t(c, s, kPhAht);
+    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, s);
+  }
+  if (c.prec == AUNMF_FP32) {
+    PhaseTimer t(c, s, kPhAht);
+    return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
+  }
+  const bool bf = c.prec == AUNMF_BF16;
+  const int S = tc::splits_for(A->m, A->n, bf);
+  cudaError_t e;
+  {
+    PhaseTimer t(c, s, kPhOther);
+    if ((e = tc::launch_transpose_to(c.Ht, A->n, c.k, c.k, c.Hk, c.ldh, bf, s)) != cudaSuccess) return e;
+  }
+  {
+    PhaseTimer t(c, s, kPhAht);
+    e = tc::launch_gemm(c.Ax, A->m, A->n, c.ldx, c.Hk, c.k, c.ldh, bf, S == 1 ? c.PW : c.parts, S,
+                        c.err, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (S > 1) {
+    PhaseTimer t(c, s, kPhOther);
+    return tc::launch_sum_splits(c.parts, S, A->m * (int64_t)c.k, c.PW, s);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const aunmf_matrix *A = c.A;
-  if (!A->dense)
-    return launch_wta_csr(A->rowptr, A->colidx, A->val, A->m, A->n, c.W, c.k, c.PHt, s);
-  if (c.prec == AUNMF_FP32) return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
   (void)h;
-  return tc::launch_wta_tc(A->dense, c.Abf, A->m, A->n, A->lda, c.W, c.Wbf, c.k, c.prec, c.PHt, s);
+  if (!A->dense) {
+    PhaseTimer t(c, s, kPhWta);
+    return launch_wta_csr(A->rowptr, A->colidx, A->val, A->m, A->n, c.W, c.k, c.PHt, s);
+  }
+  if (c.prec == AUNMF_FP32) {
+    PhaseTimer t(c, s, kPhWta);
+    return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
+  }
+  const bool bf = c.prec == AUNMF_BF16;
+  const int S = tc::splits_for(A->n, A->m, bf);
+  cudaError_t e;
+  {
+    PhaseTimer t(c, s, kPhOther);
+    if ((e = tc::launch_transpose_to(c.W, A->m, c.k, c.k, c.Wt, c.ldw, bf, s)) != cudaSuccess) return e;
+  }
+  {
+    PhaseTimer t(c, s, kPhWta);
+    e = tc::launch_gemm(c.At, A->n, A->m, c.ldat, c.Wt, c.k, c.ldw, bf, S == 1 ? c.PHt : c.parts,
+                        S, c.err, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (S > 1) {
+    PhaseTimer t(c, s, kPhOther);
+    return tc::launch_sum_splits(c.parts, S, A->n * (int64_t)c.k, c.PHt, s);
+  }
+  return cudaSuccess;
 }
+
+// Workspace and one-off layout copies of A for the tensor-core products:
+// X of A H^T is A itself (TF32, when its rows are 16-byte aligned) or a copy
+// with padded rows / in BF16; X of W^T A is A^T (FP32 or BF16).
+int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s);
 
 cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, int64_t rows,
                    cudaStream_t s) {
@@ -163,7 +220,7 @@ cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const int64_t m = c.A->m, n = c.A->n;
   const int k = c.k;
   cudaError_t e;
-  { PhaseTimer t(c, s, kPhAht); if ((e = product_aht(h, c, s)) != cudaSuccess) return e; }
+  if ((e = product_aht(h, c, s)) != cudaSuccess) return e;
   { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.W, c.PW, c.GH, m, s)) != cudaSuccess) return e; }
   {
     PhaseTimer t(c, s, kPhGram);
@@ -173,7 +230,7 @@ cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
     PhaseTimer t(c, s, kPhUpdate);
     if ((e = launch_hals_normalise(c.W, m, c.Ht, n, c.GW, k, s)) != cudaSuccess) return e;
   }
-  { PhaseTimer t(c, s, kPhWta); if ((e = product_wta(h, c, s)) != cudaSuccess) return e; }
+  if ((e = product_wta(h, c, s)) != cudaSuccess) return e;
   { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.Ht, c.PHt, c.GW, n, s)) != cudaSuccess) return e; }
   {
     PhaseTimer t(c, s, kPhGram);
@@ -203,6 +260,54 @@ int check_run_args(const aunmf_matrix *A, int k, int algo, int iters, const floa
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
     if (rc != AUNMF_OK) return rc;
   }
+  return AUNMF_OK;
+}
+
+#define ENS_TC(h, buf, bytes)              \
+  do {                                     \
+    int rc_ = ensure(h, buf, (bytes));     \
+    if (rc_ != AUNMF_OK) return rc_;       \
+  } while (0)
+
+int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
+  const aunmf_matrix *A = c.A;
+  const int64_t m = A->m, n = A->n;
+  const int k = c.k;
+  const bool bf = c.prec == AUNMF_BF16;
+  const size_t esz = bf ? 2 : 4;
+  c.ldh = tc::copy_ld(n);
+  c.ldw = tc::copy_ld(m);
+  c.ldat = tc::copy_ld(m);
+  ENS_TC(h, h->Hk, esz * tc::factor_elems(n, k));
+  ENS_TC(h, h->Wt, esz * tc::factor_elems(m, k));
+  ENS_TC(h, h->At, esz * (size_t)n * c.ldat);
+  const size_t parts = tc::parts_elems(m > n ? m : n, k);
+  ENS_TC(h, h->parts, sizeof(float) * parts);
+  ENS_TC(h, h->err, sizeof(int));
+  c.Hk = h->Hk.p;
+  c.Wt = h->Wt.p;
+  c.At = h->At.p;
+  c.parts = P<float>(h->parts);
+  c.err = P<int>(h->err);
+  cudaError_t e = cudaMemsetAsync(c.err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(err)");
+  const bool aligned = ((uintptr_t)A->dense % 16 == 0) && (A->lda % 4 == 0);
+  if (!bf && aligned) {
+    c.Ax = A->dense;
+    c.ldx = A->lda;
+  } else {
+    c.ldx = tc::copy_ld(n);
+    ENS_TC(h, h->Ax, esz * (size_t)m * c.ldx);
+    c.Ax = h->Ax.p;
+    if (bf) {
+      e = tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Ax), c.ldx, s);
+    } else {
+      e = launch_copy2d(A->dense, A->lda, P<float>(h->Ax), c.ldx, m, n, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(h, e, "copy of A");
+  }
+  e = tc::launch_transpose_to(A->dense, m, n, A->lda, h->At.p, c.ldat, bf, s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "transpose of A");
   return AUNMF_OK;
 }
 
@@ -253,8 +358,8 @@ int aunmf_destroy(aunmf_handle *h) {
   if (!h) return AUNMF_E_INVAL;
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
-                 &h->ctr, &h->relres, &h->last, &h->Abf, &h->Wbf, &h->Htbf, &h->hA, &h->hW,
-                 &h->hH};
+                 &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
+                 &h->err, &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -311,17 +416,6 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   c.ev = &ev;
   c.ev_phase = &ev_phase;
   c.profile = o.profile != 0;
-  if (o.prec != AUNMF_FP32) {
-    if (o.prec == AUNMF_BF16) {
-      ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
-      ENS(h, h->Wbf, sizeof(uint16_t) * tc::factor_elems(m, k));
-      ENS(h, h->Htbf, sizeof(uint16_t) * tc::factor_elems(n, k));
-      c.Abf = P<uint16_t>(h->Abf);
-      c.Wbf = P<uint16_t>(h->Wbf);
-      c.Htbf = P<uint16_t>(h->Htbf);
-    }
-  }
-
   const long long launches0 = g_launches;
   long long graph_launches = 0;
   cudaEvent_t t0, t1;
@@ -341,7 +435,10 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
   }
-  if (o.prec == AUNMF_BF16) CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), s));
+  if (o.prec != AUNMF_FP32) {
+    int prc = prepare_tc(h, c, s);
+    if (prc != AUNMF_OK) return prc;
+  }
   CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
 
   cudaGraphExec_t gexec = nullptr;
@@ -369,7 +466,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   CK(h, launch_transpose(c.Ht, n, k, H, s));
   CK(h, cudaEventRecord(t1, s));
   DevCounters hc{};
+  int herr = 0;
   CK(h, cudaMemcpyAsync(&hc, c.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+  if (c.err) CK(h, cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (relres && iters > 0)
     CK(h, cudaMemcpyAsync(relres, c.relres_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
@@ -398,6 +497,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  if (herr) return AUNMF_E_TIMEOUT;
   if (hc.nonfinite) return AUNMF_E_NUMERIC;
   if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
   if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;
@@ -451,12 +551,12 @@ int aunmf_gram_h(aunmf_handle *h, const float *H, int k, int64_t n, float *G) {
 int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int prec, float *Pout) {
   if (!h || !valid_matrix(A) || !H || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (!A->dense) return AUNMF_E_UNSUPPORTED;
   if (prec != AUNMF_FP32) {
-    if (!A->dense) return AUNMF_E_UNSUPPORTED;
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
     if (rc != AUNMF_OK) return rc;
   }
-  const int64_t n = A->n, m = A->m;
+  const int64_t n = A->n;
   ENS(h, h->Ht, sizeof(float) * n * k);
   RunCtx c{};
   c.A = A;
@@ -465,12 +565,9 @@ int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int
   c.Ht = P<float>(h->Ht);
   c.PW = Pout;
   CK(h, launch_transpose(H, k, n, c.Ht, h->stream));
-  if (prec == AUNMF_BF16) {
-    ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
-    ENS(h, h->Htbf, sizeof(uint16_t) * tc::factor_elems(n, k));
-    c.Abf = P<uint16_t>(h->Abf);
-    c.Htbf = P<uint16_t>(h->Htbf);
-    CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), h->stream));
+  if (prec != AUNMF_FP32) {
+    int rc = prepare_tc(h, c, h->stream);
+    if (rc != AUNMF_OK) return rc;
   }
   CK(h, product_aht(h, c, h->stream));
   return AUNMF_OK;
@@ -479,12 +576,12 @@ int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int
 int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int prec, float *Pout) {
   if (!h || !valid_matrix(A) || !W || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (!A->dense) return AUNMF_E_UNSUPPORTED;
   if (prec != AUNMF_FP32) {
-    if (!A->dense) return AUNMF_E_UNSUPPORTED;
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
     if (rc != AUNMF_OK) return rc;
   }
-  const int64_t n = A->n, m = A->m;
+  const int64_t n = A->n;
   ENS(h, h->PHt, sizeof(float) * n * k);
   RunCtx c{};
   c.A = A;
@@ -492,12 +589,9 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
   c.prec = prec;
   c.W = const_cast<float *>(W);
   c.PHt = P<float>(h->PHt);
-  if (prec == AUNMF_BF16) {
-    ENS(h, h->Abf, sizeof(uint16_t) * (size_t)m * n);
-    ENS(h, h->Wbf, sizeof(uint16_t) * tc::factor_elems(m, k));
-    c.Abf = P<uint16_t>(h->Abf);
-    c.Wbf = P<uint16_t>(h->Wbf);
-    CK(h, tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Abf), h->stream));
+  if (prec != AUNMF_FP32) {
+    int rc = prepare_tc(h, c, h->stream);
+    if (rc != AUNMF_OK) return rc;
   }
   CK(h, product_wta(h, c, h->stream));
   CK(h, launch_transpose(c.PHt, n, k, Pout, h->stream));

@@ -104,9 +104,14 @@ cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float 
 // C (M x N, ld ldc) = Aop (M x K) * B (K x N, ld ldb), FP32 FMA.
 //   AK = true : Aop(mm, kk) = A[mm * lda + kk]   (A H^T: A is K-contiguous)
 //   AK = false: Aop(mm, kk) = A[kk * lda + mm]   (W^T A as (A^T W): M-contiguous)
-// 256 threads as 16 x 16; each owns a (BM/16) x (BN/16) tile; register
-// prefetch of the next K-slab while the current one is consumed from shared
-// memory.
+// 256 threads as 16 x 16; thread (ty, tx) owns rows ty*TM .. ty*TM+TM-1 and
+// columns tx*TN .. tx*TN+TN-1 of the block tile.  The next K-slab is
+// prefetched into registers while the current one is consumed from shared
+// memory.  Accumulation is compensated: each 32-long K-slab is summed in a
+// fresh FP32 register and added to the running sum with Kahan's correction,
+// so the error does not grow with K (the residual expansion of Sec. 6.2
+// subtracts nearly equal terms and needs the products close to FP32
+// rounding).
 namespace {
 template <int BM, int BN, int BK, bool AK>
 __global__ void __launch_bounds__(256)
@@ -114,9 +119,12 @@ __global__ void __launch_bounds__(256)
                 const float *__restrict__ B, int ldb, int N, float *__restrict__ C, int ldc) {
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BK * BN / 256;
-  static_assert(LA >= 1 && LB >= 1, "tile too small");
-  __shared__ float sA[2][BK][BM];
-  __shared__ float sB[2][BK][BN];
+  constexpr int PADA = 4;  // row pad: spreads the transposed stores over banks
+  constexpr int SLAB = 32; // K elements per compensated partial
+  static_assert(LA >= 1 && LB >= 1 && TM % 4 == 0, "tile too small");
+  static_assert(SLAB % BK == 0, "slab must be a multiple of BK");
+  __shared__ __align__(16) float sA[2][BK][BM + PADA];
+  __shared__ __align__(16) float sB[2][BK][BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
@@ -157,11 +165,23 @@ __global__ void __launch_bounds__(256)
     }
   };
 
-  float acc[TM][TN];
+  float acc[TM][TN], hi[TM][TN], cor[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = hi[i][j] = cor[i][j] = 0.f;
+  auto fold = [&]() {  // hi += acc with Kahan's compensation; acc = 0
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const float y = acc[i][j] - cor[i][j];
+        const float t = hi[i][j] + y;
+        cor[i][j] = (t - hi[i][j]) - y;
+        hi[i][j] = t;
+        acc[i][j] = 0.f;
+      }
+  };
 
   load(0);
   store(0);
@@ -174,14 +194,26 @@ __global__ void __launch_bounds__(256)
     for (int kk = 0; kk < BK; ++kk) {
       float a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = sA[buf][kk][ty + 16 * i];
+      for (int i = 0; i < TM; i += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(&sA[buf][kk][ty * TM + i]);
+        a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
+      }
+      if constexpr (TN == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(&sB[buf][kk][tx * TN]);
+        b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+      } else if constexpr (TN == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(&sB[buf][kk][tx * TN]);
+        b[0] = v.x; b[1] = v.y;
+      } else {
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = sB[buf][kk][tx + 16 * j];
+        for (int j = 0; j < TN; ++j) b[j] = sB[buf][kk][tx * TN + j];
+      }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
+    if (((k0 + BK) % SLAB) == 0 || !more) fold();
     if (more) {
       store(buf ^ 1);
       __syncthreads();
@@ -190,12 +222,12 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    const int64_t gm = m0 + ty + 16 * i;
+    const int64_t gm = m0 + ty * TM + i;
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int gn = n0 + tx + 16 * j;
-      if (gn < N) C[gm * ldc + gn] = acc[i][j];
+      const int gn = n0 + tx * TN + j;
+      if (gn < N) C[gm * ldc + gn] = hi[i][j] - cor[i][j];
     }
   }
 }

@@ -1,21 +1,534 @@
-// k_tc.cu -- tensor-core products (placeholder until the tcgen05 kernels land).
+// k_tc.cu -- the two products with A on the 5th-generation tensor cores
+// (Alg. 1 lines 3-4: A H^T and W^T A), for sm_103a.
+//
+// Both products are computed as  C (M x k) = X (M x K) * Y (k x K)^T  with X
+// and Y stored K-contiguous ("K-major"):
+//   A H^T : X = A   (m x n),  Y = H   (k x n)   ->  C = P_W   (m x k)
+//   W^T A : X = A^T (n x m),  Y = W^T (k x m)   ->  C = P_H^T (n x k)
+// The library keeps a transposed copy of A for the second product (set up
+// once per run), so each product streams one copy of A exactly once.
+//
+// Kernel: persistent, one CTA per SM, 6 warps.
+//   warp 0     TMA producer: 256 x 128 B of X and BN x 128 B of Y per stage,
+//              128-byte swizzle, into an N-stage shared-memory ring
+//   warp 1     owns the TMEM allocation; one thread issues tcgen05.mma
+//              (two M = 128 MMAs per K step share the Y tile) and commits
+//              stage releases / accumulator-ready to mbarriers
+//   warps 2-5  epilogue: tcgen05.ld of the FP32 accumulators (one row per
+//              thread per 128-row half), stores to the split's partial C
+// Accumulators are double-buffered in TMEM (2 x 2 x BN columns) when
+// BN <= 128 so that a tile's epilogue overlaps the next tile's main loop.
+// Work unit = (256-row tile, K split); splits are summed afterwards in a
+// fixed order, so results do not depend on scheduling.
+//
+// Every mbarrier wait is bounded (clock64); on expiry the kernel raises a
+// device error flag, skips the rest of its work and still frees TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdio.h>
+
 #include "internal.cuh"
 #include "tc.cuh"
 
 namespace aunmf {
 namespace tc {
-int check(int64_t, int64_t, int64_t, int, int, const float *) { return AUNMF_E_UNSUPPORTED; }
-size_t factor_elems(int64_t rows, int k) { return (size_t)rows * k; }
-cudaError_t launch_to_bf16(const float *, int64_t, int64_t, int64_t, uint16_t *, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace {
+
+constexpr int kTileM = 256;          // rows of X per work unit (2 x M=128 MMAs)
+constexpr int kStageBytesK = 128;    // K extent of one stage in bytes (one 128B swizzle row)
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-cudaError_t launch_aht_tc(const float *, const uint16_t *, int64_t, int64_t, int64_t,
-                          const float *, uint16_t *, int, int, float *, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
 }
-cudaError_t launch_wta_tc(const float *, const uint16_t *, int64_t, int64_t, int64_t,
-                          const float *, uint16_t *, int, int, float *, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of parity `parity`; false on expiry (or if
+// another thread already raised the error flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t spins = 1;; ++spins) {
+    if (mbar_try(b, parity)) return true;
+    if ((spins & 1023u) == 0) {
+      if (*(volatile int *)err) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
+      "l"(map), "r"(su32(bar)), "r"(c0), "r"(c1), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Shared-memory matrix descriptor for a K-major tile in the canonical
+// 128-byte-swizzled layout written by TMA (rows of 128 B, 8-row groups of
+// 1024 B): start address >> 4, leading offset 16 B (unused for this layout),
+// stride offset 1024 B between 8-row groups, descriptor version 1, swizzle
+// mode 2 (128 B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor (kind::tf32 / kind::f16): FP32 accumulator, A and
+// B of the same type (TF32 = 2 or BF16 = 1), both K-major, N >> 3 at bit
+// 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc(bool bf16, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct GemmArgs {
+  int64_t M, K;        // rows of X, contraction length (elements)
+  int k;               // valid columns of C
+  int BN;              // MMA N (k rounded up to 16), <= 256
+  int S;               // K splits
+  int nstages;
+  int nbuf;            // TMEM accumulator buffers (1 or 2)
+  uint32_t tmem_cols;  // power of two >= nbuf * 2 * BN
+  float *P;            // partials: S x M x k, row-major
+  int *err;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+              const GemmArgs a) {
+  constexpr int ESZ = BF16 ? 2 : 4;
+  constexpr int BKE = kStageBytesK / ESZ;  // K elements per stage
+  constexpr int KPM = BF16 ? 16 : 8;       // K elements per MMA (32 bytes)
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const uint32_t xbytes = kTileM * kStageBytesK;
+  const uint32_t ybytes = (uint32_t)a.BN * kStageBytesK;
+  const uint32_t sbytes = xbytes + ybytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)a.nstages * sbytes);
+  uint64_t *full = bars;
+  uint64_t *empty = bars + a.nstages;
+  uint64_t *tfull = bars + 2 * a.nstages;
+  uint64_t *tempty = tfull + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles = (a.M + kTileM - 1) / kTileM;
+  const int64_t units = tiles * a.S;
+  const int64_t total_kb = (a.K + BKE - 1) / BKE;
+  const int64_t per_split = (total_kb + a.S - 1) / a.S;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.nstages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapX) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapY) : "memory");
+  }
+  if (warp == 1) tmem_alloc(tslot, a.tmem_cols);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      const uint64_t pol_x = policy_evict_first(), pol_y = policy_evict_last();
+      int st = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int64_t tile = u / a.S, sp = u % a.S;
+        const int64_t kb0 = sp * per_split, kb1 = min(total_kb, kb0 + per_split);
+        const int row0 = (int)(tile * kTileM);
+        for (int64_t kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) { ok = false; break; }
+          uint8_t *xs = smem + (size_t)st * sbytes;
+          mbar_expect_tx(&full[st], sbytes);
+          tma_load_2d(xs, &mapX, &full[st], (int)(kb * BKE), row0, pol_x);
+          tma_load_2d(xs + xbytes, &mapY, &full[st], (int)(kb * BKE), 0, pol_y);
+          if (++st == a.nstages) { st = 0; ph ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t id = idesc(BF16, 128, a.BN);
+      int st = 0, buf = 0;
+      uint32_t ph = 0, tph = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int64_t sp = u % a.S;
+        const int64_t kb0 = sp * per_split, kb1 = min(total_kb, kb0 + per_split);
+        if (!mbar_wait(&tempty[buf], tph ^ 1u, a.err)) break;
+        tc_fence_after();
+        const uint32_t d0 = tbase + (uint32_t)(buf * 2 * a.BN);
+        const uint32_t d1 = d0 + (uint32_t)a.BN;
+        for (int64_t kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(&full[st], ph, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t xs = su32(smem + (size_t)st * sbytes);
+          const uint32_t ys = xs + xbytes;
+#pragma unroll
+          for (int kk = 0; kk < BKE / KPM; ++kk) {
+            const uint32_t off = (uint32_t)(kk * KPM * ESZ);
+            const uint64_t bd = sdesc(ys + off);
+            const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
+            mma<BF16>(d0, sdesc(xs + off), bd, id, acc);
+            mma<BF16>(d1, sdesc(xs + 128 * kStageBytesK + off), bd, id, acc);
+          }
+          mma_commit(&empty[st]);
+          if (++st == a.nstages) { st = 0; ph ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+        if (++buf == a.nbuf) { buf = 0; tph ^= 1u; }
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    int buf = 0;
+    uint32_t tph = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const int64_t tile = u / a.S, sp = u % a.S;
+      if (!mbar_wait(&tfull[buf], tph, a.err)) break;
+      tc_fence_after();
+      float *Pp = a.P + sp * a.M * a.k;
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int64_t row = tile * kTileM + half * 128 + q * 32 + lane;
+        const uint32_t tcol = (uint32_t)(buf * 2 * a.BN + half * a.BN);
+        for (int c0 = 0; c0 < a.BN; c0 += 16) {
+          float v[16];
+          tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c0, v);
+          if (row < a.M) {
+            float *dst = Pp + row * a.k;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < a.k) dst[c0 + j] = v[j];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[buf]);
+      if (++buf == a.nbuf) { buf = 0; tph ^= 1u; }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, a.tmem_cols);
+  }
+}
+
+// P[e] = sum_s parts[s][e], s ascending.
+__global__ void k_sum_splits(const float *__restrict__ parts, int S, int64_t len,
+                             float *__restrict__ P) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = parts[e];
+    for (int p = 1; p < S; ++p) s += parts[(int64_t)p * len + e];
+    P[e] = s;
+  }
+}
+
+// out (cols x ldo) = in (rows x cols, ld ldi)^T, converting to T (float or bf16).
+template <class T>
+__device__ __forceinline__ T cvt(float x);
+template <>
+__device__ __forceinline__ float cvt<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ uint16_t cvt<uint16_t>(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+template <class T>
+__global__ void k_transpose_to(const float *__restrict__ in, int64_t rows, int64_t cols,
+                               int64_t ldi, T *__restrict__ out, int64_t ldo) {
+  __shared__ float t[32][33];
+  const int64_t tr = (rows + 31) / 32, tcn = (cols + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
+    const int64_t r0 = (tile / tcn) * 32, c0 = (tile % tcn) * 32;
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t r = r0 + y, c = c0 + threadIdx.x;
+      if (r < rows && c < cols) t[y][threadIdx.x] = in[r * ldi + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t c = c0 + y, r = r0 + threadIdx.x;
+      if (r < rows && c < cols) out[c * ldo + r] = cvt<T>(t[threadIdx.x][y]);
+    }
+  }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
+                          uint16_t *__restrict__ out, int64_t ldo) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    out[r * ldo + c] = cvt<uint16_t>(in[r * ldi + c]);
+  }
+}
+
+// ------------------------------------------------------------------ host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D tensor map over a row-major rows x cols matrix (leading dimension ld,
+// elements) with a box of box_cols (128 bytes) x box_rows, 128 B swizzle.
+bool make_map(CUtensorMap *map, const void *base, bool bf16, int64_t rows, int64_t cols,
+              int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const int esz = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(kStageBytesK / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+int pad_to(int64_t x, int q) { return (int)((x + q - 1) / q * q); }
+
+}  // namespace
+
+int bn_for(int k) { return pad_to(k, 16); }
+
+// Split count: smallest S in 1..4 whose unit count fills the SMs evenly.
+int splits_for(int64_t M, int64_t K, bool bf16) {
+  const int64_t tiles = (M + kTileM - 1) / kTileM;
+  const int64_t kb = (K + kStageBytesK / (bf16 ? 2 : 4) - 1) / (kStageBytesK / (bf16 ? 2 : 4));
+  const int sms = num_sms();
+  int best = 1;
+  double best_eff = 0;
+  for (int S = 1; S <= 4; ++S) {
+    const int64_t per = (kb + S - 1) / S;
+    if ((S - 1) * per >= kb) continue;  // the last split would be empty
+    const int64_t u = tiles * S;
+    const double waves = (double)u / sms;
+    const double eff = waves / (double)((u + sms - 1) / sms);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = S; }
+  }
+  return best;
+}
+
+int check(int64_t m, int64_t n, int64_t lda, int k, int prec, const float *A) {
+  if (prec != AUNMF_TF32 && prec != AUNMF_BF16) return AUNMF_E_INVAL;
+  if (k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (m > 0x7fffffffLL || n > 0x7fffffffLL) return AUNMF_E_UNSUPPORTED;
+  if (!encode_fn()) return AUNMF_E_UNSUPPORTED;
+  (void)lda;
+  (void)A;
+  return AUNMF_OK;
+}
+
+size_t factor_elems(int64_t rows, int k) { return (size_t)k * pad_to(rows, 8); }
+int64_t copy_ld(int64_t cols) { return pad_to(cols, 8); }
+size_t parts_elems(int64_t M, int k) { return (size_t)4 * M * k; }
+
+cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int64_t ldi, void *out,
+                                int64_t ldo, bool bf16, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+  if (tiles > (int64_t)num_sms() * 64) tiles = (int64_t)num_sms() * 64;
+  if (bf16)
+    k_transpose_to<uint16_t><<<(unsigned)tiles, dim3(32, 8), 0, s>>>(in, rows, cols, ldi,
+                                                                     (uint16_t *)out, ldo);
+  else
+    k_transpose_to<float><<<(unsigned)tiles, dim3(32, 8), 0, s>>>(in, rows, cols, ldi,
+                                                                 (float *)out, ldo);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float *A, int64_t m, int64_t n, int64_t lda, uint16_t *out,
+                           int64_t ldo, cudaStream_t s) {
+  int64_t nb = (m * n + 255) / 256;
+  if (nb > (int64_t)num_sms() * 32) nb = (int64_t)num_sms() * 32;
+  k_to_bf16<<<(unsigned)nb, 256, 0, s>>>(A, m, n, lda, out, ldo);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
+                        int64_t ldy, bool bf16, float *parts, int S, int *err, cudaStream_t s) {
+  const int BN = bn_for(k);
+  if (BN > 256) return cudaErrorInvalidValue;
+  CUtensorMap mx, my;
+  if (!make_map(&mx, X, bf16, M, K, ldx, kTileM)) return cudaErrorInvalidValue;
+  if (!make_map(&my, Y, bf16, k, K, ldy, BN)) return cudaErrorInvalidValue;
+  GemmArgs a;
+  a.M = M;
+  a.K = K;
+  a.k = k;
+  a.BN = BN;
+  a.S = S;
+  a.nbuf = (4 * BN <= 512) ? 2 : 1;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(a.nbuf * 2 * BN)) cols <<= 1;
+  a.tmem_cols = cols;
+  const size_t sbytes = (size_t)(kTileM + BN) * kStageBytesK;
+  const size_t budget = 225 * 1024 - 1024 - 256;
+  a.nstages = (int)(budget / sbytes);
+  if (a.nstages > 8) a.nstages = 8;
+  if (a.nstages < 2) return cudaErrorInvalidValue;
+  a.P = parts;
+  a.err = err;
+  const size_t smem = 1024 + (size_t)a.nstages * sbytes + 256;
+  const int64_t units = ((M + kTileM - 1) / kTileM) * S;
+  const int grid = (int)(units < num_sms() ? units : num_sms());
+  if (bf16) {
+    cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemm_tc<true><<<grid, kThreads, smem, s>>>(mx, my, a);
+  } else {
+    cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemm_tc<false><<<grid, kThreads, smem, s>>>(mx, my, a);
+  }
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s) {
+  int64_t nb = (len + 255) / 256;
+  if (nb > (int64_t)num_sms() * 16) nb = (int64_t)num_sms() * 16;
+  if (nb < 1) nb = 1;
+  k_sum_splits<<<(unsigned)nb, 256, 0, s>>>(parts, S, len, P);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 }  // namespace tc
 }  // namespace aunmf

@@ -1,4 +1,4 @@
-// tc.cuh -- tensor-core (tcgen05) products with A: declarations.
+// tc.cuh -- tensor-core (tcgen05) products with A: host-side launchers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,20 +7,31 @@
 namespace aunmf {
 namespace tc {
 
-// AUNMF_OK if the tensor-core path takes (m, n, lda, k, prec, A), else a status.
+// AUNMF_OK if the tensor-core path takes (m, n, k, prec), else a status.
 int check(int64_t m, int64_t n, int64_t lda, int k, int prec, const float *A);
-// Elements of a BF16 factor copy (rows x k, padded as the kernels need).
+// Leading dimension (elements) of the library's K-major copies: a multiple of 8
+// so that every row starts on a 16-byte boundary for TMA (FP32 and BF16).
+int64_t copy_ld(int64_t cols);
+// Elements of a factor copy rows x k stored as k x copy_ld(rows).
 size_t factor_elems(int64_t rows, int k);
-// BF16 copy of A (m x n, lda) into out (m x n, ld n).
+// Elements of the split-K partial buffer for an M x k product.
+size_t parts_elems(int64_t M, int k);
+// MMA N for rank k, and the number of K splits for an M x K product.
+int bn_for(int k);
+int splits_for(int64_t M, int64_t K, bool bf16);
+
+// out (cols x rows, ld ldo, FP32 or BF16) = in (rows x cols, ld ldi)^T.
+cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int64_t ldi, void *out,
+                                int64_t ldo, bool bf16, cudaStream_t s);
+// out (m x n, ld ldo, BF16) = A (m x n, lda).
 cudaError_t launch_to_bf16(const float *A, int64_t m, int64_t n, int64_t lda, uint16_t *out,
-                           cudaStream_t s);
-// P_W (m x k) = A Ht, P_Ht (n x k) = A^T W on tensor cores.
-cudaError_t launch_aht_tc(const float *A, const uint16_t *Abf, int64_t m, int64_t n, int64_t lda,
-                          const float *Ht, uint16_t *Htbf, int k, int prec, float *P,
-                          cudaStream_t s);
-cudaError_t launch_wta_tc(const float *A, const uint16_t *Abf, int64_t m, int64_t n, int64_t lda,
-                          const float *W, uint16_t *Wbf, int k, int prec, float *P,
-                          cudaStream_t s);
+                           int64_t ldo, cudaStream_t s);
+// parts[s] (M x k) = X (M x K, ldx) * Y (k x K, ldy)^T over the s-th K split,
+// s < S; X, Y FP32 (TF32 MMA) or BF16.  S == 1 writes the product itself.
+cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
+                        int64_t ldy, bool bf16, float *parts, int S, int *err, cudaStream_t s);
+// P = sum over s of parts[s] (len elements each), s ascending.
+cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace aunmf

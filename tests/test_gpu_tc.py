@@ -1,0 +1,126 @@
+"""Tensor-core (tcgen05) products with A against the FP64 oracle, and whole
+mixed-precision runs.
+
+Tolerances (from the arithmetic):
+  * TF32: each operand keeps 10 explicit mantissa bits (relative error below
+    2^-10 whichever way the hardware drops the low bits), so a product term is
+    off by < 2^-9 relative; with FP32 accumulation the test allows
+    (2^-9 + 2 K u) (|X| |Y|^T).
+  * BF16: both operands rounded to nearest with 7 explicit bits (2^-8
+    relative each): (2^-7 + 2 K u) (|X| |Y|^T).
+  * whole runs in mixed precision: relative residual within 1e-3 of the
+    oracle's after 30 iterations from the same start.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1609_09154_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+torch = pytest.importorskip("torch")
+REL = {"tf32": 2.0 ** -9, "bf16": 2.0 ** -7}
+
+
+@pytest.fixture(scope="module")
+def ax():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1609_09154_gb300 import aunmf
+
+    return aunmf.Handle()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def problem(m, n, k, seed):
+    A, _, _ = synth.dense_lowrank(m, n, min(k, 20), seed=seed)
+    W0, H0 = synth.init_factors(m, n, k, seed=seed)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    return r32(A), r32(W0), r32(H0)
+
+
+def check(got, ref, absprod, K, prec):
+    tol = (REL[prec] + 2 * K * U32) * absprod + 1e-30
+    err = np.abs(got - ref)
+    assert (err <= tol).all(), f"max err/tol {np.max(err / tol):.3g} at {np.argwhere(err > tol)[:4]}"
+
+
+# ragged M and K, k across the MMA N steps (16 .. 256), single and double
+# TMEM buffering (N <= 128 vs > 128), one and several units per CTA and K splits
+SHAPES = [(300, 200, 10), (517, 389, 50), (1031, 129, 33), (64, 48, 1), (700, 260, 100),
+          (257, 1000, 129), (600, 520, 256), (40000, 3000, 50), (2100, 70000, 16)]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("m,n,k", SHAPES)
+def test_products_tensor_cores(ax, m, n, k, prec):
+    A, W, H = problem(m, n, k, seed=m + n + k)
+    Ad = dev(A)
+    PW = host(ax.aht(Ad, dev(H), prec=prec))
+    PH = host(ax.wta(Ad, dev(W), prec=prec))
+    check(PW, A @ H.T, np.abs(A) @ np.abs(H).T, n, prec)
+    check(PH, W.T @ A, np.abs(W).T @ np.abs(A), m, prec)
+
+
+def test_products_tensor_cores_padded_lda(ax):
+    """A with a leading dimension that is not a multiple of 4 (copied to
+    16-byte-aligned rows before TMA)."""
+    A, W, H = problem(333, 201, 24, seed=3)
+    big = np.zeros((333, 203))
+    big[:, :201] = A
+    Abig = dev(big)
+    Av = Abig[:, :201]
+    from paper_1609_09154_gb300 import aunmf
+
+    M = aunmf.Matrix(333, 201, Av.data_ptr(), 203, None, None, None, 0)
+    PW = host(ax.aht(M, dev(H), prec="tf32"))
+    check(PW, A @ H.T, np.abs(A) @ np.abs(H).T, 201, "tf32")
+
+
+def test_tensor_core_products_deterministic(ax):
+    A, W, H = problem(40000, 3000, 50, seed=5)
+    Ad, Hd = dev(A), dev(H)
+    p1 = ax.aht(Ad, Hd, prec="tf32")
+    p2 = ax.aht(Ad, Hd, prec="tf32")
+    assert torch.equal(p1, p2)
+
+
+@pytest.fixture(scope="module")
+def config_small():
+    A, _, _ = synth.dense_lowrank(2000, 1500, 10, seed=2024)
+    W0, H0 = synth.init_factors(2000, 1500, 10, seed=2024)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    return r32(A), r32(W0), r32(H0)
+
+
+@pytest.fixture(scope="module")
+def oracle_runs(config_small):
+    A, W0, H0 = config_small
+    return {a: orc.nmf_run(A, 10, a, 30, W0, H0) for a in ("mu", "hals", "abpp")}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("algo", ["mu", "hals", "abpp"])
+def test_mixed_run_within_1e3_of_oracle(ax, config_small, oracle_runs, algo, prec):
+    A, W0, H0 = config_small
+    W, H, rel, info = ax.run(dev(A), 10, algo, 30, dev(W0), dev(H0), prec=prec)
+    ref = oracle_runs[algo]["relres"]
+    assert np.abs(rel[-1] - ref[-1]) <= 1e-3, (rel[-1], ref[-1])
+    assert np.all(np.abs(rel - ref) <= 1e-3)
+    assert (host(W) >= 0).all() and (host(H) >= 0).all()
+
+
+def test_mixed_run_with_and_without_graph_identical(ax, config_small):
+    A, W0, H0 = config_small
+    Ad = dev(A)
+    W1, H1, r1, _ = ax.run(Ad, 10, "hals", 12, dev(W0), dev(H0), prec="tf32", use_graph=True)
+    W2, H2, r2, _ = ax.run(Ad, 10, "hals", 12, dev(W0), dev(H0), prec="tf32", use_graph=False)
+    assert torch.equal(W1, W2) and torch.equal(H1, H2) and np.array_equal(r1, r2)
