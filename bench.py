@@ -287,6 +287,10 @@ def run_ours(args):
                 "peak_note": f"hbm_gbs of {pks} peaks"}
     for kk in kern.values():
         kk["ms_avg"] = round(kk["ms_avg"], 4)
+    steps = max(1, args.steps)
+    phases = {p: round(info[f"ms_{p}"] / steps, 4) for p in ("aht", "wta", "update", "gram", "other")}
+    phases["setup_and_teardown_ms_total"] = round(
+        info["ms_total"] - sum(info[f"ms_{p}"] for p in ("aht", "wta", "update", "gram", "other")), 3)
 
     # end to end through the host-buffer entry point: H2D of A, W0, H0 and the
     # D2H of W, H, relres inside the timed region
@@ -324,7 +328,8 @@ def run_ours(args):
             "data": "synthetic", "config": config_dict(args),
             "tflops": f_it * value / 1e12,
             "relres_last": float(rel[-1]) if len(rel) else None,
-            "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "kernels": kern, "phases_ms_per_step": phases,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(info["launches"]), "clocks": clk,
         }
         print(json.dumps(line))

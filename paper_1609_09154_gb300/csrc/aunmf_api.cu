@@ -38,6 +38,7 @@ struct aunmf_handle {
   // workspace
   Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last;
   Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
+  Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
@@ -111,6 +112,10 @@ struct RunCtx {
   int64_t ldh, ldw;
   float *parts;
   int *err;
+  // sparse path: CSC form of A
+  const int64_t *colptr;
+  const int32_t *rowidx;
+  const float *cval;
   bool profile;
   std::vector<cudaEvent_t> *ev;          // profile events (pairs)
   std::vector<int> *ev_phase;            // phase index per pair
@@ -175,7 +180,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   (void)h;
   if (!A->dense) {
     PhaseTimer t(c, s, kPhWta);
-    return launch_wta_csr(A->rowptr, A->colidx, A->val, A->m, A->n, c.W, c.k, c.PHt, s);
+    return launch_wta_csc(c.colptr, c.rowidx, c.cval, A->n, c.W, c.k, c.PHt, s);
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhWta);
@@ -202,9 +207,11 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
 }
 
 // Workspace and one-off layout copies of A for the tensor-core products:
-// X of A H^T is A itself (TF32, when its rows are 16-byte aligned) or a copy
-// with padded rows / in BF16; X of W^T A is A^T (FP32 or BF16).
+// X of A H^T is A and X of W^T A is A^T, both rounded to nearest TF32 (kept
+// in FP32 containers) or BF16, with 16-byte aligned rows.
 int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s);
+// CSC copy of a sparse A (setup of the W^T A product).
+int prepare_sparse(aunmf_handle *h, RunCtx &c, cudaStream_t s);
 
 cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, int64_t rows,
                    cudaStream_t s) {
@@ -248,7 +255,6 @@ cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
 int check_run_args(const aunmf_matrix *A, int k, int algo, int iters, const float *W0,
                    const float *H0, const float *W, const float *H, const aunmf_options *o) {
   if (!valid_matrix(A)) return AUNMF_E_INVAL;
-  if (!A->dense) return AUNMF_E_UNSUPPORTED;
   if (k < 1 || k > AUNMF_K_MAX || iters < 0) return AUNMF_E_INVAL;
   if (algo < AUNMF_MU || algo > AUNMF_ABPP) return AUNMF_E_INVAL;
   if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
@@ -291,23 +297,30 @@ int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   c.err = P<int>(h->err);
   cudaError_t e = cudaMemsetAsync(c.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(err)");
-  const bool aligned = ((uintptr_t)A->dense % 16 == 0) && (A->lda % 4 == 0);
-  if (!bf && aligned) {
-    c.Ax = A->dense;
-    c.ldx = A->lda;
-  } else {
-    c.ldx = tc::copy_ld(n);
-    ENS_TC(h, h->Ax, esz * (size_t)m * c.ldx);
-    c.Ax = h->Ax.p;
-    if (bf) {
-      e = tc::launch_to_bf16(A->dense, m, n, A->lda, P<uint16_t>(h->Ax), c.ldx, s);
-    } else {
-      e = launch_copy2d(A->dense, A->lda, P<float>(h->Ax), c.ldx, m, n, s);
-    }
-    if (e != cudaSuccess) return fail_cuda(h, e, "copy of A");
-  }
+  // X of A H^T: A rounded to nearest TF32 / BF16 with 16-byte aligned rows
+  c.ldx = tc::copy_ld(n);
+  ENS_TC(h, h->Ax, esz * (size_t)m * c.ldx);
+  c.Ax = h->Ax.p;
+  e = tc::launch_round_copy(A->dense, m, n, A->lda, h->Ax.p, c.ldx, bf, s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "copy of A");
   e = tc::launch_transpose_to(A->dense, m, n, A->lda, h->At.p, c.ldat, bf, s);
   if (e != cudaSuccess) return fail_cuda(h, e, "transpose of A");
+  return AUNMF_OK;
+}
+
+int prepare_sparse(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
+  const aunmf_matrix *A = c.A;
+  ENS_TC(h, h->colptr, sizeof(int64_t) * (size_t)(A->n + 1));
+  ENS_TC(h, h->rowidx, sizeof(int32_t) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+  ENS_TC(h, h->cval, sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+  ENS_TC(h, h->cscratch, csc_scratch_bytes(A->n, A->nnz));
+  cudaError_t e = launch_csr_to_csc(A->rowptr, A->colidx, A->val, A->m, A->n, A->nnz,
+                                    P<int64_t>(h->colptr), P<int32_t>(h->rowidx), P<float>(h->cval),
+                                    h->cscratch.p, s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "csr_to_csc");
+  c.colptr = P<int64_t>(h->colptr);
+  c.rowidx = P<int32_t>(h->rowidx);
+  c.cval = P<float>(h->cval);
   return AUNMF_OK;
 }
 
@@ -359,7 +372,8 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->hA, &h->hW, &h->hH};
+                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->hA, &h->hW,
+                 &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -437,6 +451,10 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   }
   if (o.prec != AUNMF_FP32) {
     int prc = prepare_tc(h, c, s);
+    if (prc != AUNMF_OK) return prc;
+  }
+  if (!A->dense) {
+    int prc = prepare_sparse(h, c, s);
     if (prc != AUNMF_OK) return prc;
   }
   CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
@@ -551,7 +569,7 @@ int aunmf_gram_h(aunmf_handle *h, const float *H, int k, int64_t n, float *G) {
 int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int prec, float *Pout) {
   if (!h || !valid_matrix(A) || !H || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
-  if (!A->dense) return AUNMF_E_UNSUPPORTED;
+  if (!A->dense && prec != AUNMF_FP32) return AUNMF_E_UNSUPPORTED;
   if (prec != AUNMF_FP32) {
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
     if (rc != AUNMF_OK) return rc;
@@ -576,7 +594,7 @@ int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int
 int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int prec, float *Pout) {
   if (!h || !valid_matrix(A) || !W || !Pout || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
-  if (!A->dense) return AUNMF_E_UNSUPPORTED;
+  if (!A->dense && prec != AUNMF_FP32) return AUNMF_E_UNSUPPORTED;
   if (prec != AUNMF_FP32) {
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
     if (rc != AUNMF_OK) return rc;
@@ -591,6 +609,10 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
   c.PHt = P<float>(h->PHt);
   if (prec != AUNMF_FP32) {
     int rc = prepare_tc(h, c, h->stream);
+    if (rc != AUNMF_OK) return rc;
+  }
+  if (!A->dense) {
+    int rc = prepare_sparse(h, c, h->stream);
     if (rc != AUNMF_OK) return rc;
   }
   CK(h, product_wta(h, c, h->stream));
@@ -693,7 +715,11 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
     CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, s));
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, dp, h->n_dparts, P<double>(h->n2a), s));
-    CK(h, launch_wta_csr(A->rowptr, A->colidx, A->val, m, n, W, k, PHt, s));
+    RunCtx c{};
+    c.A = A;
+    int rc = prepare_sparse(h, c, s);
+    if (rc != AUNMF_OK) return rc;
+    CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, W, k, PHt, s));
   }
   CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
   CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s));

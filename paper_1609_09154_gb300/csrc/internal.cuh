@@ -42,12 +42,17 @@ cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, c
 cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
                             int k, float *P, cudaStream_t s);
 
-// Sparse CSR products (FP32).
+// Sparse products (FP32).  P_W (m x k) = A Ht from CSR; P_Ht (n x k) = A^T W
+// from the CSC form (colptr[n+1], rowidx[nnz], cval[nnz]) built by
+// launch_csr_to_csc (scratch: csc_scratch_bytes(n, nnz) bytes).
 cudaError_t launch_aht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
                            int64_t m, const float *Ht, int k, float *P, cudaStream_t s);
-cudaError_t launch_wta_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, int64_t n, const float *W, int k, float *P,
-                           cudaStream_t s);
+cudaError_t launch_wta_csc(const int64_t *colptr, const int32_t *rowidx, const float *cval,
+                           int64_t n, const float *W, int k, float *P, cudaStream_t s);
+size_t csc_scratch_bytes(int64_t n, int64_t nnz);
+cudaError_t launch_csr_to_csc(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                              int64_t m, int64_t n, int64_t nnz, int64_t *colptr, int32_t *rowidx,
+                              float *cval, void *scratch, cudaStream_t s);
 
 // Transpose: out (cols x rows) = in (rows x cols)^T, both row-major, dense ld.
 cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, float *out,

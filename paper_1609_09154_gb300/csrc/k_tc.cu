@@ -334,10 +334,18 @@ __global__ void k_sum_splits(const float *__restrict__ parts, int S, int64_t len
 }
 
 // out (cols x ldo) = in (rows x cols, ld ldi)^T, converting to T (float or bf16).
+// FP32 -> TF32 with round-to-nearest (the tensor core would otherwise drop the
+// low 13 mantissa bits, a bias toward zero that does not average out on
+// nonnegative data); the result is an FP32 bit pattern with those bits zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 template <class T>
 __device__ __forceinline__ T cvt(float x);
 template <>
-__device__ __forceinline__ float cvt<float>(float x) { return x; }
+__device__ __forceinline__ float cvt<float>(float x) { return round_tf32(x); }
 template <>
 __device__ __forceinline__ uint16_t cvt<uint16_t>(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -363,13 +371,14 @@ __global__ void k_transpose_to(const float *__restrict__ in, int64_t rows, int64
   }
 }
 
-__global__ void k_to_bf16(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
-                          uint16_t *__restrict__ out, int64_t ldo) {
-  const int64_t total = rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / cols, c = e % cols;
-    out[r * ldo + c] = cvt<uint16_t>(in[r * ldi + c]);
+// out (rows x cols, ld ldo) = in rounded to T (TF32-valued FP32 or BF16).
+template <class T>
+__global__ void k_round_copy(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
+                             T *__restrict__ out, int64_t ldo) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float *src = in + r * ldi;
+    T *dst = out + r * ldo;
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) dst[c] = cvt<T>(src[c]);
   }
 }
 
@@ -474,11 +483,14 @@ cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_bf16(const float *A, int64_t m, int64_t n, int64_t lda, uint16_t *out,
-                           int64_t ldo, cudaStream_t s) {
-  int64_t nb = (m * n + 255) / 256;
-  if (nb > (int64_t)num_sms() * 32) nb = (int64_t)num_sms() * 32;
-  k_to_bf16<<<(unsigned)nb, 256, 0, s>>>(A, m, n, lda, out, ldo);
+cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda, void *out,
+                              int64_t ldo, bool bf16, cudaStream_t s) {
+  int64_t nb = m < (int64_t)num_sms() * 16 ? m : (int64_t)num_sms() * 16;
+  if (nb < 1) return cudaSuccess;
+  if (bf16)
+    k_round_copy<uint16_t><<<(unsigned)nb, 256, 0, s>>>(A, m, n, lda, (uint16_t *)out, ldo);
+  else
+    k_round_copy<float><<<(unsigned)nb, 256, 0, s>>>(A, m, n, lda, (float *)out, ldo);
   g_launches += 1;
   return cudaGetLastError();
 }

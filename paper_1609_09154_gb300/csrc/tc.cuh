@@ -20,12 +20,14 @@ size_t parts_elems(int64_t M, int k);
 int bn_for(int k);
 int splits_for(int64_t M, int64_t K, bool bf16);
 
-// out (cols x rows, ld ldo, FP32 or BF16) = in (rows x cols, ld ldi)^T.
+// out (cols x rows, ld ldo) = in (rows x cols, ld ldi)^T rounded to nearest
+// TF32 (stored as FP32) or BF16.
 cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int64_t ldi, void *out,
                                 int64_t ldo, bool bf16, cudaStream_t s);
-// out (m x n, ld ldo, BF16) = A (m x n, lda).
-cudaError_t launch_to_bf16(const float *A, int64_t m, int64_t n, int64_t lda, uint16_t *out,
-                           int64_t ldo, cudaStream_t s);
+// out (m x n, ld ldo) = A (m x n, lda) rounded to nearest TF32 (stored as
+// FP32) or BF16.  The transposed copies round the same way.
+cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda, void *out,
+                              int64_t ldo, bool bf16, cudaStream_t s);
 // parts[s] (M x k) = X (M x K, ldx) * Y (k x K, ldy)^T over the s-th K split,
 // s < S; X, Y FP32 (TF32 MMA) or BF16.  S == 1 writes the product itself.
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
