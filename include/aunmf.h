@@ -174,6 +174,31 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
 int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const float *H, int k,
                  double *relres);
 
+/* ---- fixed-memory variant ------------------------------------------------ */
+
+/* G = W^T W (k x k) for W m x k [device in/out], like aunmf_gram_w, for
+ * callers that cannot allocate device memory: code running while another
+ * framework's memory pool owns the device (a cudaMalloc there can fail or
+ * upset the pool's accounting), or code held to a fixed memory budget.  The
+ * paper has no counterpart; this is a service of the library.
+ *   - Allocates nothing and needs no handle: the per-block partial sums live
+ *     in a static device array of 4 MiB (256 partial 64 x 64 FP32 matrices)
+ *     that every GPU loading the library holds until the process exits.
+ *   - k must be in 1..64 (the array's limit); larger k returns
+ *     AUNMF_E_INVAL without launching anything.  m is unlimited.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); the call
+ *     only enqueues work and does not synchronise.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array.  Nothing in it needs to
+ *     start at zero (each call overwrites all it reads), but calls whose GPU
+ *     work overlaps in time -- e.g. on two streams -- race on it: order them
+ *     on one stream or with events.
+ * Returns AUNMF_OK, AUNMF_E_INVAL, AUNMF_E_CUDA or AUNMF_E_UNSUPPORTED (device
+ * ordinal >= 64). */
+int aunmf_gram_w_noalloc(const float *W, int64_t m, int k, float *G, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

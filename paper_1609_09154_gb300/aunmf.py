@@ -81,6 +81,7 @@ SIGNATURES = {
     "aunmf_update_h": [_P, _I, _P, _P, _P, _I, _I64, _D],
     "aunmf_nls_bpp": [_P, _P, _P, _I64, _I, _P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
+    "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
 }
 _RESTYPE = {"aunmf_strerror": ctypes.c_char_p, "aunmf_last_cuda_error": ctypes.c_char_p}
 
