@@ -39,6 +39,7 @@ struct aunmf_handle {
   Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last;
   Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
   Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
+  Buf bppq;                            // BPP: G^{-1} in FP64
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
@@ -100,6 +101,8 @@ struct RunCtx {
   int k, algo, prec;
   float mu_eps;
   int max_piv;
+  int warm;        // BPP starts from the previous iterate's support
+  void *bppq;      // BPP scratch (G^{-1})
   float *W, *Ht, *PW, *PHt, *GH, *GW, *gpart;
   double *dpart, *n2a, *relres_dev, *last;
   DevCounters *ctr;
@@ -156,16 +159,19 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
     return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
+  const bool split = tc::use_split(c.k);
   const int S = tc::splits_for(A->m, A->n, bf);
   cudaError_t e;
   {
     PhaseTimer t(c, s, kPhOther);
-    if ((e = tc::launch_transpose_to(c.Ht, A->n, c.k, c.k, c.Hk, c.ldh, bf, s)) != cudaSuccess) return e;
+    e = split ? tc::launch_split_transpose(c.Ht, A->n, c.k, c.k, c.Hk, c.ldh, bf, s)
+              : tc::launch_transpose_to(c.Ht, A->n, c.k, c.k, c.Hk, c.ldh, bf, s);
+    if (e != cudaSuccess) return e;
   }
   {
     PhaseTimer t(c, s, kPhAht);
-    e = tc::launch_gemm(c.Ax, A->m, A->n, c.ldx, c.Hk, c.k, c.ldh, bf, S == 1 ? c.PW : c.parts, S,
-                        c.err, s);
+    e = tc::launch_gemm(c.Ax, A->m, A->n, c.ldx, c.Hk, c.k, c.ldh, split, bf,
+                        S == 1 ? c.PW : c.parts, S, c.err, s);
     if (e != cudaSuccess) return e;
   }
   if (S > 1) {
@@ -187,16 +193,19 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
     return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
+  const bool split = tc::use_split(c.k);
   const int S = tc::splits_for(A->n, A->m, bf);
   cudaError_t e;
   {
     PhaseTimer t(c, s, kPhOther);
-    if ((e = tc::launch_transpose_to(c.W, A->m, c.k, c.k, c.Wt, c.ldw, bf, s)) != cudaSuccess) return e;
+    e = split ? tc::launch_split_transpose(c.W, A->m, c.k, c.k, c.Wt, c.ldw, bf, s)
+              : tc::launch_transpose_to(c.W, A->m, c.k, c.k, c.Wt, c.ldw, bf, s);
+    if (e != cudaSuccess) return e;
   }
   {
     PhaseTimer t(c, s, kPhWta);
-    e = tc::launch_gemm(c.At, A->n, A->m, c.ldat, c.Wt, c.k, c.ldw, bf, S == 1 ? c.PHt : c.parts,
-                        S, c.err, s);
+    e = tc::launch_gemm(c.At, A->n, A->m, c.ldat, c.Wt, c.k, c.ldw, split, bf,
+                        S == 1 ? c.PHt : c.parts, S, c.err, s);
     if (e != cudaSuccess) return e;
   }
   if (S > 1) {
@@ -218,7 +227,7 @@ cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, int64_t
   switch (c.algo) {
     case AUNMF_MU: return launch_mu(X, Pm, G, rows, c.k, c.mu_eps, s);
     case AUNMF_HALS: return launch_hals(X, Pm, G, rows, c.k, s);
-    default: return launch_bpp(G, Pm, rows, c.k, X, c.max_piv, c.ctr, nullptr, s);
+    default: return launch_bpp(G, Pm, rows, c.k, X, c.max_piv, c.warm, c.ctr, c.bppq, s);
   }
 }
 
@@ -372,8 +381,8 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->hA, &h->hW,
-                 &h->hH};
+                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->hA,
+                 &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -405,9 +414,12 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->relres, sizeof(double) * (iters > 0 ? iters : 1));
   ENS(h, h->last, sizeof(double));
+  ENS(h, h->bppq, bpp_scratch_bytes(k));
 
   RunCtx c{};
   c.A = A;
+  c.warm = 1;
+  c.bppq = h->bppq.p;
   c.k = k;
   c.algo = algo;
   c.prec = o.prec;
@@ -627,12 +639,14 @@ int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const f
   if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
   cudaStream_t s = h->stream;
   ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->bppq, bpp_scratch_bytes(k));
   RunCtx c{};
   c.k = k;
   c.algo = algo;
   c.mu_eps = (float)(eps > 0 ? eps : 1e-16);
   c.max_piv = 10 * k;
   c.ctr = P<DevCounters>(h->ctr);
+  c.bppq = h->bppq.p;
   CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
   CK(h, update(c, W, PW, GH, m, s));
   if (algo == AUNMF_HALS) {
@@ -660,12 +674,14 @@ int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const f
   ENS(h, h->Ht, sizeof(float) * n * k);
   ENS(h, h->PHt, sizeof(float) * n * k);
   ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->bppq, bpp_scratch_bytes(k));
   RunCtx c{};
   c.k = k;
   c.algo = algo;
   c.mu_eps = (float)(eps > 0 ? eps : 1e-16);
   c.max_piv = 10 * k;
   c.ctr = P<DevCounters>(h->ctr);
+  c.bppq = h->bppq.p;
   CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
   CK(h, launch_transpose(H, k, n, P<float>(h->Ht), s));
   CK(h, launch_transpose(PH, k, n, P<float>(h->PHt), s));
@@ -679,9 +695,10 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
   if (!h || !G || !R || !X || nrhs < 0 || k < 1 || k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
   cudaStream_t s = h->stream;
   ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->bppq, bpp_scratch_bytes(k));
   DevCounters *ctr = P<DevCounters>(h->ctr);
   CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
-  CK(h, launch_bpp(G, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, ctr, nullptr, s));
+  CK(h, launch_bpp(G, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, 0, ctr, h->bppq.p, s));
   DevCounters hc{};
   CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));

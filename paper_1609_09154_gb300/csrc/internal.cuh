@@ -67,9 +67,12 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
 // may be null, rows_y rows); GW_ij /= s_i s_j.  Zero norms leave column i as is.
 cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t rows_y, float *GW,
                                   int k, cudaStream_t s);
-// BPP: X(r, :) = argmin_{x>=0} given G, R(r, :) in FP64.
+// BPP: X(r, :) = argmin_{x>=0} ||C x - b|| given G = C^T C and R(r, :) = C^T b,
+// in FP64.  warm != 0 starts each row from the support of X's current row.
+// scratch: bpp_scratch_bytes(k) bytes of device memory (holds G^{-1}).
+size_t bpp_scratch_bytes(int k);
 cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
-                       int max_pivots, DevCounters *ctr, double *Gd, cudaStream_t s);
+                       int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s);
 
 // Reductions for the relative residual.
 // sum of squares of A (dense) or of val (CSR) into *out (device double).

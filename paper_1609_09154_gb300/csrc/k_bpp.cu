@@ -5,15 +5,23 @@
 // W^T A for H) against the shared Gram matrix G:
 //     x = argmin_{x >= 0} ||C x - b||,   G = C^T C,  r = C^T b.
 // Lane l owns the indices j = l and j = l + 32 (k <= 64): its passive flag,
-// x_j, y_j = (G x - r)_j and the tolerance of the active-set test.  Each
-// exchange solves G_FF x_F = r_F through the normal equations by a Cholesky
-// factorisation of the passive block in the warp's slice of shared memory.
+// x_j, y_j = (G x - r)_j and the tolerance of the active-set test.
 //
 // Exchange rule (Kim-He-Park / Judice-Pires): V = {passive j: x_j < 0} U
 // {active j: y_j < -tau_j}, tau_j = 1e-11 (|r_j| + sum_a |G_jF(a) x_F(a)|);
 // if |V| shrank, flip all of V and reset the backup counter to 3; else if
 // the counter is positive, decrement it and flip all of V; else flip only
-// the largest index in V.  Start: passive set empty (x = 0, y = -r).
+// the largest index in V.
+//
+// Each exchange solves the passive-set normal equations G_FF x_F = r_F in
+// FP64 with a Cholesky factorisation of at most k/2 rows:
+//   |F| <= |B|: Cholesky of G_FF itself;
+//   |F| >  |B|: with Q = G^{-1} (FP64, computed once per update),
+//               G_FF^{-1} = Q_FF - Q_FB Q_BB^{-1} Q_BF, so with u = Q_:F r_F,
+//               x_F = u_F - Q_FB w,  Q_BB w = u_B  (Cholesky of Q_BB).
+// The solution of each NLS is unique when G is positive definite (Sec. 4),
+// so the starting passive set changes only the work: the run driver starts
+// each right-hand side from the support of its previous iterate.
 #include <math.h>
 
 #include "internal.cuh"
@@ -22,7 +30,7 @@ namespace aunmf {
 namespace {
 
 constexpr double kBppYTol = 1e-11;
-constexpr int kBppMaxWarps = 8;
+constexpr int kBppWarps = 16;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -31,33 +39,131 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 struct BppLayout {
-  int ldl;         // leading dimension of L (odd, to spread shared-memory banks)
-  size_t g_dbl;    // doubles for G
-  size_t warp_dbl; // doubles per warp: L, z, r, F (ints, packed two per double)
+  int kh;          // largest factorisation: floor(k / 2)
+  int ldl;         // leading dimension of L (odd)
+  size_t g_dbl;    // doubles for G and for Q
+  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints)
 };
 
 __host__ __device__ inline BppLayout bpp_layout(int k) {
   BppLayout l;
-  l.ldl = k | 1;
+  l.kh = k / 2 > 0 ? k / 2 : 1;
+  l.ldl = l.kh | 1;
   l.g_dbl = (size_t)k * k;
-  l.warp_dbl = (size_t)k * l.ldl + 2 * (size_t)k + ((size_t)k + 1) / 2;
+  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k;
   return l;
 }
 
+// In-warp Cholesky of the n x n SPD matrix M(a, b) = Mg[I[a] * k + I[b]]
+// into L (lower, ld ldl).  Returns false (warp-uniform) on a non-positive
+// pivot.
+__device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int *I, int n,
+                                              double *L, int ldl, int lane) {
+  for (int c = 0; c < n; ++c) {
+    double part = 0.0;
+    for (int t = lane; t < c; t += 32) part = fma(L[c * ldl + t], L[c * ldl + t], part);
+    const double d = Mg[I[c] * k + I[c]] - warp_sum_d(part);
+    if (!(d > 0.0)) return false;
+    const double lcc = sqrt(d);
+    for (int a = c + 1 + lane; a < n; a += 32) {
+      double s = Mg[I[a] * k + I[c]];
+      for (int t = 0; t < c; ++t) s = fma(-L[a * ldl + t], L[c * ldl + t], s);
+      L[a * ldl + c] = s / lcc;
+    }
+    if (lane == 0) L[c * ldl + c] = lcc;
+    __syncwarp();
+  }
+  return true;
+}
+
+// v <- (L L^T)^{-1} v for v[0..n) in shared memory.
+__device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n, double *v,
+                                                int lane) {
+  for (int c = 0; c < n; ++c) {
+    const double vc = v[c] / L[c * ldl + c];
+    __syncwarp();
+    for (int a = c + 1 + lane; a < n; a += 32) v[a] = fma(-L[a * ldl + c], vc, v[a]);
+    if (lane == 0) v[c] = vc;
+    __syncwarp();
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    const double vc = v[c] / L[c * ldl + c];
+    __syncwarp();
+    for (int a = lane; a < c; a += 32) v[a] = fma(-L[c * ldl + a], vc, v[a]);
+    if (lane == 0) v[c] = vc;
+    __syncwarp();
+  }
+}
+
+// Q = G^{-1} in FP64 (one block): Cholesky of G in shared memory, then each
+// thread solves G q_j = e_j for its column j.  *ok = 0 if G is not positive
+// definite (the Q-based solves are then not used).
+__global__ void k_gram_inverse(const float *__restrict__ G32, int k, double *__restrict__ Q,
+                               int *__restrict__ ok) {
+  extern __shared__ double sm[];
+  double *L = sm;            // k x k
+  double *tmp = sm + k * k;  // one column of k per thread
+  __shared__ int good;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) L[e] = (double)G32[e];
+  if (threadIdx.x == 0) good = 1;
+  __syncthreads();
+  for (int c = 0; c < k; ++c) {  // right-looking, lower triangle
+    if (threadIdx.x == 0) {
+      const double d = L[c * k + c];
+      if (!(d > 0.0)) good = 0;
+      L[c * k + c] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double lcc = L[c * k + c];
+    for (int a = c + 1 + threadIdx.x; a < k; a += blockDim.x) L[a * k + c] /= lcc;
+    __syncthreads();
+    const int w = k - c - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int a = c + 1 + e / w, b = c + 1 + e % w;
+      if (b <= a) L[a * k + b] -= L[a * k + c] * L[b * k + c];
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double *v = tmp + (size_t)threadIdx.x * k;
+    for (int i = 0; i < k; ++i) v[i] = (i == j) ? 1.0 : 0.0;
+    for (int i = 0; i < k; ++i) {  // L v' = e_j
+      double s = v[i];
+      for (int t = 0; t < i; ++t) s -= L[i * k + t] * v[t];
+      v[i] = s / L[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {  // L^T q = v'
+      double s = v[i];
+      for (int t = i + 1; t < k; ++t) s -= L[t * k + i] * v[t];
+      v[i] = s / L[i * k + i];
+    }
+    for (int i = 0; i < k; ++i) Q[i * k + j] = v[i];
+  }
+  if (threadIdx.x == 0) *ok = good;
+}
+
 template <int KT>
-__global__ void k_bpp(const float *__restrict__ G32, const float *__restrict__ R, int64_t rows,
-                      int k, float *__restrict__ X, int max_piv, DevCounters *ctr) {
+__global__ void __launch_bounds__(32 * kBppWarps, 1)
+    k_bpp(const float *__restrict__ G32, const double *__restrict__ Qg, const int *__restrict__ q_ok,
+          const float *__restrict__ R, int64_t rows, int k, float *__restrict__ X, int warm,
+          int max_piv, DevCounters *ctr) {
   extern __shared__ double sm[];
   const BppLayout lay = bpp_layout(k);
   double *G = sm;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = (double)G32[e];
+  double *Q = sm + lay.g_dbl;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    G[e] = (double)G32[e];
+    Q[e] = Qg[e];
+  }
+  const bool have_q = *q_ok != 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
-  double *L = sm + lay.g_dbl + (size_t)wib * lay.warp_dbl;
-  double *z = L + (size_t)k * lay.ldl;
-  double *rs = z + k;
-  int *F = reinterpret_cast<int *>(rs + k);
+  double *L = sm + 2 * lay.g_dbl + (size_t)wib * lay.warp_dbl;
+  double *v = L + (size_t)lay.kh * lay.ldl;   // small system's right-hand side, then x_F
+  double *rs = v + k;                         // r, by index
+  int *Fl = reinterpret_cast<int *>(rs + k);  // passive indices, ascending
+  int *Bl = Fl + k;                           // active indices, ascending
   const int ldl = lay.ldl;
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -66,20 +172,104 @@ __global__ void k_bpp(const float *__restrict__ G32, const float *__restrict__ R
        row += (int64_t)gridDim.x * nwb) {
     double rr[KT], x[KT], y[KT], tau[KT];
     bool pas[KT];
+    bool any = false;
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
       rr[t] = j < k ? (double)R[row * k + j] : 0.0;
       if (j < k) rs[j] = rr[t];
+      pas[t] = warm && j < k && X[row * k + j] > 0.f;
+      any |= pas[t];
       x[t] = 0.0;
       y[t] = -rr[t];
       tau[t] = kBppYTol * fabs(rr[t]);
-      pas[t] = false;
     }
     __syncwarp();
     int alpha = 3, beta = k + 1, it = 0;
     bool failed_numeric = false, failed_cap = false;
+    bool need_solve = __any_sync(0xffffffffu, any);
     for (;;) {
+      if (need_solve) {
+        // ---- passive / active lists and each lane's positions in them
+        int nf = 0, nb = 0, posf[KT], posb[KT];
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          const unsigned pf = __ballot_sync(0xffffffffu, pas[t] && j < k);
+          const unsigned pb = __ballot_sync(0xffffffffu, !pas[t] && j < k);
+          posf[t] = nf + __popc(pf & lt_mask);
+          posb[t] = nb + __popc(pb & lt_mask);
+          nf += __popc(pf);
+          nb += __popc(pb);
+        }
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) {
+            if (pas[t]) Fl[posf[t]] = j; else Bl[posb[t]] = j;
+          }
+        }
+        __syncwarp();
+        if (nf <= nb || !have_q) {
+          // ---- direct: G_FF x_F = r_F; v[0..nf) ends as x_F in F order
+          if (nf > lay.kh) { failed_numeric = true; break; }
+          if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+          for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
+          __syncwarp();
+          warp_chol_solve(L, ldl, nf, v, lane);
+#pragma unroll
+          for (int t = 0; t < KT; ++t) x[t] = pas[t] ? v[posf[t]] : 0.0;
+        } else {
+          // ---- through Q = G^{-1}: u = Q_:F r_F; Q_BB w = u_B; x_F = u_F - Q_FB w
+          double u[KT];
+#pragma unroll
+          for (int t = 0; t < KT; ++t) {
+            const int j = lane + 32 * t;
+            double s = 0.0;
+            if (j < k)
+              for (int a = 0; a < nf; ++a) s = fma(Q[j * k + Fl[a]], rs[Fl[a]], s);
+            u[t] = s;
+            if (j < k && !pas[t]) v[posb[t]] = s;
+          }
+          __syncwarp();
+          if (!warp_cholesky(Q, k, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
+          warp_chol_solve(L, ldl, nb, v, lane);
+#pragma unroll
+          for (int t = 0; t < KT; ++t) {
+            const int j = lane + 32 * t;
+            double s = u[t];
+            if (j < k && pas[t])
+              for (int b = 0; b < nb; ++b) s = fma(-Q[j * k + Bl[b]], v[b], s);
+            x[t] = (j < k && pas[t]) ? s : 0.0;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int t = 0; t < KT; ++t)
+            if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the y update
+        }
+        __syncwarp();
+        // ---- y = G x - r on the active set
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j >= k) continue;
+          if (pas[t]) {
+            y[t] = 0.0;
+            tau[t] = 0.0;
+          } else {
+            double s = -rr[t], mag = fabs(rr[t]);
+            for (int a = 0; a < nf; ++a) {
+              const double g = G[j * k + Fl[a]] * v[a];
+              s += g;
+              mag += fabs(g);
+            }
+            y[t] = s;
+            tau[t] = kBppYTol * mag;
+          }
+        }
+        __syncwarp();
+      }
+      // ---- infeasible set and exchange
       bool inf[KT];
       unsigned bal[KT];
       int nv = 0;
@@ -107,74 +297,7 @@ __global__ void k_bpp(const float *__restrict__ G32, const float *__restrict__ R
         for (int t = 0; t < KT; ++t)
           if (lane + 32 * t == vmax) pas[t] = !pas[t];
       }
-      // passive list F, ascending, and each lane's position in it
-      int nf = 0, pos[KT];
-#pragma unroll
-      for (int t = 0; t < KT; ++t) {
-        const int j = lane + 32 * t;
-        const unsigned pb = __ballot_sync(0xffffffffu, pas[t] && j < k);
-        pos[t] = nf + __popc(pb & lt_mask);
-        nf += __popc(pb);
-      }
-#pragma unroll
-      for (int t = 0; t < KT; ++t)
-        if (pas[t]) F[pos[t]] = lane + 32 * t;
-      __syncwarp();
-      // Cholesky of G_FF (left-looking, column c; lanes over rows below c)
-      for (int c = 0; c < nf; ++c) {
-        double part = 0.0;
-        for (int t = lane; t < c; t += 32) part = fma(L[c * ldl + t], L[c * ldl + t], part);
-        const double d = G[F[c] * k + F[c]] - warp_sum_d(part);
-        if (!(d > 0.0)) { failed_numeric = true; break; }
-        const double lcc = sqrt(d);
-        for (int a = c + 1 + lane; a < nf; a += 32) {
-          double s = G[F[a] * k + F[c]];
-          for (int t = 0; t < c; ++t) s = fma(-L[a * ldl + t], L[c * ldl + t], s);
-          L[a * ldl + c] = s / lcc;
-        }
-        if (lane == 0) L[c * ldl + c] = lcc;
-        __syncwarp();
-      }
-      if (failed_numeric) break;
-      // z = G_FF^{-1} r_F: forward (L) then backward (L^T), column-oriented
-      for (int a = lane; a < nf; a += 32) z[a] = rs[F[a]];
-      __syncwarp();
-      for (int c = 0; c < nf; ++c) {
-        const double zc = z[c] / L[c * ldl + c];
-        __syncwarp();
-        for (int a = c + 1 + lane; a < nf; a += 32) z[a] = fma(-L[a * ldl + c], zc, z[a]);
-        if (lane == 0) z[c] = zc;
-        __syncwarp();
-      }
-      for (int c = nf - 1; c >= 0; --c) {
-        const double zc = z[c] / L[c * ldl + c];
-        __syncwarp();
-        for (int a = lane; a < c; a += 32) z[a] = fma(-L[c * ldl + a], zc, z[a]);
-        if (lane == 0) z[c] = zc;
-        __syncwarp();
-      }
-      // x on the passive set, y = G x - r on the active set
-#pragma unroll
-      for (int t = 0; t < KT; ++t) {
-        const int j = lane + 32 * t;
-        if (j >= k) continue;
-        if (pas[t]) {
-          x[t] = z[pos[t]];
-          y[t] = 0.0;
-          tau[t] = 0.0;
-        } else {
-          x[t] = 0.0;
-          double s = -rr[t], mag = fabs(rr[t]);
-          for (int a = 0; a < nf; ++a) {
-            const double g = G[j * k + F[a]] * z[a];
-            s += g;
-            mag += fabs(g);
-          }
-          y[t] = s;
-          tau[t] = kBppYTol * mag;
-        }
-      }
-      __syncwarp();
+      need_solve = true;
     }
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
@@ -196,28 +319,48 @@ __global__ void k_bpp(const float *__restrict__ G32, const float *__restrict__ R
   }
 }
 
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
 }  // namespace
 
+size_t bpp_scratch_bytes(int k) { return sizeof(double) * (size_t)k * k + 64; }
+
 cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
-                       int max_pivots, DevCounters *ctr, double * /*unused*/, cudaStream_t s) {
+                       int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
   if (k < 1 || k > AUNMF_BPP_K_MAX) return cudaErrorInvalidValue;
+  double *Q = reinterpret_cast<double *>(scratch);
+  int *q_ok = reinterpret_cast<int *>(Q + (size_t)k * k);
+  const size_t inv_smem = sizeof(double) * ((size_t)k * k + (size_t)k * 64);
+  cudaFuncSetAttribute(k_gram_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
+  k_gram_inverse<<<1, 64, inv_smem, s>>>(G, k, Q, q_ok);
   const BppLayout lay = bpp_layout(k);
   const size_t budget = 200 * 1024;
-  int wpb = (int)((budget / sizeof(double) - lay.g_dbl) / lay.warp_dbl);
-  if (wpb > kBppMaxWarps) wpb = kBppMaxWarps;
+  int wpb = (int)((budget / sizeof(double) - 2 * lay.g_dbl) / lay.warp_dbl);
+  if (wpb > kBppWarps) wpb = kBppWarps;
   if (wpb < 1) wpb = 1;
-  const size_t smem = sizeof(double) * (lay.g_dbl + (size_t)wpb * lay.warp_dbl);
+  const size_t smem = sizeof(double) * (2 * lay.g_dbl + (size_t)wpb * lay.warp_dbl);
   int64_t nb = (rows + wpb - 1) / wpb;
-  if (nb > 152 * 4) nb = 152 * 4;
+  if (nb > (int64_t)sm_count() * 2) nb = (int64_t)sm_count() * 2;
   if (k <= 32) {
     cudaFuncSetAttribute(k_bpp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bpp<1><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, R, rows, k, X, max_pivots, ctr);
+    k_bpp<1><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, Q, q_ok, R, rows, k, X, warm, max_pivots,
+                                                  ctr);
   } else {
     cudaFuncSetAttribute(k_bpp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bpp<2><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, R, rows, k, X, max_pivots, ctr);
+    k_bpp<2><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, Q, q_ok, R, rows, k, X, warm, max_pivots,
+                                                  ctr);
   }
-  g_launches += 1;
+  g_launches += 2;
   return cudaGetLastError();
 }
 

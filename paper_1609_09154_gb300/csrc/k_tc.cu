@@ -180,6 +180,7 @@ struct GemmArgs {
   int nstages;
   int nbuf;            // TMEM accumulator buffers (1 or 2)
   uint32_t tmem_cols;  // power of two >= nbuf * 2 * BN
+  int pair;            // 1: Y holds hi/lo rows (2i, 2i+1) per factor column i; C_i = acc_2i + acc_2i+1
   float *P;            // partials: S x M x k, row-major
   int *err;
 };
@@ -304,9 +305,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c0, v);
           if (row < a.M) {
             float *dst = Pp + row * a.k;
+            if (a.pair) {
+              const int o0 = c0 >> 1;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + j < a.k) dst[c0 + j] = v[j];
+              for (int j = 0; j < 8; ++j)
+                if (o0 + j < a.k) dst[o0 + j] = v[2 * j] + v[2 * j + 1];
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (c0 + j < a.k) dst[c0 + j] = v[j];
+            }
           }
         }
       }
@@ -367,6 +375,44 @@ __global__ void k_transpose_to(const float *__restrict__ in, int64_t rows, int64
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
       const int64_t c = c0 + y, r = r0 + threadIdx.x;
       if (r < rows && c < cols) out[c * ldo + r] = cvt<T>(t[threadIdx.x][y]);
+    }
+  }
+}
+
+// Two-term split of a factor, transposed: for in (rows x k, ld ldi),
+//   out row 2c   = hi_c = round(in(:, c)),
+//   out row 2c+1 = lo_c = round(in(:, c) - hi_c)      (ld ldo),
+// so hi + lo carries the factor to ~2x the bits of one rounded value.
+template <class T>
+__device__ __forceinline__ float widen(T x);
+template <>
+__device__ __forceinline__ float widen<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float widen<uint16_t>(uint16_t x) {
+  return __bfloat162float(__ushort_as_bfloat16(x));
+}
+
+template <class T>
+__global__ void k_split_transpose(const float *__restrict__ in, int64_t rows, int k, int64_t ldi,
+                                  T *__restrict__ out, int64_t ldo) {
+  __shared__ float t[32][33];
+  const int64_t tr = (rows + 31) / 32, tcn = (k + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
+    const int64_t r0 = (tile / tcn) * 32, c0 = (tile % tcn) * 32;
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t r = r0 + y, c = c0 + threadIdx.x;
+      if (r < rows && c < k) t[y][threadIdx.x] = in[r * ldi + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      const int64_t c = c0 + y, r = r0 + threadIdx.x;
+      if (r < rows && c < k) {
+        const float x = t[threadIdx.x][y];
+        const T hi = cvt<T>(x);
+        out[(2 * c) * ldo + r] = hi;
+        out[(2 * c + 1) * ldo + r] = cvt<T>(x - widen<T>(hi));
+      }
     }
   }
 }
@@ -464,7 +510,7 @@ int check(int64_t m, int64_t n, int64_t lda, int k, int prec, const float *A) {
   return AUNMF_OK;
 }
 
-size_t factor_elems(int64_t rows, int k) { return (size_t)k * pad_to(rows, 8); }
+size_t factor_elems(int64_t rows, int k) { return (size_t)2 * k * pad_to(rows, 8); }
 int64_t copy_ld(int64_t cols) { return pad_to(cols, 8); }
 size_t parts_elems(int64_t M, int k) { return (size_t)4 * M * k; }
 
@@ -483,6 +529,23 @@ cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int
   return cudaGetLastError();
 }
 
+bool use_split(int k) { return 2 * k <= 256; }
+
+cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,
+                                   int64_t ldo, bool bf16, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  int64_t tiles = ((rows + 31) / 32) * ((k + 31) / 32);
+  if (tiles > (int64_t)num_sms() * 64) tiles = (int64_t)num_sms() * 64;
+  if (bf16)
+    k_split_transpose<uint16_t><<<(unsigned)tiles, dim3(32, 8), 0, s>>>(in, rows, k, ldi,
+                                                                        (uint16_t *)out, ldo);
+  else
+    k_split_transpose<float><<<(unsigned)tiles, dim3(32, 8), 0, s>>>(in, rows, k, ldi,
+                                                                    (float *)out, ldo);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda, void *out,
                               int64_t ldo, bool bf16, cudaStream_t s) {
   int64_t nb = m < (int64_t)num_sms() * 16 ? m : (int64_t)num_sms() * 16;
@@ -496,18 +559,21 @@ cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda,
 }
 
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
-                        int64_t ldy, bool bf16, float *parts, int S, int *err, cudaStream_t s) {
-  const int BN = bn_for(k);
+                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
+                        cudaStream_t s) {
+  const int ny = split ? 2 * k : k;
+  const int BN = bn_for(ny);
   if (BN > 256) return cudaErrorInvalidValue;
   CUtensorMap mx, my;
   if (!make_map(&mx, X, bf16, M, K, ldx, kTileM)) return cudaErrorInvalidValue;
-  if (!make_map(&my, Y, bf16, k, K, ldy, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&my, Y, bf16, ny, K, ldy, BN)) return cudaErrorInvalidValue;
   GemmArgs a;
   a.M = M;
   a.K = K;
   a.k = k;
   a.BN = BN;
   a.S = S;
+  a.pair = split ? 1 : 0;
   a.nbuf = (4 * BN <= 512) ? 2 : 1;
   uint32_t cols = 32;
   while (cols < (uint32_t)(a.nbuf * 2 * BN)) cols <<= 1;

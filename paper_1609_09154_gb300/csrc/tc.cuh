@@ -12,7 +12,7 @@ int check(int64_t m, int64_t n, int64_t lda, int k, int prec, const float *A);
 // Leading dimension (elements) of the library's K-major copies: a multiple of 8
 // so that every row starts on a 16-byte boundary for TMA (FP32 and BF16).
 int64_t copy_ld(int64_t cols);
-// Elements of a factor copy rows x k stored as k x copy_ld(rows).
+// Elements of a factor copy rows x k stored as (up to) 2k x copy_ld(rows).
 size_t factor_elems(int64_t rows, int k);
 // Elements of the split-K partial buffer for an M x k product.
 size_t parts_elems(int64_t M, int k);
@@ -28,10 +28,20 @@ cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int
 // FP32) or BF16.  The transposed copies round the same way.
 cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda, void *out,
                               int64_t ldo, bool bf16, cudaStream_t s);
-// parts[s] (M x k) = X (M x K, ldx) * Y (k x K, ldy)^T over the s-th K split,
-// s < S; X, Y FP32 (TF32 MMA) or BF16.  S == 1 writes the product itself.
+// parts[s] (M x k) = X (M x K, ldx) * F (k x K)^T over the s-th K split, s < S;
+// X, Y FP32 (TF32 MMA) or BF16.  split == false: Y = F (k x K, ldy);
+// split == true: Y holds 2k rows, hi/lo of F's row i at rows 2i, 2i+1
+// (launch_split_transpose), and the kernel adds each pair.  S == 1 writes the
+// product itself.
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
-                        int64_t ldy, bool bf16, float *parts, int S, int *err, cudaStream_t s);
+                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
+                        cudaStream_t s);
+// Whether the two-term factor split fits the MMA (2k <= 256).
+bool use_split(int k);
+// Y (2k x rows, ld ldo) = [hi; lo] rows of in (rows x k, ld ldi)^T, rounded to
+// nearest TF32 (FP32 containers) or BF16: hi = round(x), lo = round(x - hi).
+cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,
+                                   int64_t ldo, bool bf16, cudaStream_t s);
 // P = sum over s of parts[s] (len elements each), s ascending.
 cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s);
 
