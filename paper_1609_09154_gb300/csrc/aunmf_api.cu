@@ -414,7 +414,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->relres, sizeof(double) * (iters > 0 ? iters : 1));
   ENS(h, h->last, sizeof(double));
-  ENS(h, h->bppq, bpp_scratch_bytes(k));
+  ENS(h, h->bppq, bpp_scratch_bytes(k, m > n ? m : n));
 
   RunCtx c{};
   c.A = A;
@@ -639,7 +639,7 @@ int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const f
   if (algo == AUNMF_ABPP && k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
   cudaStream_t s = h->stream;
   ENS(h, h->ctr, sizeof(DevCounters));
-  ENS(h, h->bppq, bpp_scratch_bytes(k));
+  ENS(h, h->bppq, bpp_scratch_bytes(k, m));
   RunCtx c{};
   c.k = k;
   c.algo = algo;
@@ -674,7 +674,7 @@ int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const f
   ENS(h, h->Ht, sizeof(float) * n * k);
   ENS(h, h->PHt, sizeof(float) * n * k);
   ENS(h, h->ctr, sizeof(DevCounters));
-  ENS(h, h->bppq, bpp_scratch_bytes(k));
+  ENS(h, h->bppq, bpp_scratch_bytes(k, n));
   RunCtx c{};
   c.k = k;
   c.algo = algo;
@@ -695,7 +695,7 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
   if (!h || !G || !R || !X || nrhs < 0 || k < 1 || k > AUNMF_BPP_K_MAX) return AUNMF_E_INVAL;
   cudaStream_t s = h->stream;
   ENS(h, h->ctr, sizeof(DevCounters));
-  ENS(h, h->bppq, bpp_scratch_bytes(k));
+  ENS(h, h->bppq, bpp_scratch_bytes(k, nrhs));
   DevCounters *ctr = P<DevCounters>(h->ctr);
   CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
   CK(h, launch_bpp(G, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, 0, ctr, h->bppq.p, s));

@@ -69,8 +69,9 @@ cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t ro
                                   int k, cudaStream_t s);
 // BPP: X(r, :) = argmin_{x>=0} ||C x - b|| given G = C^T C and R(r, :) = C^T b,
 // in FP64.  warm != 0 starts each row from the support of X's current row.
-// scratch: bpp_scratch_bytes(k) bytes of device memory (holds G^{-1}).
-size_t bpp_scratch_bytes(int k);
+// scratch: bpp_scratch_bytes(k, rows) bytes of device memory (G^{-1} and a
+// per-row flag for the direct fallback).
+size_t bpp_scratch_bytes(int k, int64_t rows);
 cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
                        int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s);
 

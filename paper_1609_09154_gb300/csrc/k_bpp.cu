@@ -21,7 +21,9 @@
 //               x_F = u_F - Q_FB w,  Q_BB w = u_B  (Cholesky of Q_BB).
 // The solution of each NLS is unique when G is positive definite (Sec. 4),
 // so the starting passive set changes only the work: the run driver starts
-// each right-hand side from the support of its previous iterate.
+// each right-hand side from the support of its previous iterate.  Rows whose
+// fast solve is not trustworthy (see k_bpp_direct) are redone from a cold
+// start with full-size Cholesky factorisations of G_FF.
 #include <math.h>
 
 #include "internal.cuh"
@@ -30,6 +32,10 @@ namespace aunmf {
 namespace {
 
 constexpr double kBppYTol = 1e-11;
+// passive residual accepted after a solve through Q = G^{-1}: |(G x - r)_j| <=
+// kQResTol (|r_j| + sum |G_jF x_F|); FP64 solves of well-conditioned systems
+// land near 1e-15, so this only rejects solves that lost most of their digits
+constexpr double kQResTol = 1e-9;
 constexpr int kBppWarps = 16;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -146,7 +152,7 @@ template <int KT>
 __global__ void __launch_bounds__(32 * kBppWarps, 1)
     k_bpp(const float *__restrict__ G32, const double *__restrict__ Qg, const int *__restrict__ q_ok,
           const float *__restrict__ R, int64_t rows, int k, float *__restrict__ X, int warm,
-          int max_piv, DevCounters *ctr) {
+          int max_piv, DevCounters *ctr, uint8_t *__restrict__ redo) {
   extern __shared__ double sm[];
   const BppLayout lay = bpp_layout(k);
   double *G = sm;
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
   const int ldl = lay.ldl;
   const unsigned lt_mask = (1u << lane) - 1u;
 
-  long long piv_total = 0, nonconv = 0, numeric = 0;
+  long long piv_total = 0, nonconv = 0;
   for (int64_t row = (int64_t)blockIdx.x * nwb + wib; row < rows;
        row += (int64_t)gridDim.x * nwb) {
     double rr[KT], x[KT], y[KT], tau[KT];
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
     }
     __syncwarp();
     int alpha = 3, beta = k + 1, it = 0;
-    bool failed_numeric = false, failed_cap = false;
+    bool failed_numeric = false, failed_cap = false, used_q = false;
     bool need_solve = __any_sync(0xffffffffu, any);
     for (;;) {
       if (need_solve) {
@@ -214,6 +220,7 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
           // ---- direct: G_FF x_F = r_F; v[0..nf) ends as x_F in F order
           if (nf > lay.kh) { failed_numeric = true; break; }
           if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+          used_q = false;
           for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
           __syncwarp();
           warp_chol_solve(L, ldl, nf, v, lane);
@@ -233,6 +240,7 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
           }
           __syncwarp();
           if (!warp_cholesky(Q, k, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
+          used_q = true;
           warp_chol_solve(L, ldl, nb, v, lane);
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
@@ -248,12 +256,15 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
             if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the y update
         }
         __syncwarp();
-        // ---- y = G x - r on the active set
+        // ---- y = G x - r on the active set; after a solve through Q, also
+        // the passive rows, which must vanish (else the row is re-solved by
+        // the direct fallback)
+        bool bad_res = false;
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int j = lane + 32 * t;
           if (j >= k) continue;
-          if (pas[t]) {
+          if (pas[t] && !used_q) {
             y[t] = 0.0;
             tau[t] = 0.0;
           } else {
@@ -263,10 +274,17 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
               s += g;
               mag += fabs(g);
             }
-            y[t] = s;
-            tau[t] = kBppYTol * mag;
+            if (pas[t]) {
+              bad_res |= !(fabs(s) <= kQResTol * mag);
+              y[t] = 0.0;
+              tau[t] = 0.0;
+            } else {
+              y[t] = s;
+              tau[t] = kBppYTol * mag;
+            }
           }
         }
+        if (__any_sync(0xffffffffu, bad_res)) { failed_numeric = true; break; }
         __syncwarp();
       }
       // ---- infeasible set and exchange
@@ -304,6 +322,133 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
       const int j = lane + 32 * t;
       if (j < k) X[row * k + j] = (float)x[t];
     }
+    if (lane == 0) redo[row] = failed_numeric ? 1 : 0;
+    if (!failed_numeric) {
+      piv_total += it;
+      nonconv += failed_cap;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (piv_total) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_pivots),
+                             (unsigned long long)piv_total);
+    if (nonconv) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_nonconv),
+                           (unsigned long long)nonconv);
+  }
+}
+
+// Fallback for the rows the fast kernel flagged (a non-positive pivot in a
+// k/2-sized factorisation, a passive set too large for it while G itself is
+// not numerically positive definite, or a solve through Q whose passive
+// residual did not vanish): the same exchange rule from a cold start, every
+// passive system solved by a Cholesky factorisation of G_FF of any size.
+template <int KT>
+__global__ void __launch_bounds__(256)
+    k_bpp_direct(const float *__restrict__ G32, const float *__restrict__ R, int64_t rows, int k,
+                 float *__restrict__ X, int max_piv, DevCounters *ctr,
+                 const uint8_t *__restrict__ redo) {
+  extern __shared__ double sm[];
+  const int ldl = k | 1;
+  double *G = sm;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = (double)G32[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nwb = blockDim.x >> 5;
+  double *L = sm + (size_t)k * k + (size_t)wib * ((size_t)k * ldl + 3 * (size_t)k);
+  double *v = L + (size_t)k * ldl;
+  double *rs = v + k;
+  int *Fl = reinterpret_cast<int *>(rs + k);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  long long piv_total = 0, nonconv = 0, numeric = 0;
+  for (int64_t row = (int64_t)blockIdx.x * nwb + wib; row < rows;
+       row += (int64_t)gridDim.x * nwb) {
+    if (!redo[row]) continue;
+    double rr[KT], x[KT], y[KT], tau[KT];
+    bool pas[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      rr[t] = j < k ? (double)R[row * k + j] : 0.0;
+      if (j < k) rs[j] = rr[t];
+      pas[t] = false;
+      x[t] = 0.0;
+      y[t] = -rr[t];
+      tau[t] = kBppYTol * fabs(rr[t]);
+    }
+    __syncwarp();
+    int alpha = 3, beta = k + 1, it = 0;
+    bool failed_numeric = false, failed_cap = false;
+    for (;;) {
+      bool inf[KT];
+      unsigned bal[KT];
+      int nv = 0;
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (y[t] < -tau[t]));
+        bal[t] = __ballot_sync(0xffffffffu, inf[t]);
+        nv += __popc(bal[t]);
+      }
+      if (nv == 0) break;
+      if (it >= max_piv) { failed_cap = true; break; }
+      ++it;
+      if (nv < beta || alpha >= 1) {
+        if (nv < beta) { beta = nv; alpha = 3; } else { alpha -= 1; }
+#pragma unroll
+        for (int t = 0; t < KT; ++t)
+          if (inf[t]) pas[t] = !pas[t];
+      } else {
+        int vmax = -1;
+#pragma unroll
+        for (int t = KT - 1; t >= 0; --t)
+          if (vmax < 0 && bal[t]) vmax = 32 * t + 31 - __clz(bal[t]);
+#pragma unroll
+        for (int t = 0; t < KT; ++t)
+          if (lane + 32 * t == vmax) pas[t] = !pas[t];
+      }
+      int nf = 0, pos[KT];
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        const unsigned pb = __ballot_sync(0xffffffffu, pas[t] && j < k);
+        pos[t] = nf + __popc(pb & lt_mask);
+        nf += __popc(pb);
+      }
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (pas[t]) Fl[pos[t]] = lane + 32 * t;
+      __syncwarp();
+      if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+      for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
+      __syncwarp();
+      warp_chol_solve(L, ldl, nf, v, lane);
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        if (j >= k) continue;
+        if (pas[t]) {
+          x[t] = v[pos[t]];
+          y[t] = 0.0;
+          tau[t] = 0.0;
+        } else {
+          x[t] = 0.0;
+          double s = -rr[t], mag = fabs(rr[t]);
+          for (int a = 0; a < nf; ++a) {
+            const double g = G[j * k + Fl[a]] * v[a];
+            s += g;
+            mag += fabs(g);
+          }
+          y[t] = s;
+          tau[t] = kBppYTol * mag;
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) X[row * k + j] = (float)x[t];
+    }
     piv_total += it;
     nonconv += failed_cap;
     numeric += failed_numeric;
@@ -332,7 +477,9 @@ int sm_count() {
 
 }  // namespace
 
-size_t bpp_scratch_bytes(int k) { return sizeof(double) * (size_t)k * k + 64; }
+size_t bpp_scratch_bytes(int k, int64_t rows) {
+  return sizeof(double) * (size_t)k * k + 256 + (size_t)rows;
+}
 
 cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
                        int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s) {
@@ -340,6 +487,7 @@ cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, floa
   if (k < 1 || k > AUNMF_BPP_K_MAX) return cudaErrorInvalidValue;
   double *Q = reinterpret_cast<double *>(scratch);
   int *q_ok = reinterpret_cast<int *>(Q + (size_t)k * k);
+  uint8_t *redo = reinterpret_cast<uint8_t *>(scratch) + sizeof(double) * (size_t)k * k + 256;
   const size_t inv_smem = sizeof(double) * ((size_t)k * k + (size_t)k * 64);
   cudaFuncSetAttribute(k_gram_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
   k_gram_inverse<<<1, 64, inv_smem, s>>>(G, k, Q, q_ok);
@@ -351,16 +499,32 @@ cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, floa
   const size_t smem = sizeof(double) * (2 * lay.g_dbl + (size_t)wpb * lay.warp_dbl);
   int64_t nb = (rows + wpb - 1) / wpb;
   if (nb > (int64_t)sm_count() * 2) nb = (int64_t)sm_count() * 2;
+  // fallback: a full-size factor per warp, as many warps (<= 8) as fit
+  const size_t fb_warp = (size_t)k * (k | 1) + 3 * (size_t)k;
+  int fbw = (int)((budget / sizeof(double) - (size_t)k * k) / fb_warp);
+  if (fbw > 8) fbw = 8;
+  if (fbw < 1) fbw = 1;
+  const size_t fb_smem = sizeof(double) * ((size_t)k * k + (size_t)fbw * fb_warp);
+  int64_t nbf = (rows + fbw - 1) / fbw;
+  if (nbf > (int64_t)sm_count()) nbf = sm_count();
   if (k <= 32) {
     cudaFuncSetAttribute(k_bpp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bpp<1><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, Q, q_ok, R, rows, k, X, warm, max_pivots,
-                                                  ctr);
+                                                  ctr, redo);
+    cudaFuncSetAttribute(k_bpp_direct<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fb_smem);
+    k_bpp_direct<1><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, max_pivots, ctr,
+                                                             redo);
   } else {
     cudaFuncSetAttribute(k_bpp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bpp<2><<<(unsigned)nb, 32 * wpb, smem, s>>>(G, Q, q_ok, R, rows, k, X, warm, max_pivots,
-                                                  ctr);
+                                                  ctr, redo);
+    cudaFuncSetAttribute(k_bpp_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fb_smem);
+    k_bpp_direct<2><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, max_pivots, ctr,
+                                                             redo);
   }
-  g_launches += 2;
+  g_launches += 3;
   return cudaGetLastError();
 }
 
