@@ -217,9 +217,10 @@ def run_reference(args):
 
 
 def config_dict(args):
-    return {"workload": f"dense {M_FULL}x{N_FULL} FP32, planted rank {RANK_FULL} + |N(0,0.01^2)|, "
+    m, n = getattr(args, "m", M_FULL), getattr(args, "n", N_FULL)
+    return {"workload": f"dense {m}x{n} FP32, planted rank {RANK_FULL} + |N(0,0.01^2)|, "
                         f"k={args.k}, {args.algo.upper()}, products in {args.prec.upper()}",
-            "m": M_FULL, "n": N_FULL, "k": args.k, "algo": args.algo, "prec": args.prec,
+            "m": m, "n": n, "k": args.k, "algo": args.algo, "prec": args.prec,
             "l2": "inputs larger than L2 (A is 24.6 GB), no flush needed",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -234,7 +235,7 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    m, n, k = M_FULL, N_FULL, args.k
+    m, n, k = args.m, args.n, args.k
     A, _, _ = synth.dense_lowrank_torch(m, n, RANK_FULL, seed=SEED + rank, device=dev)
     W0, H0 = synth.init_factors_torch(m, n, k, seed=SEED + rank, device=dev)
     torch.cuda.synchronize()
@@ -315,7 +316,7 @@ def run_ours(args):
                "note": f"one aunmf_run_host call of {args.steps} iterations; copies of "
                        f"the whole input/output amortised over its steps"}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and (m, n) == (M_FULL, N_FULL):
         cpu = cpu_baseline(args.algo, k)
 
     if rank == 0:
@@ -349,6 +350,8 @@ def main():
     ap.add_argument("--algo", default="hals", choices=["mu", "hals", "abpp"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--k", type=int, default=K_FULL)
+    ap.add_argument("--m", type=int, default=M_FULL, help="rows of A (profiling cases)")
+    ap.add_argument("--n", type=int, default=N_FULL, help="columns of A (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -60,6 +60,12 @@ int fail_cuda(aunmf_handle *h, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return fail_cuda(h, e_, #call); \
   } while (0)
 
+// FP64 partial sums: residual partials, and the layout pass's per-block partials
+size_t dpart_bytes(const aunmf_handle *h) {
+  const size_t a = (size_t)h->n_dparts + 8, b = (size_t)tc::prepare_blocks();
+  return sizeof(double) * (a > b ? a : b);
+}
+
 int ensure(aunmf_handle *h, Buf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return AUNMF_OK;
@@ -306,14 +312,18 @@ int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   c.err = P<int>(h->err);
   cudaError_t e = cudaMemsetAsync(c.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return fail_cuda(h, e, "cudaMemsetAsync(err)");
-  // X of A H^T: A rounded to nearest TF32 / BF16 with 16-byte aligned rows
+  // X of A H^T: A rounded to nearest TF32 / BF16 with 16-byte aligned rows;
+  // X of W^T A: the same, transposed; and ||A||^2, all in one pass over A
   c.ldx = tc::copy_ld(n);
   ENS_TC(h, h->Ax, esz * (size_t)m * c.ldx);
+  ENS_TC(h, h->dpart, dpart_bytes(h));
+  ENS_TC(h, h->n2a, sizeof(double));
   c.Ax = h->Ax.p;
-  e = tc::launch_round_copy(A->dense, m, n, A->lda, h->Ax.p, c.ldx, bf, s);
-  if (e != cudaSuccess) return fail_cuda(h, e, "copy of A");
-  e = tc::launch_transpose_to(A->dense, m, n, A->lda, h->At.p, c.ldat, bf, s);
-  if (e != cudaSuccess) return fail_cuda(h, e, "transpose of A");
+  c.dpart = P<double>(h->dpart);
+  if (!c.n2a) c.n2a = P<double>(h->n2a);
+  e = tc::launch_prepare(A->dense, m, n, A->lda, h->Ax.p, c.ldx, h->At.p, c.ldat, bf, c.dpart,
+                         c.n2a, s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "layout copies of A");
   return AUNMF_OK;
 }
 
@@ -409,7 +419,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   ENS(h, h->GH, sizeof(float) * k * k);
   ENS(h, h->GW, sizeof(float) * k * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
-  ENS(h, h->dpart, sizeof(double) * (h->n_dparts + 8));
+  ENS(h, h->dpart, dpart_bytes(h));
   ENS(h, h->n2a, sizeof(double));
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->relres, sizeof(double) * (iters > 0 ? iters : 1));
@@ -456,7 +466,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     CK(h, cudaMemsetAsync(W, 0, sizeof(float) * m * k, s));
   }
   CK(h, launch_transpose(H0, k, n, c.Ht, s));
-  if (A->dense) {
+  if (A->dense && o.prec != AUNMF_FP32) {
+    // ||A||^2 comes out of the layout pass (prepare_tc below)
+  } else if (A->dense) {
     CK(h, launch_norm2(A->dense, m, n, A->lda, c.dpart, h->n_dparts, c.n2a, s));
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
@@ -719,7 +731,7 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   ENS(h, h->GH, sizeof(float) * k * k);
   ENS(h, h->GW, sizeof(float) * k * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
-  ENS(h, h->dpart, sizeof(double) * (h->n_dparts + 8));
+  ENS(h, h->dpart, dpart_bytes(h));
   ENS(h, h->n2a, sizeof(double));
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->last, sizeof(double));

@@ -70,14 +70,27 @@ __global__ void __launch_bounds__(kGramThreads)
   }
 }
 
-// G_ij = sum_b partials[b]_ij, in FP64, b ascending.
-__global__ void k_gram_reduce(const float *__restrict__ partials, int nb, int k,
-                              float *__restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += (double)partials[(int64_t)b * k * k + e];
-  G[e] = (float)s;
+// G_e = sum_b partials[b]_e in FP64: 32 entries per block; warp w sums the
+// w-th eighth of the blocks (b ascending), and the eight sums are added in
+// warp order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256)
+    k_gram_reduce(const float *__restrict__ partials, int nb, int k, float *__restrict__ G) {
+  __shared__ double sw[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kk = k * k;
+  const int e = blockIdx.x * 32 + lane;
+  const int per = (nb + 7) / 8;
+  const int b0 = w * per, b1 = min(nb, b0 + per);
+  double acc = 0.0;
+  if (e < kk)
+    for (int b = b0; b < b1; ++b) acc += (double)partials[(int64_t)b * kk + e];
+  sw[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && e < kk) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += sw[i][lane];
+    G[e] = (float)t;
+  }
 }
 }  // namespace
 
@@ -95,7 +108,7 @@ cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float 
   const int kp = (k + 3) & ~3;
   const size_t smem = sizeof(float) * kGramRows * kp;
   k_gram_partial<<<nb, kGramThreads, smem, s>>>(X, rows, k, ldx, chunk, partials);
-  k_gram_reduce<<<(k * k + 255) / 256, 256, 0, s>>>(partials, nb, k, G);
+  k_gram_reduce<<<(k * k + 31) / 32, 256, 0, s>>>(partials, nb, k, G);
   g_launches += 2;
   return cudaGetLastError();
 }
@@ -338,13 +351,15 @@ __device__ double block_sum_d(double v) {
 // partials[b] = sum of squares over rows r = b, b + nb, ... of A (m x n, lda)
 __global__ void k_norm2_partial(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                                 double *__restrict__ partials) {
+  // squares of one row are summed in FP32 by each thread (<= n/256 terms),
+  // then added in FP64: FP64 adds at every element would bound the pass by
+  // the FP64 rate instead of HBM
   double s = 0.0;
   for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
     const float *row = A + r * lda;
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-      const double v = (double)row[c];
-      s = fma(v, v, s);
-    }
+    float sr = 0.f;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) sr = fmaf(row[c], row[c], sr);
+    s += (double)sr;
   }
   s = block_sum_d(s);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;

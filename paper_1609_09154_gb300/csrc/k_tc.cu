@@ -417,6 +417,63 @@ __global__ void k_split_transpose(const float *__restrict__ in, int64_t rows, in
   }
 }
 
+// One pass over A (m x n, lda) for the tensor-core runs: writes the rounded
+// copy X (m x n, ld ldx), the rounded transposed copy Xt (n x m, ld ldxt) and
+// per-block partial sums of a_ij^2 (FP64; each thread adds its squares of
+// one 64 x 64 tile in FP32 first).  Tiles of 64 x 64 go through shared
+// memory so both writes are row-contiguous.
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_prepare(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, T *__restrict__ X,
+              int64_t ldx, T *__restrict__ Xt, int64_t ldxt, double *__restrict__ part) {
+  __shared__ float t[64][65];
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+  const int64_t tr = (m + 63) / 64, tcn = (n + 63) / 64;
+  double acc = 0.0;
+  for (int64_t tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
+    const int64_t r0 = (tile / tcn) * 64, c0 = (tile % tcn) * 64;
+    float sq = 0.f;
+    __syncthreads();
+#pragma unroll 4
+    for (int y = ty; y < 64; y += 4) {
+      const int64_t r = r0 + y, c = c0 + tx;
+      float v = 0.f;
+      if (r < m && c < n) {
+        v = A[r * lda + c];
+        X[r * ldx + c] = cvt<T>(v);
+      }
+      sq = fmaf(v, v, sq);
+      t[y][tx] = v;
+    }
+    acc += (double)sq;
+    __syncthreads();
+#pragma unroll 4
+    for (int y = ty; y < 64; y += 4) {
+      const int64_t c = c0 + y, r = r0 + tx;
+      if (r < m && c < n) Xt[c * ldxt + r] = cvt<T>(t[tx][y]);
+    }
+  }
+  // block sum in a fixed order
+  __shared__ double ws[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += ws[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_partials_d(const double *__restrict__ part, int np, double *__restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += part[i];
+    *out = s;
+  }
+}
+
 // out (rows x cols, ld ldo) = in rounded to T (TF32-valued FP32 or BF16).
 template <class T>
 __global__ void k_round_copy(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
@@ -530,6 +587,22 @@ cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int
 }
 
 bool use_split(int k) { return 2 * k <= 256; }
+
+int prepare_blocks() { return num_sms() * 8; }
+
+cudaError_t launch_prepare(const float *A, int64_t m, int64_t n, int64_t lda, void *X, int64_t ldx,
+                           void *Xt, int64_t ldxt, bool bf16, double *part, double *norm2,
+                           cudaStream_t s) {
+  const int nb = prepare_blocks();
+  if (bf16)
+    k_prepare<uint16_t><<<nb, 256, 0, s>>>(A, m, n, lda, (uint16_t *)X, ldx, (uint16_t *)Xt, ldxt,
+                                          part);
+  else
+    k_prepare<float><<<nb, 256, 0, s>>>(A, m, n, lda, (float *)X, ldx, (float *)Xt, ldxt, part);
+  k_sum_partials_d<<<1, 32, 0, s>>>(part, nb, norm2);
+  g_launches += 2;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,
                                    int64_t ldo, bool bf16, cudaStream_t s) {
