@@ -8,7 +8,8 @@
 // x_j, y_j = (G x - r)_j and the tolerance of the active-set test.
 //
 // Exchange rule (Kim-He-Park / Judice-Pires): V = {passive j: x_j < 0} U
-// {active j: y_j < -tau_j}, tau_j = 1e-11 (|r_j| + sum_a |G_jF(a) x_F(a)|);
+// {active j: y_j < -tau_j}, tau_j = 1e-11 (|r_j| + sum_a |G_jF(a) x_F(a)|)
+// (y_j in FP64, the scale tau_j in FP32 in the fast kernel);
 // if |V| shrank, flip all of V and reset the backup counter to 3; else if
 // the counter is positive, decrement it and flip all of V; else flip only
 // the largest index in V.
@@ -32,10 +33,9 @@ namespace aunmf {
 namespace {
 
 constexpr double kBppYTol = 1e-11;
-// passive residual accepted after a solve through Q = G^{-1}: |(G x - r)_j| <=
-// kQResTol (|r_j| + sum |G_jF x_F|); FP64 solves of well-conditioned systems
-// land near 1e-15, so this only rejects solves that lost most of their digits
-constexpr double kQResTol = 1e-9;
+// G^{-1} is used for the passive-set solves only when cond_1(G) is below
+// this (FP64 solves through it then keep at least ~8 digits)
+constexpr double kQMaxCond = 1e8;
 constexpr int kBppWarps = 16;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -47,8 +47,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 struct BppLayout {
   int kh;          // largest factorisation: floor(k / 2)
   int ldl;         // leading dimension of L (odd)
-  size_t g_dbl;    // doubles for G and for Q
-  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints)
+  size_t g_dbl;    // doubles for G and for Q (each)
+  size_t gf_dbl;   // doubles holding |G| in FP32 (tolerance scales)
+  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k)
 };
 
 __host__ __device__ inline BppLayout bpp_layout(int k) {
@@ -56,7 +57,8 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
   l.kh = k / 2 > 0 ? k / 2 : 1;
   l.ldl = l.kh | 1;
   l.g_dbl = (size_t)k * k;
-  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k;
+  l.gf_dbl = ((size_t)k * k + 1) / 2;
+  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + ((size_t)k + 1) / 2;
   return l;
 }
 
@@ -103,7 +105,7 @@ __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n,
 
 // Q = G^{-1} in FP64 (one block): Cholesky of G in shared memory, then each
 // thread solves G q_j = e_j for its column j.  *ok = 0 if G is not positive
-// definite (the Q-based solves are then not used).
+// definite or cond_1(G) >= kQMaxCond (the Q-based solves are then not used).
 __global__ void k_gram_inverse(const float *__restrict__ G32, int k, double *__restrict__ Q,
                                int *__restrict__ ok) {
   extern __shared__ double sm[];
@@ -145,7 +147,22 @@ __global__ void k_gram_inverse(const float *__restrict__ G32, int k, double *__r
     }
     for (int i = 0; i < k; ++i) Q[i * k + j] = v[i];
   }
-  if (threadIdx.x == 0) *ok = good;
+  __syncthreads();
+  // cond_1(G) = ||G||_1 ||Q||_1 (max column sums): solves through Q lose
+  // about log10(cond) digits, so Q is used only for well-conditioned G
+  if (threadIdx.x == 0) {
+    double ng = 0.0, nq = 0.0;
+    for (int j = 0; j < k; ++j) {
+      double cg = 0.0, cq = 0.0;
+      for (int i = 0; i < k; ++i) {
+        cg += fabs((double)G32[i * k + j]);
+        cq += fabs(Q[i * k + j]);
+      }
+      ng = cg > ng ? cg : ng;
+      nq = cq > nq ? cq : nq;
+    }
+    *ok = (good && ng * nq < kQMaxCond) ? 1 : 0;
+  }
 }
 
 template <int KT>
@@ -157,19 +174,22 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
   const BppLayout lay = bpp_layout(k);
   double *G = sm;
   double *Q = sm + lay.g_dbl;
+  float *Gabs = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);  // |G| in FP32
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     G[e] = (double)G32[e];
     Q[e] = Qg[e];
+    Gabs[e] = fabsf(G32[e]);
   }
   const bool have_q = *q_ok != 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
-  double *L = sm + 2 * lay.g_dbl + (size_t)wib * lay.warp_dbl;
+  double *L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
   double *v = L + (size_t)lay.kh * lay.ldl;   // small system's right-hand side, then x_F
   double *rs = v + k;                         // r, by index
   int *Fl = reinterpret_cast<int *>(rs + k);  // passive indices, ascending
   int *Bl = Fl + k;                           // active indices, ascending
+  float *xa = reinterpret_cast<float *>(Bl + k);  // |x_F| in FP32, F order
   const int ldl = lay.ldl;
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -192,7 +212,7 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
     }
     __syncwarp();
     int alpha = 3, beta = k + 1, it = 0;
-    bool failed_numeric = false, failed_cap = false, used_q = false;
+    bool failed_numeric = false, failed_cap = false;
     bool need_solve = __any_sync(0xffffffffu, any);
     for (;;) {
       if (need_solve) {
@@ -220,7 +240,6 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
           // ---- direct: G_FF x_F = r_F; v[0..nf) ends as x_F in F order
           if (nf > lay.kh) { failed_numeric = true; break; }
           if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
-          used_q = false;
           for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
           __syncwarp();
           warp_chol_solve(L, ldl, nf, v, lane);
@@ -240,7 +259,6 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
           }
           __syncwarp();
           if (!warp_cholesky(Q, k, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
-          used_q = true;
           warp_chol_solve(L, ldl, nb, v, lane);
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
@@ -256,35 +274,30 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
             if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the y update
         }
         __syncwarp();
-        // ---- y = G x - r on the active set; after a solve through Q, also
-        // the passive rows, which must vanish (else the row is re-solved by
-        // the direct fallback)
-        bool bad_res = false;
+        for (int a = lane; a < nf; a += 32) xa[a] = fabsf((float)v[a]);
+        __syncwarp();
+        // ---- y = G x - r on the active set: one FP64 FMA per term; the
+        // tolerance scale |r_j| + sum |G_jF x_F| needs no FP64 and is summed
+        // in FP32 from |G| and |x_F|
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int j = lane + 32 * t;
           if (j >= k) continue;
-          if (pas[t] && !used_q) {
+          if (pas[t]) {
             y[t] = 0.0;
             tau[t] = 0.0;
           } else {
-            double s = -rr[t], mag = fabs(rr[t]);
+            double s = -rr[t];
+            float mag = fabsf((float)rr[t]);
             for (int a = 0; a < nf; ++a) {
-              const double g = G[j * k + Fl[a]] * v[a];
-              s += g;
-              mag += fabs(g);
+              const int f = Fl[a];
+              s = fma(G[j * k + f], v[a], s);
+              mag = fmaf(Gabs[j * k + f], xa[a], mag);
             }
-            if (pas[t]) {
-              bad_res |= !(fabs(s) <= kQResTol * mag);
-              y[t] = 0.0;
-              tau[t] = 0.0;
-            } else {
-              y[t] = s;
-              tau[t] = kBppYTol * mag;
-            }
+            y[t] = s;
+            tau[t] = kBppYTol * (double)mag;
           }
         }
-        if (__any_sync(0xffffffffu, bad_res)) { failed_numeric = true; break; }
         __syncwarp();
       }
       // ---- infeasible set and exchange
@@ -338,10 +351,10 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
 }
 
 // Fallback for the rows the fast kernel flagged (a non-positive pivot in a
-// k/2-sized factorisation, a passive set too large for it while G itself is
-// not numerically positive definite, or a solve through Q whose passive
-// residual did not vanish): the same exchange rule from a cold start, every
-// passive system solved by a Cholesky factorisation of G_FF of any size.
+// k/2-sized factorisation, or a passive set too large for it while Q is not
+// in use because G is not numerically positive definite or is badly
+// conditioned): the same exchange rule from a cold start, every passive
+// system solved by a Cholesky factorisation of G_FF of any size.
 template <int KT>
 __global__ void __launch_bounds__(256)
     k_bpp_direct(const float *__restrict__ G32, const float *__restrict__ R, int64_t rows, int k,
@@ -493,10 +506,10 @@ cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, floa
   k_gram_inverse<<<1, 64, inv_smem, s>>>(G, k, Q, q_ok);
   const BppLayout lay = bpp_layout(k);
   const size_t budget = 200 * 1024;
-  int wpb = (int)((budget / sizeof(double) - 2 * lay.g_dbl) / lay.warp_dbl);
+  int wpb = (int)((budget / sizeof(double) - 2 * lay.g_dbl - lay.gf_dbl) / lay.warp_dbl);
   if (wpb > kBppWarps) wpb = kBppWarps;
   if (wpb < 1) wpb = 1;
-  const size_t smem = sizeof(double) * (2 * lay.g_dbl + (size_t)wpb * lay.warp_dbl);
+  const size_t smem = sizeof(double) * (2 * lay.g_dbl + lay.gf_dbl + (size_t)wpb * lay.warp_dbl);
   int64_t nb = (rows + wpb - 1) / wpb;
   if (nb > (int64_t)sm_count() * 2) nb = (int64_t)sm_count() * 2;
   // fallback: a full-size factor per warp, as many warps (<= 8) as fit

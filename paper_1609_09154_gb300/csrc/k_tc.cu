@@ -419,38 +419,93 @@ __global__ void k_split_transpose(const float *__restrict__ in, int64_t rows, in
 
 // One pass over A (m x n, lda) for the tensor-core runs: writes the rounded
 // copy X (m x n, ld ldx), the rounded transposed copy Xt (n x m, ld ldxt) and
-// per-block partial sums of a_ij^2 (FP64; each thread adds its squares of
-// one 64 x 64 tile in FP32 first).  Tiles of 64 x 64 go through shared
-// memory so both writes are row-contiguous.
+// per-block partial sums of a_ij^2 (FP64; each thread first adds the 16
+// squares it holds in FP32).  64 x 64 tiles: thread (ty, c4) loads the four
+// 16-byte pieces A[r0 + ty + 16 i][c0 + 4 c4 .. +3], i < 4, before storing
+// anything (VEC: rows of A are 16-byte aligned), then the tile is written
+// row-contiguously to X and, through shared memory, to Xt.
 template <class T>
+__device__ __forceinline__ void store4(T *dst, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store4<float>(float *dst, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(dst) =
+      make_float4(cvt<float>(a), cvt<float>(b), cvt<float>(c), cvt<float>(d));
+}
+template <>
+__device__ __forceinline__ void store4<uint16_t>(uint16_t *dst, float a, float b, float c,
+                                                 float d) {
+  uint2 u;
+  u.x = (uint32_t)cvt<uint16_t>(a) | ((uint32_t)cvt<uint16_t>(b) << 16);
+  u.y = (uint32_t)cvt<uint16_t>(c) | ((uint32_t)cvt<uint16_t>(d) << 16);
+  *reinterpret_cast<uint2 *>(dst) = u;
+}
+
+template <class T, bool VEC>
 __global__ void __launch_bounds__(256)
     k_prepare(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, T *__restrict__ X,
               int64_t ldx, T *__restrict__ Xt, int64_t ldxt, double *__restrict__ part) {
   __shared__ float t[64][65];
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+  const int c4 = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16
   const int64_t tr = (m + 63) / 64, tcn = (n + 63) / 64;
   double acc = 0.0;
   for (int64_t tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
     const int64_t r0 = (tile / tcn) * 64, c0 = (tile % tcn) * 64;
-    float sq = 0.f;
-    __syncthreads();
-#pragma unroll 4
-    for (int y = ty; y < 64; y += 4) {
-      const int64_t r = r0 + y, c = c0 + tx;
-      float v = 0.f;
-      if (r < m && c < n) {
-        v = A[r * lda + c];
-        X[r * ldx + c] = cvt<T>(v);
+    const int64_t c = c0 + 4 * c4;
+    float v[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty + 16 * i;
+      const float *src = A + r * lda + c;
+      if (r < m && VEC && c + 3 < n) {
+        const float4 q = __ldcs(reinterpret_cast<const float4 *>(src));
+        v[i][0] = q.x; v[i][1] = q.y; v[i][2] = q.z; v[i][3] = q.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[i][u] = (r < m && c + u < n) ? src[u] : 0.f;
       }
-      sq = fmaf(v, v, sq);
-      t[y][tx] = v;
     }
+    float sq = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sq = fmaf(v[i][u], v[i][u], sq);
     acc += (double)sq;
+    __syncthreads();  // previous tile's transposed reads are done
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int y = ty + 16 * i;
+      const int64_t r = r0 + y;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[y][4 * c4 + u] = v[i][u];
+      if (r < m) {
+        T *dst = X + r * ldx + c;
+        if (c + 3 < n) {
+          store4<T>(dst, v[i][0], v[i][1], v[i][2], v[i][3]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (c + u < n) dst[u] = cvt<T>(v[i][u]);
+        }
+      }
+    }
     __syncthreads();
-#pragma unroll 4
-    for (int y = ty; y < 64; y += 4) {
-      const int64_t c = c0 + y, r = r0 + tx;
-      if (r < m && c < n) Xt[c * ldxt + r] = cvt<T>(t[tx][y]);
+    // transposed: thread -> output row cc = c0 + threadIdx.x / 4, 16 entries
+    const int oc = threadIdx.x >> 2, seg = (threadIdx.x & 3) * 16;
+    const int64_t cc = c0 + oc;
+    if (cc < n) {
+      T *dst = Xt + cc * ldxt + r0 + seg;
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const int64_t r = r0 + seg + q;
+        if (r + 3 < m) {
+          store4<T>(dst + q, t[seg + q][oc], t[seg + q + 1][oc], t[seg + q + 2][oc],
+                    t[seg + q + 3][oc]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (r + u < m) dst[q + u] = cvt<T>(t[seg + q + u][oc]);
+        }
+      }
     }
   }
   // block sum in a fixed order
@@ -594,11 +649,22 @@ cudaError_t launch_prepare(const float *A, int64_t m, int64_t n, int64_t lda, vo
                            void *Xt, int64_t ldxt, bool bf16, double *part, double *norm2,
                            cudaStream_t s) {
   const int nb = prepare_blocks();
-  if (bf16)
-    k_prepare<uint16_t><<<nb, 256, 0, s>>>(A, m, n, lda, (uint16_t *)X, ldx, (uint16_t *)Xt, ldxt,
-                                          part);
-  else
-    k_prepare<float><<<nb, 256, 0, s>>>(A, m, n, lda, (float *)X, ldx, (float *)Xt, ldxt, part);
+  const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
+  if (bf16) {
+    if (vec)
+      k_prepare<uint16_t, true><<<nb, 256, 0, s>>>(A, m, n, lda, (uint16_t *)X, ldx,
+                                                   (uint16_t *)Xt, ldxt, part);
+    else
+      k_prepare<uint16_t, false><<<nb, 256, 0, s>>>(A, m, n, lda, (uint16_t *)X, ldx,
+                                                    (uint16_t *)Xt, ldxt, part);
+  } else {
+    if (vec)
+      k_prepare<float, true><<<nb, 256, 0, s>>>(A, m, n, lda, (float *)X, ldx, (float *)Xt, ldxt,
+                                                part);
+    else
+      k_prepare<float, false><<<nb, 256, 0, s>>>(A, m, n, lda, (float *)X, ldx, (float *)Xt, ldxt,
+                                                 part);
+  }
   k_sum_partials_d<<<1, 32, 0, s>>>(part, nb, norm2);
   g_launches += 2;
   return cudaGetLastError();
