@@ -15,12 +15,6 @@ constexpr int kLucThreads = 256;
 constexpr int kLucWarps = kLucThreads / kWarp;
 constexpr int kSmemGramMaxK = 108;  // 108*108*4 B < 48 KB default dynamic limit
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <bool SMEM>
 __device__ __forceinline__ const float *stage_gram(const float *G, int k, float *sG) {
   if constexpr (!SMEM) {
