@@ -17,9 +17,11 @@
 // Each exchange solves the passive-set normal equations G_FF x_F = r_F in
 // FP64 with a Cholesky factorisation of at most k/2 rows:
 //   |F| <= |B|: Cholesky of G_FF itself;
-//   |F| >  |B|: with Q = G^{-1} (FP64, computed once per update),
-//               G_FF^{-1} = Q_FF - Q_FB Q_BB^{-1} Q_BF, so with u = Q_:F r_F,
-//               x_F = u_F - Q_FB w,  Q_BB w = u_B  (Cholesky of Q_BB).
+//   |F| >  |B|: with Q = G^{-1} (FP64, computed once per update) and
+//               z = Q r (once per right-hand side): the solution with x_B = 0
+//               and y_F = 0 satisfies x = Q (r + y), so Q_BB y_B = -z_B
+//               (Cholesky of Q_BB) and x_F = z_F + Q_FB y_B -- the block
+//               inverse G_FF^{-1} = Q_FF - Q_FB Q_BB^{-1} Q_BF in other words.
 // The solution of each NLS is unique when G is positive definite (Sec. 4),
 // so the starting passive set changes only the work: the run driver starts
 // each right-hand side from the support of its previous iterate.  Rows whose
@@ -211,6 +213,16 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
       tau[t] = kBppYTol * fabs(rr[t]);
     }
     __syncwarp();
+    // z = G^{-1} r, shared by every exchange of this right-hand side
+    double z[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      double acc = 0.0;
+      if (have_q && j < k)
+        for (int l = 0; l < k; ++l) acc = fma(Q[j * k + l], rs[l], acc);
+      z[t] = acc;
+    }
     int alpha = 3, beta = k + 1, it = 0;
     bool failed_numeric = false, failed_cap = false;
     bool need_solve = __any_sync(0xffffffffu, any);
@@ -246,39 +258,37 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
 #pragma unroll
           for (int t = 0; t < KT; ++t) x[t] = pas[t] ? v[posf[t]] : 0.0;
         } else {
-          // ---- through Q = G^{-1}: u = Q_:F r_F; Q_BB w = u_B; x_F = u_F - Q_FB w
-          double u[KT];
+          // ---- through Q = G^{-1} and z = Q r: the constrained solution has
+          // Q_BB y_B = -z_B and x_F = z_F + Q_FB y_B (y_F = 0, x_B = 0)
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
-            double s = 0.0;
-            if (j < k)
-              for (int a = 0; a < nf; ++a) s = fma(Q[j * k + Fl[a]], rs[Fl[a]], s);
-            u[t] = s;
-            if (j < k && !pas[t]) v[posb[t]] = s;
+            if (j < k && !pas[t]) v[posb[t]] = z[t];
           }
           __syncwarp();
           if (!warp_cholesky(Q, k, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
-          warp_chol_solve(L, ldl, nb, v, lane);
+          warp_chol_solve(L, ldl, nb, v, lane);  // v = Q_BB^{-1} z_B = -y_B
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
-            double s = u[t];
+            double s = z[t];
             if (j < k && pas[t])
               for (int b = 0; b < nb; ++b) s = fma(-Q[j * k + Bl[b]], v[b], s);
             x[t] = (j < k && pas[t]) ? s : 0.0;
+            if (j < k && !pas[t]) y[t] = -v[posb[t]];
           }
           __syncwarp();
 #pragma unroll
           for (int t = 0; t < KT; ++t)
-            if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the y update
+            if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the tolerance scales
         }
         __syncwarp();
         for (int a = lane; a < nf; a += 32) xa[a] = fabsf((float)v[a]);
         __syncwarp();
-        // ---- y = G x - r on the active set: one FP64 FMA per term; the
-        // tolerance scale |r_j| + sum |G_jF x_F| needs no FP64 and is summed
+        // ---- active set: y = G_BF x_F - r_B (direct route; the Q route has
+        // it already) and the tolerance scale |r_j| + sum |G_jF x_F|, summed
         // in FP32 from |G| and |x_F|
+        const bool direct = nf <= nb || !have_q;
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int j = lane + 32 * t;
@@ -287,15 +297,14 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
             y[t] = 0.0;
             tau[t] = 0.0;
           } else {
-            double s = -rr[t];
             float mag = fabsf((float)rr[t]);
-            for (int a = 0; a < nf; ++a) {
-              const int f = Fl[a];
-              s = fma(G[j * k + f], v[a], s);
-              mag = fmaf(Gabs[j * k + f], xa[a], mag);
-            }
-            y[t] = s;
+            for (int a = 0; a < nf; ++a) mag = fmaf(Gabs[j * k + Fl[a]], xa[a], mag);
             tau[t] = kBppYTol * (double)mag;
+            if (direct) {
+              double s = -rr[t];
+              for (int a = 0; a < nf; ++a) s = fma(G[j * k + Fl[a]], v[a], s);
+              y[t] = s;
+            }
           }
         }
         __syncwarp();

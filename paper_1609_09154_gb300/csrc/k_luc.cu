@@ -15,6 +15,12 @@ constexpr int kLucThreads = 256;
 constexpr int kLucWarps = kLucThreads / kWarp;
 constexpr int kSmemGramMaxK = 108;  // 108*108*4 B < 48 KB default dynamic limit
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <bool SMEM>
 __device__ __forceinline__ const float *stage_gram(const float *G, int k, float *sG) {
   if constexpr (!SMEM) {
@@ -69,9 +75,6 @@ __global__ void __launch_bounds__(kLucThreads)
 // HALS column sweep (Sec. 4.2, Eq. halsupdate, exact coordinate steps):
 //   for i = 0..k-1:  x_i <- max(0, x_i + (p_i - (x G)_i) / G_ii)
 // with the current x (earlier entries already updated); G_ii <= 0 skips i.
-// The lanes keep d = x G for the current x: one mat-vec per row, then each
-// step's change delta of x_i (broadcast by its owner lane) updates
-// d += delta G(i, :) -- one shuffle per step instead of a warp reduction.
 template <int KT, bool SMEM>
 __global__ void __launch_bounds__(kLucThreads)
     k_hals(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ Gg,
@@ -82,48 +85,30 @@ __global__ void __launch_bounds__(kLucThreads)
   const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
   const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
   for (int64_t r = w0; r < rows; r += wstride) {
-    float x[KT], p[KT], d[KT];
+    float x[KT], p[KT];
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
       x[t] = j < k ? X[r * k + j] : 0.f;
       p[t] = j < k ? P[r * k + j] : 0.f;
-      d[t] = 0.f;
-    }
-#pragma unroll
-    for (int tl = 0; tl < KT; ++tl) {
-      for (int ll = 0; ll < 32; ++ll) {
-        const int l = 32 * tl + ll;
-        if (l >= k) break;
-        const float xl = __shfl_sync(0xffffffffu, x[tl], ll);
-#pragma unroll
-        for (int t = 0; t < KT; ++t) {
-          const int j = lane + 32 * t;
-          if (j < k) d[t] = fmaf(xl, G[l * k + j], d[t]);
-        }
-      }
     }
 #pragma unroll
     for (int ti = 0; ti < KT; ++ti) {
       for (int ii = 0; ii < 32; ++ii) {
         const int i = 32 * ti + ii;
         if (i >= k) break;
-        const float *Gi = G + i * k;  // G is symmetric: row i = column i
-        const float gii = Gi[i];
-        float delta = 0.f;
-        if (lane == ii && gii > 0.f) {
-          const float v = x[ti] + (p[ti] - d[ti]) / gii;
-          const float xn = v > 0.f ? v : 0.f;
-          delta = xn - x[ti];
-          x[ti] = xn;
-        }
-        delta = __shfl_sync(0xffffffffu, delta, ii);
-        if (delta != 0.f) {
+        const float* Gi = G + i * k;  // G is symmetric: row i = column i
+        float part = 0.f;
 #pragma unroll
-          for (int t = 0; t < KT; ++t) {
-            const int j = lane + 32 * t;
-            if (j < k) d[t] = fmaf(delta, Gi[j], d[t]);
-          }
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) part = fmaf(x[t], Gi[j], part);
+        }
+        const float dot = warp_sum(part);
+        const float gii = Gi[i];
+        if (lane == ii && gii > 0.f) {
+          const float v = x[ti] + (p[ti] - dot) / gii;
+          x[ti] = v > 0.f ? v : 0.f;
         }
       }
     }
