@@ -174,6 +174,26 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
 int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const float *H, int k,
                  double *relres);
 
+/* ---- differentiable objective -------------------------------------------- */
+
+/* L = 0.5 ||A - W H||_F^2, the squared objective of Eq. (original NMF),
+ * halved, evaluated as 0.5 (||A||^2 - 2 <W^T A, H> + <W^T W, H H^T>) with the
+ * products in precision `prec` and FP64 reductions.
+ *   A [device], W m x k and H k x n [device]
+ *   loss   [device] one double (written, not synchronised)
+ *   WtA    [device] k x n, may be NULL: receives W^T A for aunmf_loss_bwd
+ * The call enqueues work on the handle's stream and returns. */
+int aunmf_loss_fwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
+                   int prec, double *loss, float *WtA);
+
+/* Gradient of L: dW = g (W H H^T - A H^T) (m x k) and dH = g (W^T W H - W^T A)
+ * (k x n) -- the two terms whose ratio is Eq. (muupdate) -- with g = *grad_out
+ * read on the device (grad_out NULL: g = 1).  WtA (k x n, from
+ * aunmf_loss_fwd) may be NULL, in which case W^T A is recomputed.  dW or dH
+ * may be NULL to skip that gradient.  All pointers [device]; enqueues only. */
+int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
+                   int prec, const float *WtA, const float *grad_out, float *dW, float *dH);
+
 /* ---- fixed-memory variant ------------------------------------------------ */
 
 /* G = W^T W (k x k) for W m x k [device in/out], like aunmf_gram_w, for

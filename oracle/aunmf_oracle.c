@@ -475,6 +475,34 @@ double or_loss_grad(const or_matrix *A, const double *W, const double *H, int k,
   return loss;
 }
 
+/* One row of dL/dW and one column of dL/dH from the same definitions, for
+   checks on matrices too large for or_loss_grad:
+     (dL/dW)_r,: = sum_c R_rc H_:,c^T,   (dL/dH)_:,c = sum_r W_r,:^T R_rc,
+   with R_rc = (W H)_rc - A_rc formed entry by entry. */
+void or_grad_w_row(const or_matrix *A, const double *W, const double *H, int k, int64_t r,
+                   double *out) {
+  const int64_t n = A->n;
+  for (int i = 0; i < k; ++i) out[i] = 0.0;
+  for (int64_t c = 0; c < n; ++c) {
+    double wh = 0.0;
+    for (int i = 0; i < k; ++i) wh += W[r * k + i] * H[i * n + c];
+    const double R = wh - A->dense[r * n + c];
+    for (int i = 0; i < k; ++i) out[i] += R * H[i * n + c];
+  }
+}
+
+void or_grad_h_col(const or_matrix *A, const double *W, const double *H, int k, int64_t c,
+                   double *out) {
+  const int64_t m = A->m, n = A->n;
+  for (int i = 0; i < k; ++i) out[i] = 0.0;
+  for (int64_t r = 0; r < m; ++r) {
+    double wh = 0.0;
+    for (int i = 0; i < k; ++i) wh += W[r * k + i] * H[i * n + c];
+    const double R = wh - A->dense[r * n + c];
+    for (int i = 0; i < k; ++i) out[i] += W[r * k + i] * R;
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* AU-NMF driver (Alg. 1)                                                     */
 /* ------------------------------------------------------------------------ */

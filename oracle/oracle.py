@@ -83,6 +83,8 @@ def lib():
                 "or_relres_direct": (D, [P, P, P, I]),
                 "or_relres_trace": (D, [D, P, P, P, P, I, I64]),
                 "or_loss_grad": (D, [P, P, P, I, P, P]),
+                "or_grad_w_row": (None, [P, P, P, I, I64, P]),
+                "or_grad_h_col": (None, [P, P, P, I, I64, P]),
                 "or_nmf_run": (I, [P, I, I, I, P, P, P, P, P, D, I, P]),
             }
             for name, (res, args) in sig.items():
@@ -260,6 +262,38 @@ def loss_grad(A, W, H):
     dH = np.empty_like(H)
     loss = lib().or_loss_grad(A.ptr, _p(W), _p(H), k, _p(dW), _p(dH))
     return float(loss), dW, dH
+
+
+def grad_w_rows(A, W, H, rows):
+    """Rows `rows` of dL/dW for dense A (large-matrix checks)."""
+    A = as_matrix(A)
+    W, H = _d(W), _d(H)
+    k = W.shape[1]
+    out = np.empty((len(rows), k))
+    for t, r in enumerate(rows):
+        row = np.empty(k)
+        lib().or_grad_w_row(A.ptr, _p(W), _p(H), k, int(r), _p(row))
+        out[t] = row
+    return out
+
+
+def grad_h_cols(A, W, H, cols):
+    """Columns `cols` of dL/dH (as rows of the result) for dense A."""
+    A = as_matrix(A)
+    W, H = _d(W), _d(H)
+    k = W.shape[1]
+    out = np.empty((len(cols), k))
+    for t, c in enumerate(cols):
+        col = np.empty(k)
+        lib().or_grad_h_col(A.ptr, _p(W), _p(H), k, int(c), _p(col))
+        out[t] = col
+    return out
+
+
+def resid2(A, W, H):
+    """||A - W H||_F^2 entry by entry."""
+    W, H = _d(W), _d(H)
+    return float(lib().or_resid2_direct(as_matrix(A).ptr, _p(W), _p(H), W.shape[1]))
 
 
 def nmf_run(A, k, algo, iters, W0, H0, mu_eps=1e-16, bpp_max_iter=None):

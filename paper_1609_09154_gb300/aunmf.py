@@ -82,6 +82,8 @@ SIGNATURES = {
     "aunmf_nls_bpp": [_P, _P, _P, _I64, _I, _P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
     "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
+    "aunmf_loss_fwd": [_P, _MP, _I, _P, _P, _I, _P, _P],
+    "aunmf_loss_bwd": [_P, _MP, _I, _P, _P, _I, _P, _P, _P, _P],
 }
 _RESTYPE = {"aunmf_strerror": ctypes.c_char_p, "aunmf_last_cuda_error": ctypes.c_char_p}
 
@@ -293,6 +295,32 @@ class Handle:
                                      ctypes.byref(piv), ctypes.byref(nc))
         self._check(rc, allow=(E_NOCONVERGE,))
         return X, piv.value, nc.value
+
+    def loss_fwd(self, A, W, H, prec="fp32", save_wta=True):
+        """Returns (loss as a 0-dim float64 CUDA tensor, W^T A or None)."""
+        torch = _torch()
+        M = A if isinstance(A, Matrix) else dense_matrix(A)
+        _check_dev(W, H)
+        k = W.shape[1]
+        prec = PRECS[prec] if isinstance(prec, str) else prec
+        loss = torch.empty((), device=W.device, dtype=torch.float64)
+        wta = torch.empty((k, M.n), device=W.device, dtype=torch.float32) if save_wta else None
+        self._check(self._lib.aunmf_loss_fwd(self._h, ctypes.byref(M), k, _ptr(W), _ptr(H), prec,
+                                             _ptr(loss), _ptr(wta)))
+        return loss, wta
+
+    def loss_bwd(self, A, W, H, grad_out=None, wta=None, prec="fp32", need_w=True, need_h=True):
+        """Returns (dW, dH); grad_out is a 1-element float32 CUDA tensor or None."""
+        torch = _torch()
+        M = A if isinstance(A, Matrix) else dense_matrix(A)
+        _check_dev(W, H, wta, grad_out)
+        k = W.shape[1]
+        prec = PRECS[prec] if isinstance(prec, str) else prec
+        dW = torch.empty_like(W) if need_w else None
+        dH = torch.empty_like(H) if need_h else None
+        self._check(self._lib.aunmf_loss_bwd(self._h, ctypes.byref(M), k, _ptr(W), _ptr(H), prec,
+                                             _ptr(wta), _ptr(grad_out), _ptr(dW), _ptr(dH)))
+        return dW, dH
 
     def relres(self, A, W, H):
         M = A if isinstance(A, Matrix) else dense_matrix(A)

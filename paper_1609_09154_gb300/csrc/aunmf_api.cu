@@ -40,6 +40,7 @@ struct aunmf_handle {
   Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
   Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
   Buf bppq;                            // BPP: G^{-1} in FP64
+  Buf dHt;                             // loss backward: (dL/dH)^T
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
@@ -391,8 +392,8 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->hA,
-                 &h->hW, &h->hH};
+                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
+                 &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -757,6 +758,100 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
                       P<double>(h->last), s));
   CK(h, cudaMemcpyAsync(relres, h->last.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
+  return AUNMF_OK;
+}
+
+// ------------------------------------------------------------ loss / gradient
+namespace {
+int loss_setup(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
+               int prec, RunCtx &c) {
+  if (!valid_matrix(A) || !W || !H || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
+  if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (!A->dense && prec != AUNMF_FP32) return AUNMF_E_UNSUPPORTED;
+  if (prec != AUNMF_FP32) {
+    int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
+    if (rc != AUNMF_OK) return rc;
+  }
+  const int64_t m = A->m, n = A->n;
+  ENS(h, h->Ht, sizeof(float) * n * k);
+  ENS(h, h->PW, sizeof(float) * m * k);
+  ENS(h, h->PHt, sizeof(float) * n * k);
+  ENS(h, h->GH, sizeof(float) * k * k);
+  ENS(h, h->GW, sizeof(float) * k * k);
+  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  ENS(h, h->dpart, dpart_bytes(h));
+  ENS(h, h->n2a, sizeof(double));
+  c.A = A;
+  c.k = k;
+  c.prec = prec;
+  c.W = const_cast<float *>(W);
+  c.Ht = P<float>(h->Ht);
+  c.PW = P<float>(h->PW);
+  c.PHt = P<float>(h->PHt);
+  c.GH = P<float>(h->GH);
+  c.GW = P<float>(h->GW);
+  c.gpart = P<float>(h->gpart);
+  c.dpart = P<double>(h->dpart);
+  c.n2a = P<double>(h->n2a);
+  cudaStream_t s = h->stream;
+  CK(h, launch_transpose(H, k, n, c.Ht, s));
+  if (prec != AUNMF_FP32) {
+    int rc = prepare_tc(h, c, s);  // also writes ||A||^2
+    if (rc != AUNMF_OK) return rc;
+  } else if (A->dense) {
+    CK(h, launch_norm2(A->dense, m, n, A->lda, c.dpart, h->n_dparts, c.n2a, s));
+  } else {
+    CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
+  }
+  if (!A->dense) {
+    int rc = prepare_sparse(h, c, s);
+    if (rc != AUNMF_OK) return rc;
+  }
+  return AUNMF_OK;
+}
+}  // namespace
+
+int aunmf_loss_fwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
+                   int prec, double *loss, float *WtA) {
+  if (!h || !loss) return AUNMF_E_INVAL;
+  RunCtx c{};
+  int rc = loss_setup(h, A, k, W, H, prec, c);
+  if (rc != AUNMF_OK) return rc;
+  cudaStream_t s = h->stream;
+  const int64_t m = A->m, n = A->n;
+  CK(h, product_wta(h, c, s));
+  CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s));
+  CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+  CK(h, launch_loss(c.PHt, c.Ht, n * (int64_t)k, c.GW, c.GH, k, c.n2a, c.dpart, h->n_dparts, loss,
+                    s));
+  if (WtA) CK(h, launch_transpose(c.PHt, n, k, WtA, s));
+  return AUNMF_OK;
+}
+
+int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
+                   int prec, const float *WtA, const float *grad_out, float *dW, float *dH) {
+  if (!h || (!dW && !dH)) return AUNMF_E_INVAL;
+  RunCtx c{};
+  int rc = loss_setup(h, A, k, W, H, prec, c);
+  if (rc != AUNMF_OK) return rc;
+  cudaStream_t s = h->stream;
+  const int64_t m = A->m, n = A->n;
+  if (dW) {  // dL/dW = W (H H^T) - A H^T
+    CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+    CK(h, product_aht(h, c, s));
+    CK(h, launch_xg_minus_p(c.W, c.PW, c.GH, m, k, grad_out, dW, s));
+  }
+  if (dH) {  // dL/dH = (W^T W) H - W^T A, formed transposed
+    ENS(h, h->dHt, sizeof(float) * n * k);
+    CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s));
+    if (WtA) {
+      CK(h, launch_transpose(WtA, k, n, c.PHt, s));
+    } else {
+      CK(h, product_wta(h, c, s));
+    }
+    CK(h, launch_xg_minus_p(c.Ht, c.PHt, c.GW, n, k, grad_out, P<float>(h->dHt), s));
+    CK(h, launch_transpose(P<float>(h->dHt), n, k, dH, s));
+  }
   return AUNMF_OK;
 }
 

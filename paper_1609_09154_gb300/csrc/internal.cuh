@@ -88,6 +88,14 @@ cudaError_t launch_relres(const float *P, const float *Ht, int64_t len, const fl
                           int nparts, double *relres_dev, DevCounters *ctr, double *last,
                           cudaStream_t s);
 
+// 0.5 ||A - W H||^2 = 0.5 (n2a - 2 <P, Ht> + <GW, GH>) into *loss (device).
+cudaError_t launch_loss(const float *P, const float *Ht, int64_t len, const float *GW,
+                        const float *GH, int k, const double *n2a, double *partials, int nparts,
+                        double *loss, cudaStream_t s);
+// out = g (X G - P), X and P rows x k, G k x k, g = *gscale (NULL: 1).
+cudaError_t launch_xg_minus_p(const float *X, const float *P, const float *G, int64_t rows, int k,
+                              const float *gscale, float *out, cudaStream_t s);
+
 // Copy with a different leading dimension (rows x cols).
 cudaError_t launch_copy2d(const float *in, int64_t ld_in, float *out, int64_t ld_out,
                           int64_t rows, int64_t cols, cudaStream_t s);

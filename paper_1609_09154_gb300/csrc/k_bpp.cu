@@ -65,7 +65,10 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
 }
 
 // In-warp Cholesky of the n x n SPD matrix M(a, b) = Mg[I[a] * k + I[b]]
-// into L (lower, ld ldl).  Returns false (warp-uniform) on a non-positive
+// into L (lower, ld ldl); the diagonal slot holds 1 / L_cc instead of L_cc
+// (one reciprocal square root per column, then only multiplications: the
+// FP64 pipe is the bottleneck, and each FP64 division or square root costs
+// it several instructions).  Returns false (warp-uniform) on a non-positive
 // pivot.
 __device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int *I, int n,
                                               double *L, int ldl, int lane) {
@@ -74,30 +77,31 @@ __device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int
     for (int t = lane; t < c; t += 32) part = fma(L[c * ldl + t], L[c * ldl + t], part);
     const double d = Mg[I[c] * k + I[c]] - warp_sum_d(part);
     if (!(d > 0.0)) return false;
-    const double lcc = sqrt(d);
+    const double inv = rsqrt(d);
     for (int a = c + 1 + lane; a < n; a += 32) {
       double s = Mg[I[a] * k + I[c]];
       for (int t = 0; t < c; ++t) s = fma(-L[a * ldl + t], L[c * ldl + t], s);
-      L[a * ldl + c] = s / lcc;
+      L[a * ldl + c] = s * inv;
     }
-    if (lane == 0) L[c * ldl + c] = lcc;
+    if (lane == 0) L[c * ldl + c] = inv;
     __syncwarp();
   }
   return true;
 }
 
-// v <- (L L^T)^{-1} v for v[0..n) in shared memory.
+// v <- (L L^T)^{-1} v for v[0..n) in shared memory (L from warp_cholesky,
+// reciprocal diagonal).
 __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n, double *v,
                                                 int lane) {
   for (int c = 0; c < n; ++c) {
-    const double vc = v[c] / L[c * ldl + c];
+    const double vc = v[c] * L[c * ldl + c];
     __syncwarp();
     for (int a = c + 1 + lane; a < n; a += 32) v[a] = fma(-L[a * ldl + c], vc, v[a]);
     if (lane == 0) v[c] = vc;
     __syncwarp();
   }
   for (int c = n - 1; c >= 0; --c) {
-    const double vc = v[c] / L[c * ldl + c];
+    const double vc = v[c] * L[c * ldl + c];
     __syncwarp();
     for (int a = lane; a < c; a += 32) v[a] = fma(-L[c * ldl + a], vc, v[a]);
     if (lane == 0) v[c] = vc;

@@ -120,6 +120,50 @@ __global__ void __launch_bounds__(kLucThreads)
   }
 }
 
+// Gradient rows of 0.5 ||A - W H||_F^2: out = g (X G - P) for X rows x k,
+// G k x k, P rows x k (X = W, G = H H^T, P = A H^T gives dL/dW; X = H^T,
+// G = W^T W, P = (W^T A)^T gives (dL/dH)^T).  g is read from device memory
+// (NULL: g = 1).  Same lane layout as k_mu.
+template <int KT, bool SMEM>
+__global__ void __launch_bounds__(kLucThreads)
+    k_xg_minus_p(const float *__restrict__ X, const float *__restrict__ P,
+                 const float *__restrict__ Gg, int64_t rows, int k, const float *__restrict__ gscale,
+                 float *__restrict__ out) {
+  extern __shared__ float sG[];
+  const float *G = stage_gram<SMEM>(Gg, k, sG);
+  const float g = gscale ? *gscale : 1.f;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
+  const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
+  for (int64_t r = w0; r < rows; r += wstride) {
+    float x[KT], acc[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      x[t] = j < k ? X[r * k + j] : 0.f;
+      acc[t] = 0.f;
+    }
+#pragma unroll
+    for (int tl = 0; tl < KT; ++tl) {
+      for (int ll = 0; ll < 32; ++ll) {
+        const int l = 32 * tl + ll;
+        if (l >= k) break;
+        const float xl = __shfl_sync(0xffffffffu, x[tl], ll);
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) acc[t] = fmaf(xl, G[l * k + j], acc[t]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) out[r * k + j] = g * (acc[t] - P[r * k + j]);
+    }
+  }
+}
+
 // HALS normalisation (Eq. halsupdate, w^i / ||w^i||, compensated in H):
 // s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i; GW_ij /= s_i s_j.
 __global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
@@ -197,6 +241,21 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
   else k_hals<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k);
   AUNMF_KT_SWITCH(kt, AUNMF_CALL_HALS)
 #undef AUNMF_CALL_HALS
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xg_minus_p(const float *X, const float *P, const float *G, int64_t rows, int k,
+                              const float *gscale, float *out, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  const int kt = (k + 31) / 32, nb = luc_blocks(rows);
+  const bool sm = k <= kSmemGramMaxK;
+  const size_t smem = sm ? sizeof(float) * k * k : 0;
+#define AUNMF_CALL_XG(KT)                                                                  \
+  if (sm) k_xg_minus_p<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k, gscale, out); \
+  else k_xg_minus_p<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k, gscale, out);
+  AUNMF_KT_SWITCH(kt, AUNMF_CALL_XG)
+#undef AUNMF_CALL_XG
   g_launches += 1;
   return cudaGetLastError();
 }

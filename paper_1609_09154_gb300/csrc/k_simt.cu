@@ -416,7 +416,28 @@ __global__ void k_relres_final(const double *__restrict__ partials, int nparts,
     if (last) *last = rr;
   }
 }
+// loss = 0.5 (||A||^2 - 2 <P, Ht> + <GW, GH>), FP64 (not clamped).
+__global__ void k_loss_final(const double *__restrict__ partials, int nparts,
+                             const float *__restrict__ GW, const float *__restrict__ GH, int k,
+                             const double *__restrict__ n2a, double *__restrict__ loss) {
+  double cross = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) cross += partials[b];
+  cross = block_sum_d(cross);
+  double quad = 0.0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
+  quad = block_sum_d(quad);
+  if (threadIdx.x == 0) *loss = 0.5 * (*n2a - 2.0 * cross + quad);
+}
 }  // namespace
+
+cudaError_t launch_loss(const float *P, const float *Ht, int64_t len, const float *GW,
+                        const float *GH, int k, const double *n2a, double *partials, int nparts,
+                        double *loss, cudaStream_t s) {
+  k_dot_partial<<<nparts, 256, 0, s>>>(P, Ht, len, partials);
+  k_loss_final<<<1, 256, 0, s>>>(partials, nparts, GW, GH, k, n2a, loss);
+  g_launches += 2;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_norm2(const float *A, int64_t m, int64_t n, int64_t lda, double *partials,
                          int nparts, double *out, cudaStream_t s) {

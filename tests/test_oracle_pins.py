@@ -366,3 +366,18 @@ def test_sparse_run_matches_dense_run():
         a = orc.nmf_run(Ms, 4, algo, 10, W0, H0)
         b = orc.nmf_run(D, 4, algo, 10, W0, H0)
         np.testing.assert_allclose(a["relres"], b["relres"], rtol=1e-10)
+
+
+def test_sampled_gradient_rows_and_columns_match_full_gradient():
+    """or_grad_w_row / or_grad_h_col (used at sizes where the full gradient is
+    too costly) against or_loss_grad, and the gradient against the closed form
+    (WH - A) H^T, W^T (WH - A) written with numpy."""
+    A, _, _ = synth.dense_lowrank(23, 19, 3, seed=21)
+    W, H = synth.init_factors(23, 19, 4, seed=21)
+    _, dW, dH = orc.loss_grad(A, W, H)
+    np.testing.assert_allclose(orc.grad_w_rows(A, W, H, [0, 7, 22]), dW[[0, 7, 22]], rtol=1e-12)
+    np.testing.assert_allclose(orc.grad_h_cols(A, W, H, [0, 5, 18]), dH[:, [0, 5, 18]].T, rtol=1e-12)
+    R = W @ H - A
+    np.testing.assert_allclose(dW, R @ H.T, rtol=1e-12)
+    np.testing.assert_allclose(dH, W.T @ R, rtol=1e-12)
+    assert orc.resid2(A, W, H) == pytest.approx(np.sum(R * R), rel=1e-13)
