@@ -25,6 +25,34 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NMF iters/s & TFLOP/s (MU/HALS/ABPP), mixed vs FP32 at matched rel. residual"
 M_FULL, N_FULL, K_FULL, RANK_FULL, SEED = 96_000, 64_000, 50, 50, 1609
+# --workload: the default dense case, the sparse case and the 80 GB dense case
+WORKLOADS = {
+    "dense": {"m": M_FULL, "n": N_FULL, "k": K_FULL, "rank": RANK_FULL},
+    "sparse": {"m": 1_000_000, "n": 500_000, "k": 50, "density": 1e-4},
+    "scale": {"m": 172_800, "n": 115_200, "k": 100, "rank": 100},
+}
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def recorded_traffic(workload_key, prec, launch):
+    """DRAM bytes of one product launch from a committed ncu capture, or None
+    when there is none or the kernel's source changed since it was taken."""
+    import hashlib
+
+    try:
+        entries = json.load(open(TRAFFIC))["entries"]
+    except Exception:
+        return None
+    for e in entries:
+        if (e["workload"], e["prec"], e["launch"]) != (workload_key, prec, launch):
+            continue
+        src = os.path.join(ROOT, e["source"])
+        try:
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        except OSError:
+            return None
+        return e["dram_bytes"] if sha == e["source_sha256"] else None
+    return None
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SMS, FP32_LANES = 152, 128
@@ -49,10 +77,17 @@ def flops_per_iter(m, n, k, algo):
 
 
 def product_bytes(m, n, k, prec):
-    """Algorithmic bytes of one product launch: A once (4 B FP32/TF32, 2 B for
-    the BF16 copy), the fixed factor once, the output once."""
+    """Algorithmic bytes of one dense product launch: A once (4 B FP32/TF32,
+    2 B for the BF16 copy), the fixed factor once, the output once."""
     ea = 2 if prec == "bf16" else 4
     return ea * m * n + 4 * (n * k + m * k)
+
+
+def spmm_bytes(rows, cols, nnz, k):
+    """Algorithmic bytes of one sparse product launch: values and column
+    indices once (8 B per nonzero), row pointers, the fixed factor once, the
+    output once."""
+    return 8 * nnz + 8 * (rows + 1) + 4 * cols * k + 4 * rows * k
 
 
 class Clocks:
@@ -218,11 +253,24 @@ def run_reference(args):
 
 def config_dict(args):
     m, n = getattr(args, "m", M_FULL), getattr(args, "n", N_FULL)
-    return {"workload": f"dense {m}x{n} FP32, planted rank {RANK_FULL} + |N(0,0.01^2)|, "
-                        f"k={args.k}, {args.algo.upper()}, products in {args.prec.upper()}",
-            "m": m, "n": n, "k": args.k, "algo": args.algo, "prec": args.prec,
-            "l2": "inputs larger than L2 (A is 24.6 GB), no flush needed",
+    wl = getattr(args, "workload", "dense")
+    if wl == "sparse":
+        desc = (f"sparse CSR {m}x{n}, density {args.density:g} at uniform positions, values "
+                f"U(0,1], k={args.k}, {args.algo.upper()}, FP32 SpMM")
+        size = f"{8 * m * n * args.density / 1e9:.2f} GB of CSR values and indices"
+    else:
+        desc = (f"dense {m}x{n} FP32, planted rank {getattr(args, 'rank', RANK_FULL)} + "
+                f"|N(0,0.01^2)|, k={args.k}, {args.algo.upper()}, products in "
+                f"{args.prec.upper()}")
+        size = f"A is {4 * m * n / 1e9:.1f} GB"
+    return {"workload": desc, "m": m, "n": n, "k": args.k, "algo": args.algo,
+            "prec": args.prec,
+            "l2": f"inputs larger than the 129 MB L2 ({size}), no flush needed",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+def workload_key(args):
+    return f"{args.workload} {args.m}x{args.n} k={args.k}"
 
 
 # --------------------------------------------------------------------- ours
@@ -236,7 +284,14 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     m, n, k = args.m, args.n, args.k
-    A, _, _ = synth.dense_lowrank_torch(m, n, RANK_FULL, seed=SEED + rank, device=dev)
+    sparse = args.workload == "sparse"
+    if sparse:
+        csr = synth.sparse_uniform_torch(m, n, args.density, seed=SEED + rank, device=dev)
+        A = aunmf.csr_matrix(*csr, (m, n))
+        nnz = int(csr[2].numel())
+    else:
+        A, _, _ = synth.dense_lowrank_torch(m, n, args.rank, seed=SEED + rank, device=dev)
+        nnz = m * n
     W0, H0 = synth.init_factors_torch(m, n, k, seed=SEED + rank, device=dev)
     torch.cuda.synchronize()
     h = aunmf.Handle()
@@ -271,7 +326,17 @@ def run_ours(args):
     }
     dom = max(kern, key=lambda x: kern[x]["ms_avg"] * kern[x]["launches"])
     t_launch = kern[dom]["ms_avg"] / 1e3
-    if args.prec == "fp32":
+    if sparse:
+        by = spmm_bytes(m, n, nnz, k) if dom == "aht" else spmm_bytes(n, m, nnz, k)
+        ach = by / t_launch / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": recorded_traffic(workload_key(args), args.prec, dom),
+                "kernel": f"{dom} (CSR/CSC SpMM)",
+                "peak_note": f"hbm_gbs of {pks} peaks; algorithmic bytes count each nonzero, "
+                             f"the fixed factor and the output once (the k-vector gathers "
+                             f"are served from L2)"}
+    elif args.prec == "fp32":
         sm_mhz = (clk or {}).get("sm_mhz") or 1485.0
         peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         ach = 2.0 * m * n * k / t_launch / 1e12
@@ -284,7 +349,8 @@ def run_ours(args):
         ach = by / t_launch / 1e9
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "kernel": dom,
+                "frac": ach / peak, "traffic": recorded_traffic(workload_key(args), args.prec, dom),
+                "kernel": f"{dom} (k_gemm_tc)",
                 "peak_note": f"hbm_gbs of {pks} peaks"}
     for kk in kern.values():
         kk["ms_avg"] = round(kk["ms_avg"], 4)
@@ -296,7 +362,7 @@ def run_ours(args):
     # end to end through the host-buffer entry point: H2D of A, W0, H0 and the
     # D2H of W, H, relres inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not sparse:
         Ah = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         Ah.copy_(A)
         W0h = W0.cpu().pin_memory()
@@ -316,11 +382,14 @@ def run_ours(args):
                "note": f"one aunmf_run_host call of {args.steps} iterations; copies of "
                        f"the whole input/output amortised over its steps"}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and (m, n) == (M_FULL, N_FULL):
+    if (rank == 0 and world == 1 and not args.no_cpu and args.workload == "dense"
+            and (m, n) == (M_FULL, N_FULL)):
         cpu = cpu_baseline(args.algo, k)
 
     if rank == 0:
         f_it = flops_per_iter(m, n, k, args.algo)
+        if sparse:  # Sec. 5.2.1: 4 nnz k for the products
+            f_it = f_it - 4.0 * m * n * k + 4.0 * nnz * k
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
@@ -349,14 +418,23 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="hals", choices=["mu", "hals", "abpp"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"])
-    ap.add_argument("--k", type=int, default=K_FULL)
-    ap.add_argument("--m", type=int, default=M_FULL, help="rows of A (profiling cases)")
-    ap.add_argument("--n", type=int, default=N_FULL, help="columns of A (profiling cases)")
+    ap.add_argument("--workload", default="dense", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None, help="rows of A (profiling cases)")
+    ap.add_argument("--n", type=int, default=None, help="columns of A (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    args.m = args.m or wl["m"]
+    args.n = args.n or wl["n"]
+    args.k = args.k or wl["k"]
+    args.rank = wl.get("rank", RANK_FULL)
+    args.density = wl.get("density", 0.0)
+    if args.workload == "sparse":
+        args.prec = "fp32"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -101,3 +101,23 @@ def init_factors_torch(m: int, n: int, k: int, seed: int, device):
     H0 = torch.rand((k, n), generator=g, device=device, dtype=torch.float32)
     W0 = torch.rand((m, k), generator=g, device=device, dtype=torch.float32)
     return W0, H0
+
+
+def sparse_uniform_torch(m: int, n: int, density: float, seed: int, device):
+    """CSR on ``device``: round(m n density) positions drawn uniformly with
+    replacement (repeats dropped), values uniform on (0, 1].  Returns
+    (rowptr int64, colidx int32, val float32)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    nnz = int(round(m * n * density))
+    key = torch.randint(0, m * n, (nnz,), generator=g, device=device, dtype=torch.int64)
+    key = torch.unique(key)  # sorted by (row, col)
+    rows = key // n
+    cols = (key % n).to(torch.int32)
+    counts = torch.bincount(rows, minlength=m)
+    rowptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=rowptr[1:])
+    val = 1.0 - torch.rand(key.shape[0], generator=g, device=device, dtype=torch.float32)
+    return rowptr, cols.contiguous(), val
