@@ -154,6 +154,13 @@ struct PhaseTimer {
   }
 };
 
+// The tensor-core products stream the fixed factor as a two-term split (hi +
+// lo rows, MMA N = 2k) for k <= 64.  Beyond that the doubled N brings the
+// tensor pipe near saturation at HBM speed (k = 100 at 172,800 x 115,200 ran
+// the BF16 product at 91% of HBM with N = 208), and the factor's rounding
+// averages out over more terms in the residual's cross term anyway.
+bool use_split(int k) { return 2 * k <= 128; }
+
 cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const aunmf_matrix *A = c.A;
   (void)h;
@@ -166,7 +173,7 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
     return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
-  const bool split = tc::use_split(c.k);
+  const bool split = use_split(c.k);
   const int S = tc::splits_for(A->m, A->n, bf);
   cudaError_t e;
   {
@@ -200,7 +207,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
     return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
-  const bool split = tc::use_split(c.k);
+  const bool split = use_split(c.k);
   const int S = tc::splits_for(A->n, A->m, bf);
   cudaError_t e;
   {

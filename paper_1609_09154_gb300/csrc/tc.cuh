@@ -42,8 +42,6 @@ cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda,
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
                         int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
                         cudaStream_t s);
-// Whether the two-term factor split fits the MMA (2k <= 256).
-bool use_split(int k);
 // Y (2k x rows, ld ldo) = [hi; lo] rows of in (rows x k, ld ldi)^T, rounded to
 // nearest TF32 (FP32 containers) or BF16: hi = round(x), lo = round(x - hi).
 cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,
