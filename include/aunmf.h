@@ -93,6 +93,8 @@ typedef struct {
   float ms_aht, ms_wta, ms_update, ms_gram, ms_other;
   int n_aht, n_wta;
   int64_t launches;         /* kernels this call launched (graph replays counted per kernel) */
+  int tuned_bpp_warps;      /* aunmf_run_batched: autotuned BPP work tile (warps per block, */
+  int tuned_bpp_rows;       /*   rows per warp per item)                                    */
 } aunmf_info;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -135,6 +137,23 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
 int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_t lda, int k,
                    int algo, int iters, const float *W0, const float *H0, float *W, float *H,
                    double *relres, const aunmf_options *opt, aunmf_info *info);
+
+/* Many independent problems at once: `count` runs of Alg. 1 with ANLS/BPP
+ * (Sec. 4.3), problem p on dense A[p] (m_p x n_p [device]) with rank k[p]
+ * (1..64), from H0[p] (k_p x n_p [device]; W starts at 0 as in Alg. 1), into
+ * W[p] (m_p x k_p) and H[p] (k_p x n_p) [device].  A, k, W0, H0, W, H are
+ * HOST arrays of `count` entries (W0 is unused and may be NULL).
+ * Every phase of an iteration -- both tensor-core products, the Gram
+ * matrices, G^{-1}, the BPP solves, the residual -- is one launch covering
+ * all problems; one iteration is captured as a CUDA graph (use_graph) and
+ * replayed.  The BPP work tile is autotuned on the first call for a batch
+ * signature (count, sum m, sum n, max k, precision) and cached in the handle.
+ * Requires algo == AUNMF_ABPP and opt->prec TF32 or BF16.
+ * relres [host] count x iters, row p = problem p (may be NULL).  Synchronises. */
+int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const int *k, int algo,
+                      int iters, const float *const *W0, const float *const *H0, float *const *W,
+                      float *const *H, double *relres, const aunmf_options *opt,
+                      aunmf_info *info);
 
 /* ---- single steps of Alg. 1 (for step-by-step checks and custom drivers) -- */
 

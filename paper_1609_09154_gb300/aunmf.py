@@ -55,6 +55,7 @@ class Info(ctypes.Structure):
         ("ms_aht", ctypes.c_float), ("ms_wta", ctypes.c_float), ("ms_update", ctypes.c_float),
         ("ms_gram", ctypes.c_float), ("ms_other", ctypes.c_float),
         ("n_aht", ctypes.c_int), ("n_wta", ctypes.c_int), ("launches", ctypes.c_int64),
+        ("tuned_bpp_warps", ctypes.c_int), ("tuned_bpp_rows", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -83,6 +84,7 @@ SIGNATURES = {
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
     "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
     "aunmf_loss_fwd": [_P, _MP, _I, _P, _P, _I, _P, _P],
+    "aunmf_run_batched": [_P, _I, _MP, _P, _I, _I, _P, _P, _P, _P, _P, _OP, _IP],
     "aunmf_loss_bwd": [_P, _MP, _I, _P, _P, _I, _P, _P, _P, _P],
 }
 _RESTYPE = {"aunmf_strerror": ctypes.c_char_p, "aunmf_last_cuda_error": ctypes.c_char_p}
@@ -209,6 +211,31 @@ class Handle:
                                  ctypes.byref(opt), ctypes.byref(info))
         self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else ())
         return W, H, rel[:iters], info.as_dict()
+
+    def run_batched(self, As, ks, iters, H0s, *, prec="tf32", use_graph=True, bpp_max_pivots=0,
+                    allow_noconverge=False):
+        """ABPP on many problems at once (lists of dense CUDA tensors A_p, ranks
+        k_p, initial H0_p).  Returns (Ws, Hs, relres ndarray count x iters, info)."""
+        torch = _torch()
+        count = len(As)
+        mats = (Matrix * count)(*[dense_matrix(A) for A in As])
+        karr = (ctypes.c_int * count)(*ks)
+        Ws = [torch.empty((A.shape[0], k), device=A.device, dtype=torch.float32)
+              for A, k in zip(As, ks)]
+        Hs = [torch.empty((k, A.shape[1]), device=A.device, dtype=torch.float32)
+              for A, k in zip(As, ks)]
+        _check_dev(*H0s)
+        parr = lambda ts: (ctypes.c_void_p * count)(*[t.data_ptr() for t in ts])  # noqa: E731
+        rel = np.zeros((count, max(iters, 1)), dtype=np.float64)
+        prec = PRECS[prec] if isinstance(prec, str) else prec
+        opt = Options(prec, 0.0, bpp_max_pivots, int(use_graph), 0)
+        info = Info()
+        rc = self._lib.aunmf_run_batched(self._h, count, mats, karr, ABPP, iters, None,
+                                         parr(H0s), parr(Ws), parr(Hs),
+                                         rel.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt),
+                                         ctypes.byref(info))
+        self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else ())
+        return Ws, Hs, rel[:, :iters], info.as_dict()
 
     def run_host(self, A, k, algo, iters, W0, H0, *, prec="fp32", use_graph=True,
                  profile=False, W=None, H=None):

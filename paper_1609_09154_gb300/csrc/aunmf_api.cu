@@ -15,9 +15,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
+#include "batched.cuh"
 #include "internal.cuh"
 #include "tc.cuh"
 
@@ -41,6 +44,9 @@ struct aunmf_handle {
   Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
   Buf bppq;                            // BPP: G^{-1} in FP64
   Buf dHt;                             // loss backward: (dL/dH)^T
+  Buf batch, batch_meta;               // batched runs: arena, descriptors
+  // autotuned BPP work tile per batch signature: (warps per block, rows per warp)
+  std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> bpp_tuned;
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
@@ -400,7 +406,7 @@ int aunmf_destroy(aunmf_handle *h) {
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
                  &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
-                 &h->hA, &h->hW, &h->hH};
+                 &h->batch, &h->batch_meta, &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -859,6 +865,379 @@ int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
     CK(h, launch_xg_minus_p(c.Ht, c.PHt, c.GW, n, k, grad_out, P<float>(h->dHt), s));
     CK(h, launch_transpose(P<float>(h->dHt), n, k, dH, s));
   }
+  return AUNMF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched runs
+namespace {
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct BatchPlan {
+  std::vector<batched::BInst> inst;
+  std::vector<batched::Item> rows_w, rows_h, gram_w, gram_h, dot;
+  std::vector<int64_t> tiles_a, tiles_fh, tiles_fw, rows_mx;
+  std::vector<uint8_t> probs_aht, probs_wta;  // grouped GEMM descriptors
+  int64_t units_aht = 0, units_wta = 0;
+  int bn_aht = 16, bn_wta = 16;
+  int kmax = 1;
+  // device copies (offsets into the meta buffer)
+  size_t o_inst, o_rw, o_rh, o_gw, o_gh, o_dot, o_ta, o_tfh, o_tfw, o_rmx, o_pa, o_pw, o_h0, o_h, o_end;
+};
+
+// Items of up to `chunk` rows per problem (rows(b) rows); chunk index counts
+// the problem's items.
+template <class F>
+void make_items(std::vector<batched::Item> &out, const std::vector<batched::BInst> &inst,
+                int64_t chunk, F rows) {
+  out.clear();
+  for (int p = 0; p < (int)inst.size(); ++p) {
+    const int64_t R = rows(inst[p]);
+    int c = 0;
+    for (int64_t r = 0; r < R; r += chunk, ++c) {
+      batched::Item it;
+      it.p = p;
+      it.chunk = c;
+      it.r0 = r;
+      it.r1 = r + chunk < R ? r + chunk : R;
+      out.push_back(it);
+    }
+  }
+}
+
+template <class F>
+std::vector<int64_t> prefix_of(const std::vector<batched::BInst> &inst, F count) {
+  std::vector<int64_t> pre(inst.size() + 1, 0);
+  for (size_t p = 0; p < inst.size(); ++p) pre[p + 1] = pre[p] + count(inst[p]);
+  return pre;
+}
+}  // namespace
+
+extern "C" {
+
+int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const int *k, int algo,
+                      int iters, const float *const *W0, const float *const *H0, float *const *W,
+                      float *const *H, double *relres, const aunmf_options *opt,
+                      aunmf_info *info) {
+  (void)W0;
+  if (!h || count < 1 || !A || !k || iters < 0 || !H0 || !W || !H) return AUNMF_E_INVAL;
+  aunmf_options o{};
+  if (opt) o = *opt;
+  if (algo != AUNMF_ABPP) return AUNMF_E_UNSUPPORTED;
+  if (o.prec != AUNMF_TF32 && o.prec != AUNMF_BF16) return AUNMF_E_UNSUPPORTED;
+  const bool bf = o.prec == AUNMF_BF16;
+  const size_t esz = bf ? 2 : 4;
+  for (int p = 0; p < count; ++p) {
+    if (!A[p].dense || A[p].m < 1 || A[p].n < 1 || A[p].lda < A[p].n) return AUNMF_E_INVAL;
+    if (k[p] < 1 || k[p] > batched::kMaxK || !W[p] || !H0[p] || !H[p]) return AUNMF_E_INVAL;
+    if (A[p].m > 0x7fffffffLL || A[p].n > 0x7fffffffLL) return AUNMF_E_UNSUPPORTED;
+  }
+  if (tc::check(1, 1, 1, 1, o.prec, nullptr) != AUNMF_OK) return AUNMF_E_UNSUPPORTED;
+  cudaStream_t s = h->stream;
+  const int max_piv_opt = o.bpp_max_pivots;
+  constexpr int64_t kGramChunk = 256, kDotChunk = 16384;
+
+  // ---- arena layout
+  BatchPlan pl;
+  pl.inst.resize(count);
+  std::vector<size_t> off(count * 20);
+  size_t top = 0;
+  auto take = [&](size_t bytes) { const size_t at = top; top += al256(bytes ? bytes : 16); return at; };
+  const size_t relres_off = take(sizeof(double) * (size_t)count * (iters > 0 ? iters : 1));
+  for (int p = 0; p < count; ++p) {
+    batched::BInst &b = pl.inst[p];
+    b.m = A[p].m;
+    b.n = A[p].n;
+    b.k = k[p];
+    pl.kmax = b.k > pl.kmax ? b.k : pl.kmax;
+    b.lda = A[p].lda;
+    b.ldx = tc::copy_ld(b.n);
+    b.ldat = tc::copy_ld(b.m);
+    b.ldh = tc::copy_ld(b.n);
+    b.ldw = tc::copy_ld(b.m);
+    b.ngw = (int)((b.m + kGramChunk - 1) / kGramChunk);
+    b.ngh = (int)((b.n + kGramChunk - 1) / kGramChunk);
+    b.nr = (int)((b.n * b.k + kDotChunk - 1) / kDotChunk);
+    const size_t kk = (size_t)b.k * b.k, mx = (size_t)(b.m > b.n ? b.m : b.n);
+    size_t *o_ = &off[p * 20];
+    o_[0] = take(sizeof(float) * b.n * b.k);            // Ht
+    o_[1] = take(sizeof(float) * b.m * b.k);            // PW
+    o_[2] = take(sizeof(float) * b.n * b.k);            // PHt
+    o_[3] = take(sizeof(float) * kk);                   // GH
+    o_[4] = take(sizeof(float) * kk);                   // GW
+    o_[5] = take(sizeof(float) * kk * b.ngw);           // Gram partials (W)
+    o_[6] = take(sizeof(float) * kk * b.ngh);           // Gram partials (Ht)
+    o_[7] = take(esz * (size_t)b.m * b.ldx);            // Ax
+    o_[8] = take(esz * (size_t)b.n * b.ldat);           // At
+    o_[9] = take(esz * 2 * (size_t)b.k * b.ldh);        // Hk
+    o_[10] = take(esz * 2 * (size_t)b.k * b.ldw);       // Wt
+    o_[11] = take(sizeof(double) * kk);                 // Q
+    o_[12] = take(sizeof(int));                         // q_ok
+    o_[13] = take(mx);                                  // redo
+    o_[14] = take(sizeof(double));                      // n2a
+    o_[15] = take(sizeof(double) * b.nr);               // residual partials
+  }
+  std::vector<int64_t> tiles_prep;
+  pl.tiles_a = prefix_of(pl.inst, [](const batched::BInst &b) {
+    return ((b.m + 31) / 32) * ((b.n + 31) / 32);
+  });
+  const size_t tsq_off = take(sizeof(double) * (size_t)pl.tiles_a[count]);
+  ENS(h, h->batch, top);
+  uint8_t *base = P<uint8_t>(h->batch);
+  for (int p = 0; p < count; ++p) {
+    batched::BInst &b = pl.inst[p];
+    const size_t *o_ = &off[p * 20];
+    b.A = A[p].dense;
+    b.W = W[p];
+    b.Ht = reinterpret_cast<float *>(base + o_[0]);
+    b.PW = reinterpret_cast<float *>(base + o_[1]);
+    b.PHt = reinterpret_cast<float *>(base + o_[2]);
+    b.GH = reinterpret_cast<float *>(base + o_[3]);
+    b.GW = reinterpret_cast<float *>(base + o_[4]);
+    b.gpart_w = reinterpret_cast<float *>(base + o_[5]);
+    b.gpart_h = reinterpret_cast<float *>(base + o_[6]);
+    b.Ax = base + o_[7];
+    b.At = base + o_[8];
+    b.Hk = base + o_[9];
+    b.Wt = base + o_[10];
+    b.Q = reinterpret_cast<double *>(base + o_[11]);
+    b.q_ok = reinterpret_cast<int *>(base + o_[12]);
+    b.redo = base + o_[13];
+    b.n2a = reinterpret_cast<double *>(base + o_[14]);
+    b.rpart = reinterpret_cast<double *>(base + o_[15]);
+    b.relres = reinterpret_cast<double *>(base + relres_off) + (size_t)p * (iters > 0 ? iters : 1);
+  }
+  double *tile_sq = reinterpret_cast<double *>(base + tsq_off);
+
+  // ---- work lists and tile prefixes
+  make_items(pl.gram_w, pl.inst, kGramChunk, [](const batched::BInst &b) { return b.m; });
+  make_items(pl.gram_h, pl.inst, kGramChunk, [](const batched::BInst &b) { return b.n; });
+  make_items(pl.dot, pl.inst, kDotChunk, [](const batched::BInst &b) { return b.n * b.k; });
+  pl.tiles_fh = prefix_of(pl.inst, [](const batched::BInst &b) { return ((b.n + 31) / 32) * ((b.k + 31) / 32); });
+  pl.tiles_fw = prefix_of(pl.inst, [](const batched::BInst &b) { return ((b.m + 31) / 32) * ((b.k + 31) / 32); });
+  pl.rows_mx = prefix_of(pl.inst, [](const batched::BInst &b) { return (b.m > b.n ? b.m : b.n) * b.k; });
+
+  // ---- grouped GEMM descriptors
+  const size_t pb = tc::problem_bytes();
+  pl.probs_aht.assign(pb * count, 0);
+  pl.probs_wta.assign(pb * count, 0);
+  for (int p = 0; p < count; ++p) {
+    const batched::BInst &b = pl.inst[p];
+    int64_t u = 0;
+    int bn = 0;
+    if (!tc::fill_group_problem(&pl.probs_aht[pb * p], b.Ax, b.m, b.n, b.ldx, b.Hk, b.k, b.ldh,
+                                true, bf, b.PW, pl.units_aht, &u, &bn))
+      return AUNMF_E_UNSUPPORTED;
+    pl.units_aht += u;
+    pl.bn_aht = bn > pl.bn_aht ? bn : pl.bn_aht;
+    if (!tc::fill_group_problem(&pl.probs_wta[pb * p], b.At, b.n, b.m, b.ldat, b.Wt, b.k, b.ldw,
+                                true, bf, b.PHt, pl.units_wta, &u, &bn))
+      return AUNMF_E_UNSUPPORTED;
+    pl.units_wta += u;
+    pl.bn_wta = bn > pl.bn_wta ? bn : pl.bn_wta;
+  }
+
+  // ---- BPP work tile (autotuned once per batch signature)
+  int64_t sum_m = 0, sum_n = 0;
+  for (const auto &b : pl.inst) { sum_m += b.m; sum_n += b.n; }
+  const auto sig = std::make_tuple(count, sum_m, sum_n, pl.kmax, o.prec);
+  const int wmax = batched::bpp_max_warps(pl.kmax);
+  auto tune_it = h->bpp_tuned.find(sig);
+  std::pair<int, int> tile = tune_it != h->bpp_tuned.end() ? tune_it->second
+                                                           : std::make_pair(wmax, 4);
+
+  // ---- descriptors to the device: one staging copy
+  auto stage_meta = [&](std::vector<uint8_t> &buf) {
+    buf.clear();
+    auto put = [&](const void *src, size_t bytes) {
+      const size_t at = al256(buf.size());
+      buf.resize(at + al256(bytes ? bytes : 16), 0);
+      if (bytes) memcpy(&buf[at], src, bytes);
+      return at;
+    };
+    make_items(pl.rows_w, pl.inst, (int64_t)tile.first * tile.second,
+               [](const batched::BInst &b) { return b.m; });
+    make_items(pl.rows_h, pl.inst, (int64_t)tile.first * tile.second,
+               [](const batched::BInst &b) { return b.n; });
+    pl.o_inst = put(pl.inst.data(), sizeof(batched::BInst) * count);
+    pl.o_rw = put(pl.rows_w.data(), sizeof(batched::Item) * pl.rows_w.size());
+    pl.o_rh = put(pl.rows_h.data(), sizeof(batched::Item) * pl.rows_h.size());
+    pl.o_gw = put(pl.gram_w.data(), sizeof(batched::Item) * pl.gram_w.size());
+    pl.o_gh = put(pl.gram_h.data(), sizeof(batched::Item) * pl.gram_h.size());
+    pl.o_dot = put(pl.dot.data(), sizeof(batched::Item) * pl.dot.size());
+    pl.o_ta = put(pl.tiles_a.data(), sizeof(int64_t) * pl.tiles_a.size());
+    pl.o_tfh = put(pl.tiles_fh.data(), sizeof(int64_t) * pl.tiles_fh.size());
+    pl.o_tfw = put(pl.tiles_fw.data(), sizeof(int64_t) * pl.tiles_fw.size());
+    pl.o_rmx = put(pl.rows_mx.data(), sizeof(int64_t) * pl.rows_mx.size());
+    pl.o_pa = put(pl.probs_aht.data(), pl.probs_aht.size());
+    pl.o_pw = put(pl.probs_wta.data(), pl.probs_wta.size());
+    pl.o_h0 = put(H0, sizeof(float *) * count);
+    pl.o_h = put(H, sizeof(float *) * count);
+    pl.o_end = buf.size();
+  };
+  std::vector<uint8_t> meta;
+  {  // size the device copy for the most items any candidate tile produces
+    const std::pair<int, int> keep = tile;
+    tile = {8, 2};
+    stage_meta(meta);
+    const size_t most = meta.size();
+    tile = keep;
+    stage_meta(meta);
+    ENS(h, h->batch_meta, (most > meta.size() ? most : meta.size()) + 1024);
+  }
+  uint8_t *mb = P<uint8_t>(h->batch_meta);
+  CK(h, cudaMemcpyAsync(mb, meta.data(), meta.size(), cudaMemcpyHostToDevice, s));
+  auto D = [&](size_t o) { return mb + o; };
+  auto inst_d = [&]() { return reinterpret_cast<const batched::BInst *>(D(pl.o_inst)); };
+
+  ENS(h, h->ctr, sizeof(DevCounters));
+  ENS(h, h->err, sizeof(int));
+  DevCounters *ctr = P<DevCounters>(h->ctr);
+  int *err = P<int>(h->err);
+  const int max_piv = max_piv_opt > 0 ? max_piv_opt : 10 * pl.kmax;
+  const long long launches0 = g_launches;
+  long long graph_launches = 0;
+  cudaEvent_t t0, t1;
+  CK(h, cudaEventCreate(&t0));
+  CK(h, cudaEventCreate(&t1));
+  CK(h, cudaEventRecord(t0, s));
+  CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+  CK(h, cudaMemsetAsync(err, 0, sizeof(int), s));
+
+  // ---- setup: layout copies and norms, Ht = H0^T, W = 0, G_H
+  CK(h, batched::launch_prepare(inst_d(), reinterpret_cast<const int64_t *>(D(pl.o_ta)), count,
+                                pl.tiles_a[count], bf, tile_sq, s));
+  CK(h, batched::launch_init(inst_d(), reinterpret_cast<const float *const *>(D(pl.o_h0)),
+                             reinterpret_cast<const int64_t *>(D(pl.o_rmx)), count,
+                             pl.rows_mx[count], s));
+  CK(h, batched::launch_gram(inst_d(), reinterpret_cast<const batched::Item *>(D(pl.o_gh)),
+                             (int)pl.gram_h.size(), count, 0, s));
+
+  auto w_half = [&](cudaStream_t st, const batched::BInst *I, const batched::Item *rw, int nrw) {
+    cudaError_t e;
+    if ((e = batched::launch_split_transpose(I, reinterpret_cast<const int64_t *>(D(pl.o_tfh)),
+                                             count, pl.tiles_fh[count], 0, bf, st)) != cudaSuccess)
+      return e;
+    if ((e = tc::launch_gemm_group(D(pl.o_pa), pl.probs_aht.data(), count, pl.units_aht,
+                                   pl.bn_aht, bf, err, st)) != cudaSuccess)
+      return e;
+    return batched::launch_bpp(I, rw, nrw, count, 0, pl.kmax, max_piv, ctr, tile.first, st);
+  };
+  auto h_half = [&](cudaStream_t st, const batched::BInst *I, const batched::Item *rh, int nrh) {
+    cudaError_t e;
+    if ((e = batched::launch_gram(I, reinterpret_cast<const batched::Item *>(D(pl.o_gw)),
+                                  (int)pl.gram_w.size(), count, 1, st)) != cudaSuccess)
+      return e;
+    if ((e = batched::launch_split_transpose(I, reinterpret_cast<const int64_t *>(D(pl.o_tfw)),
+                                             count, pl.tiles_fw[count], 1, bf, st)) != cudaSuccess)
+      return e;
+    if ((e = tc::launch_gemm_group(D(pl.o_pw), pl.probs_wta.data(), count, pl.units_wta,
+                                   pl.bn_wta, bf, err, st)) != cudaSuccess)
+      return e;
+    if ((e = batched::launch_bpp(I, rh, nrh, count, 1, pl.kmax, max_piv, ctr, tile.first, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = batched::launch_gram(I, reinterpret_cast<const batched::Item *>(D(pl.o_gh)),
+                                  (int)pl.gram_h.size(), count, 0, st)) != cudaSuccess)
+      return e;
+    return batched::launch_relres(I, reinterpret_cast<const batched::Item *>(D(pl.o_dot)),
+                                  (int)pl.dot.size(), count, ctr, iters, st);
+  };
+
+  // ---- autotune the BPP work tile on the first W update (factors restored)
+  if (tune_it == h->bpp_tuned.end() && iters > 0) {
+    std::vector<std::pair<int, int>> cand;
+    for (int wp : {8, 16})
+      for (int rpw : {2, 8})
+        if (wp <= wmax) cand.push_back({wp, rpw});
+    if (cand.empty()) cand.push_back({wmax, 4});
+    float best = 1e30f;
+    std::pair<int, int> best_tile = cand[0];
+    cudaEvent_t a0, a1;
+    CK(h, cudaEventCreate(&a0));
+    CK(h, cudaEventCreate(&a1));
+    for (const auto &c : cand) {
+      tile = c;
+      stage_meta(meta);
+      CK(h, cudaMemcpyAsync(mb, meta.data(), meta.size(), cudaMemcpyHostToDevice, s));
+      for (const auto &b : pl.inst)  // W is all zero before the first update: restore it
+        CK(h, cudaMemsetAsync(b.W, 0, sizeof(float) * b.m * b.k, s));
+      CK(h, cudaEventRecord(a0, s));
+      CK(h, w_half(s, inst_d(), reinterpret_cast<const batched::Item *>(D(pl.o_rw)),
+                   (int)pl.rows_w.size()));
+      CK(h, cudaEventRecord(a1, s));
+      CK(h, cudaEventSynchronize(a1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a0, a1);
+      if (ms < best) { best = ms; best_tile = c; }
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    tile = best_tile;
+    h->bpp_tuned[sig] = tile;
+    for (const auto &b : pl.inst) CK(h, cudaMemsetAsync(b.W, 0, sizeof(float) * b.m * b.k, s));
+    CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
+    stage_meta(meta);
+    CK(h, cudaMemcpyAsync(mb, meta.data(), meta.size(), cudaMemcpyHostToDevice, s));
+  }
+
+  // ---- iterations: one captured iteration, replayed
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  if (iters > 0) {
+    const batched::Item *rw = reinterpret_cast<const batched::Item *>(D(pl.o_rw));
+    const batched::Item *rh = reinterpret_cast<const batched::Item *>(D(pl.o_rh));
+    if (o.use_graph && iters > 1) {
+      CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const long long lc0 = g_launches;
+      cudaError_t ce = w_half(h->cap_stream, inst_d(), rw, (int)pl.rows_w.size());
+      if (ce == cudaSuccess) ce = h_half(h->cap_stream, inst_d(), rh, (int)pl.rows_h.size());
+      const long long per_iter = g_launches - lc0;
+      g_launches = lc0;
+      cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (ce != cudaSuccess) return fail_cuda(h, ce, "batched iteration (capture)");
+      if (ee != cudaSuccess) return fail_cuda(h, ee, "cudaStreamEndCapture");
+      CK(h, cudaGraphInstantiate(&gexec, graph, 0));
+      graph_launches = per_iter * iters;
+      for (int t = 0; t < iters; ++t) CK(h, cudaGraphLaunch(gexec, s));
+    } else {
+      for (int t = 0; t < iters; ++t) {
+        CK(h, w_half(s, inst_d(), rw, (int)pl.rows_w.size()));
+        CK(h, h_half(s, inst_d(), rh, (int)pl.rows_h.size()));
+      }
+    }
+  }
+  CK(h, batched::launch_finish(inst_d(), reinterpret_cast<float *const *>(D(pl.o_h)),
+                               reinterpret_cast<const int64_t *>(D(pl.o_rmx)), count,
+                               pl.rows_mx[count], s));
+  CK(h, cudaEventRecord(t1, s));
+  DevCounters hc{};
+  int herr = 0;
+  CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (relres && iters > 0)
+    CK(h, cudaMemcpyAsync(relres, base + relres_off, sizeof(double) * (size_t)count * iters,
+                          cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->bpp_pivots = hc.bpp_pivots;
+    info->bpp_nonconverged = hc.bpp_nonconv;
+    info->bpp_numeric = hc.bpp_numeric;
+    info->iters_done = iters;
+    cudaEventElapsedTime(&info->ms_total, t0, t1);
+    info->launches = g_launches - launches0 + graph_launches;
+    info->tuned_bpp_warps = tile.first;
+    info->tuned_bpp_rows = tile.second;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (herr) return AUNMF_E_TIMEOUT;
+  if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
+  if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;
   return AUNMF_OK;
 }
 

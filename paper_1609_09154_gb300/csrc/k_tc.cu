@@ -172,23 +172,50 @@ __host__ __device__ constexpr uint32_t idesc(bool bf16, int M, int N) {
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-struct GemmArgs {
-  int64_t M, K;        // rows of X, contraction length (elements)
-  int k;               // valid columns of C
-  int BN;              // MMA N (k rounded up to 16), <= 256
+// One product C (M x k) = X (M x K) * F (k x K)^T of a launch.  A launch
+// runs one problem (passed by value) or a group of problems (a device array,
+// e.g. all instances of a batch); work units are numbered across the group.
+struct GemmProblem {
+  CUtensorMap mapX;    // X: M rows x K, box 128 B x 256 rows
+  CUtensorMap mapY;    // Y: F (k rows) or its hi/lo split (2k rows), box 128 B x BN rows
+  int64_t M, K;
+  int64_t unit0;       // first work unit of this problem in the launch
+  int64_t total_kb;    // K blocks of 128 bytes
+  int64_t per_split;   // K blocks per split
+  float *P;            // partials: S x M x k, row-major (S == 1: C itself)
+  int k;               // columns of C
+  int BN;              // MMA N (rows of Y rounded up to 16), <= BNmax
   int S;               // K splits
+  int pair;            // 1: Y rows (2i, 2i+1) hold hi/lo of F's row i; C_i = acc_2i + acc_2i+1
+};
+
+// Launch-wide shape: the shared-memory ring and TMEM are sized for BNmax.
+struct GemmLaunch {
+  int64_t units;       // total work units
+  int nprob;           // problems in `group` (0: the by-value problem only)
+  int BNmax;
   int nstages;
   int nbuf;            // TMEM accumulator buffers (1 or 2)
-  uint32_t tmem_cols;  // power of two >= nbuf * 2 * BN
-  int pair;            // 1: Y holds hi/lo rows (2i, 2i+1) per factor column i; C_i = acc_2i + acc_2i+1
-  float *P;            // partials: S x M x k, row-major
+  uint32_t tmem_cols;  // power of two >= nbuf * 2 * BNmax
   int *err;
 };
 
+__device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &one,
+                                                          const GemmProblem *group, int nprob,
+                                                          int64_t u) {
+  if (!group) return &one;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (group[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+  }
+  return group + lo;
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
-              const GemmArgs a) {
+    k_gemm_tc(const __grid_constant__ GemmProblem one, const GemmProblem *__restrict__ group,
+              const GemmLaunch L) {
   constexpr int ESZ = BF16 ? 2 : 4;
   constexpr int BKE = kStageBytesK / ESZ;  // K elements per stage
   constexpr int KPM = BF16 ? 16 : 8;       // K elements per MMA (32 bytes)
@@ -196,23 +223,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const uint32_t xbytes = kTileM * kStageBytesK;
-  const uint32_t ybytes = (uint32_t)a.BN * kStageBytesK;
-  const uint32_t sbytes = xbytes + ybytes;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)a.nstages * sbytes);
+  const uint32_t sbytes = xbytes + (uint32_t)L.BNmax * kStageBytesK;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)L.nstages * sbytes);
   uint64_t *full = bars;
-  uint64_t *empty = bars + a.nstages;
-  uint64_t *tfull = bars + 2 * a.nstages;
+  uint64_t *empty = bars + L.nstages;
+  uint64_t *tfull = bars + 2 * L.nstages;
   uint64_t *tempty = tfull + 2;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tiles = (a.M + kTileM - 1) / kTileM;
-  const int64_t units = tiles * a.S;
-  const int64_t total_kb = (a.K + BKE - 1) / BKE;
-  const int64_t per_split = (total_kb + a.S - 1) / a.S;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < a.nstages; ++s) {
+    for (int s = 0; s < L.nstages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -222,10 +244,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapX) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapY) : "memory");
+    if (!group) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&one.mapX) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&one.mapY) : "memory");
+    }
   }
-  if (warp == 1) tmem_alloc(tslot, a.tmem_cols);
+  if (warp == 1) tmem_alloc(tslot, L.tmem_cols);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
@@ -237,36 +261,41 @@ __global__ void __launch_bounds__(kThreads, 1)
       int st = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const int64_t tile = u / a.S, sp = u % a.S;
-        const int64_t kb0 = sp * per_split, kb1 = min(total_kb, kb0 + per_split);
+      for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
+        const GemmProblem *p = find_problem(one, group, L.nprob, u);
+        const int64_t v = u - p->unit0;
+        const int64_t tile = v / p->S, sp = v % p->S;
+        const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
         const int row0 = (int)(tile * kTileM);
+        const uint32_t tx = xbytes + (uint32_t)p->BN * kStageBytesK;
         for (int64_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) { ok = false; break; }
+          if (!mbar_wait(&empty[st], ph ^ 1u, L.err)) { ok = false; break; }
           uint8_t *xs = smem + (size_t)st * sbytes;
-          mbar_expect_tx(&full[st], sbytes);
-          tma_load_2d(xs, &mapX, &full[st], (int)(kb * BKE), row0, pol_x);
-          tma_load_2d(xs + xbytes, &mapY, &full[st], (int)(kb * BKE), 0, pol_y);
-          if (++st == a.nstages) { st = 0; ph ^= 1u; }
+          mbar_expect_tx(&full[st], tx);
+          tma_load_2d(xs, &p->mapX, &full[st], (int)(kb * BKE), row0, pol_x);
+          tma_load_2d(xs + xbytes, &p->mapY, &full[st], (int)(kb * BKE), 0, pol_y);
+          if (++st == L.nstages) { st = 0; ph ^= 1u; }
         }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id = idesc(BF16, 128, a.BN);
       int st = 0, buf = 0;
       uint32_t ph = 0, tph = 0;
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const int64_t sp = u % a.S;
-        const int64_t kb0 = sp * per_split, kb1 = min(total_kb, kb0 + per_split);
-        if (!mbar_wait(&tempty[buf], tph ^ 1u, a.err)) break;
+      for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
+        const GemmProblem *p = find_problem(one, group, L.nprob, u);
+        const int64_t v = u - p->unit0;
+        const int64_t sp = v % p->S;
+        const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
+        const uint32_t id = idesc(BF16, 128, p->BN);
+        if (!mbar_wait(&tempty[buf], tph ^ 1u, L.err)) break;
         tc_fence_after();
-        const uint32_t d0 = tbase + (uint32_t)(buf * 2 * a.BN);
-        const uint32_t d1 = d0 + (uint32_t)a.BN;
+        const uint32_t d0 = tbase + (uint32_t)(buf * 2 * L.BNmax);
+        const uint32_t d1 = d0 + (uint32_t)L.BNmax;
         for (int64_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(&full[st], ph, a.err)) { ok = false; break; }
+          if (!mbar_wait(&full[st], ph, L.err)) { ok = false; break; }
           tc_fence_after();
           const uint32_t xs = su32(smem + (size_t)st * sbytes);
           const uint32_t ys = xs + xbytes;
@@ -279,11 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma<BF16>(d1, sdesc(xs + 128 * kStageBytesK + off), bd, id, acc);
           }
           mma_commit(&empty[st]);
-          if (++st == a.nstages) { st = 0; ph ^= 1u; }
+          if (++st == L.nstages) { st = 0; ph ^= 1u; }
         }
         if (!ok) break;
         mma_commit(&tfull[buf]);
-        if (++buf == a.nbuf) { buf = 0; tph ^= 1u; }
+        if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
       }
     }
   } else {
@@ -291,42 +320,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     int buf = 0;
     uint32_t tph = 0;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const int64_t tile = u / a.S, sp = u % a.S;
-      if (!mbar_wait(&tfull[buf], tph, a.err)) break;
+    for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
+      const GemmProblem *p = find_problem(one, group, L.nprob, u);
+      const int64_t v = u - p->unit0;
+      const int64_t tile = v / p->S, sp = v % p->S;
+      const int64_t M = p->M;
+      const int k = p->k, BN = p->BN, pair = p->pair;
+      if (!mbar_wait(&tfull[buf], tph, L.err)) break;
       tc_fence_after();
-      float *Pp = a.P + sp * a.M * a.k;
+      float *Pp = p->P + sp * M * k;
 #pragma unroll 1
       for (int half = 0; half < 2; ++half) {
         const int64_t row = tile * kTileM + half * 128 + q * 32 + lane;
-        const uint32_t tcol = (uint32_t)(buf * 2 * a.BN + half * a.BN);
-        for (int c0 = 0; c0 < a.BN; c0 += 16) {
-          float v[16];
-          tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c0, v);
-          if (row < a.M) {
-            float *dst = Pp + row * a.k;
-            if (a.pair) {
+        const uint32_t tcol = (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float vv[16];
+          tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c0, vv);
+          if (row < M) {
+            float *dst = Pp + row * k;
+            if (pair) {
               const int o0 = c0 >> 1;
 #pragma unroll
               for (int j = 0; j < 8; ++j)
-                if (o0 + j < a.k) dst[o0 + j] = v[2 * j] + v[2 * j + 1];
+                if (o0 + j < k) dst[o0 + j] = vv[2 * j] + vv[2 * j + 1];
             } else {
 #pragma unroll
               for (int j = 0; j < 16; ++j)
-                if (c0 + j < a.k) dst[c0 + j] = v[j];
+                if (c0 + j < k) dst[c0 + j] = vv[j];
             }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&tempty[buf]);
-      if (++buf == a.nbuf) { buf = 0; tph ^= 1u; }
+      if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
     }
   }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tbase, a.tmem_cols);
+    tmem_dealloc(tbase, L.tmem_cols);
   }
 }
 
@@ -641,8 +674,6 @@ cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int
   return cudaGetLastError();
 }
 
-bool use_split(int k) { return 2 * k <= 256; }
-
 int prepare_blocks() { return num_sms() * 8; }
 
 cudaError_t launch_prepare(const float *A, int64_t m, int64_t n, int64_t lda, void *X, int64_t ldx,
@@ -697,45 +728,92 @@ cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda,
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
-                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
-                        cudaStream_t s) {
+bool fill_problem(GemmProblem *p, const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y,
+                  int k, int64_t ldy, bool split, bool bf16, float *parts, int S) {
   const int ny = split ? 2 * k : k;
   const int BN = bn_for(ny);
-  if (BN > 256) return cudaErrorInvalidValue;
-  CUtensorMap mx, my;
-  if (!make_map(&mx, X, bf16, M, K, ldx, kTileM)) return cudaErrorInvalidValue;
-  if (!make_map(&my, Y, bf16, ny, K, ldy, BN)) return cudaErrorInvalidValue;
-  GemmArgs a;
-  a.M = M;
-  a.K = K;
-  a.k = k;
-  a.BN = BN;
-  a.S = S;
-  a.pair = split ? 1 : 0;
-  a.nbuf = (4 * BN <= 512) ? 2 : 1;
+  if (BN > 256 || S < 1) return false;
+  if (!make_map(&p->mapX, X, bf16, M, K, ldx, kTileM)) return false;
+  if (!make_map(&p->mapY, Y, bf16, ny, K, ldy, BN)) return false;
+  const int64_t bke = kStageBytesK / (bf16 ? 2 : 4);
+  p->M = M;
+  p->K = K;
+  p->unit0 = 0;
+  p->total_kb = (K + bke - 1) / bke;
+  p->per_split = (p->total_kb + S - 1) / S;
+  p->P = parts;
+  p->k = k;
+  p->BN = BN;
+  p->S = S;
+  p->pair = split ? 1 : 0;
+  return true;
+}
+
+int64_t problem_units(const GemmProblem &p) { return ((p.M + kTileM - 1) / kTileM) * p.S; }
+
+bool launch_shape(GemmLaunch *L, int BNmax, int64_t units, int nprob, int *err) {
+  L->units = units;
+  L->nprob = nprob;
+  L->BNmax = BNmax;
+  L->nbuf = (4 * BNmax <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(a.nbuf * 2 * BN)) cols <<= 1;
-  a.tmem_cols = cols;
-  const size_t sbytes = (size_t)(kTileM + BN) * kStageBytesK;
+  while (cols < (uint32_t)(L->nbuf * 2 * BNmax)) cols <<= 1;
+  L->tmem_cols = cols;
+  const size_t sbytes = (size_t)(kTileM + BNmax) * kStageBytesK;
   const size_t budget = 225 * 1024 - 1024 - 256;
-  a.nstages = (int)(budget / sbytes);
-  if (a.nstages > 8) a.nstages = 8;
-  if (a.nstages < 2) return cudaErrorInvalidValue;
-  a.P = parts;
-  a.err = err;
-  const size_t smem = 1024 + (size_t)a.nstages * sbytes + 256;
-  const int64_t units = ((M + kTileM - 1) / kTileM) * S;
-  const int grid = (int)(units < num_sms() ? units : num_sms());
+  L->nstages = (int)(budget / sbytes);
+  if (L->nstages > 8) L->nstages = 8;
+  L->err = err;
+  return L->nstages >= 2;
+}
+
+cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, const GemmLaunch &L,
+                          bool bf16, cudaStream_t s) {
+  const size_t sbytes = (size_t)(kTileM + L.BNmax) * kStageBytesK;
+  const size_t smem = 1024 + (size_t)L.nstages * sbytes + 256;
+  const int grid = (int)(L.units < num_sms() ? L.units : num_sms());
+  if (grid < 1) return cudaSuccess;
   if (bf16) {
     cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemm_tc<true><<<grid, kThreads, smem, s>>>(mx, my, a);
+    k_gemm_tc<true><<<grid, kThreads, smem, s>>>(one, group, L);
   } else {
     cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemm_tc<false><<<grid, kThreads, smem, s>>>(mx, my, a);
+    k_gemm_tc<false><<<grid, kThreads, smem, s>>>(one, group, L);
   }
   g_launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
+                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
+                        cudaStream_t s) {
+  GemmProblem p;
+  if (!fill_problem(&p, X, M, K, ldx, Y, k, ldy, split, bf16, parts, S))
+    return cudaErrorInvalidValue;
+  GemmLaunch L;
+  if (!launch_shape(&L, p.BN, problem_units(p), 0, err)) return cudaErrorInvalidValue;
+  return launch_kernel(p, nullptr, L, bf16, s);
+}
+
+size_t problem_bytes() { return sizeof(GemmProblem); }
+
+bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int64_t ldx,
+                        const void *Y, int k, int64_t ldy, bool split, bool bf16, float *C,
+                        int64_t unit0, int64_t *units, int *BN) {
+  GemmProblem *p = reinterpret_cast<GemmProblem *>(host_dst);
+  if (!fill_problem(p, X, M, K, ldx, Y, k, ldy, split, bf16, C, 1)) return false;
+  p->unit0 = unit0;
+  *units = problem_units(*p);
+  *BN = p->BN;
+  return true;
+}
+
+cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
+                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s) {
+  GemmLaunch L;
+  if (!launch_shape(&L, BNmax, units, nprob, err)) return cudaErrorInvalidValue;
+  return launch_kernel(*reinterpret_cast<const GemmProblem *>(host_first),
+                       reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
 }
 
 cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s) {

@@ -46,6 +46,17 @@ cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const 
 // nearest TF32 (FP32 containers) or BF16: hi = round(x), lo = round(x - hi).
 cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,
                                    int64_t ldo, bool bf16, cudaStream_t s);
+// Grouped products (one launch for many problems, e.g. a batch of NMF
+// instances): each problem's descriptor is filled on the host into a
+// problem_bytes()-sized slot (64-byte aligned) of a host array that the
+// caller copies to device memory; unit0 numbers the problems' work units
+// consecutively (no K splits: each problem writes C directly).
+size_t problem_bytes();
+bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int64_t ldx,
+                        const void *Y, int k, int64_t ldy, bool split, bool bf16, float *C,
+                        int64_t unit0, int64_t *units, int *BN);
+cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
+                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s);
 // P = sum over s of parts[s] (len elements each), s ascending.
 cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s);
 

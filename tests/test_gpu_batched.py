@@ -1,0 +1,84 @@
+"""Batched ABPP (aunmf_run_batched): many uneven problems advanced together
+with one launch per phase, against the single-problem path and the oracle.
+
+Each problem is checked against aunmf_run on the same inputs (same
+arithmetic, but the single path may split long products differently, so the
+bar is 1e-5 in the relative residual) and against the FP64 oracle at the
+mixed-precision bar (1e-3)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1609_09154_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ax():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1609_09154_gb300 import aunmf
+
+    return aunmf.Handle()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+
+
+def batch(seed, count, lo=100, hi=700):
+    """Uneven problems: m, n uniform in [lo, hi], k from {8, 16, 32, 64},
+    planted rank k + noise."""
+    g = np.random.default_rng(seed)
+    probs = []
+    for i in range(count):
+        m, n = (int(x) for x in g.integers(lo, hi + 1, size=2))
+        k = int(g.choice([8, 16, 32, 64]))
+        A, _, _ = synth.dense_lowrank(m, n, k, seed=seed * 1000 + i)
+        _, H0 = synth.init_factors(m, n, k, seed=seed * 1000 + i)
+        probs.append((A.astype(np.float32).astype(np.float64), H0.astype(np.float32).astype(np.float64), k))
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_batched_matches_single_and_oracle(ax, prec):
+    probs = batch(11, 7)
+    As = [dev(A) for A, _, _ in probs]
+    H0s = [dev(H0) for _, H0, _ in probs]
+    ks = [k for _, _, k in probs]
+    Ws, Hs, rel, info = ax.run_batched(As, ks, 8, H0s, prec=prec)
+    assert info["bpp_nonconverged"] == 0 and info["bpp_numeric"] == 0
+    assert info["tuned_bpp_warps"] > 0 and info["tuned_bpp_rows"] > 0
+    for p, (A, H0, k) in enumerate(probs):
+        W1, H1, r1, _ = ax.run(As[p], k, "abpp", 8, dev(np.zeros((A.shape[0], k))), H0s[p],
+                               prec=prec)
+        assert np.abs(rel[p] - r1).max() <= 1e-5, (p, rel[p], r1)
+        ref = orc.nmf_run(A, k, "abpp", 8, None, H0)
+        assert np.abs(rel[p] - ref["relres"]).max() <= 1e-3
+        assert bool((Ws[p] >= 0).all()) and bool((Hs[p] >= 0).all())
+
+
+def test_batched_deterministic_graph_and_eager(ax):
+    probs = batch(12, 5)
+    As = [dev(A) for A, _, _ in probs]
+    H0s = [dev(H0) for _, H0, _ in probs]
+    ks = [k for _, _, k in probs]
+    W1, H1, r1, _ = ax.run_batched(As, ks, 6, H0s, use_graph=True)
+    W2, H2, r2, _ = ax.run_batched(As, ks, 6, H0s, use_graph=False)
+    assert np.array_equal(r1, r2)
+    for a, b in zip(W1 + H1, W2 + H2):
+        assert torch.equal(a, b)
+
+
+def test_batched_rejects_unsupported(ax):
+    from paper_1609_09154_gb300 import aunmf
+
+    A = dev(np.ones((50, 40)))
+    with pytest.raises(aunmf.AunmfError) as e:
+        ax.run_batched([A], [65], 2, [dev(np.ones((65, 40)))])
+    assert e.value.code == aunmf.E_INVAL
+    with pytest.raises(aunmf.AunmfError) as e:
+        ax.run_batched([A], [4], 2, [dev(np.ones((4, 40)))], prec="fp32")
+    assert e.value.code == aunmf.E_UNSUPPORTED
