@@ -39,6 +39,9 @@
  *      a backup counter of 3, single-index exchange (largest index) after
  *      that; the passive-set systems are solved through the normal equations
  *      by Cholesky, as the paper states.  Cold start (empty passive set).
+ *      An index whose Gram diagonal is <= 1e-12 of the largest one (a zero
+ *      column of the fixed factor, which ABPP can produce) is never made
+ *      passive: its x is 0, as the normal equations leave it undetermined.
  *   R5 (Sec. 6.2) the relative error is measured after both updates of an
  *      iteration, directly as ||A - WH||_F / ||A||_F.
  */
@@ -59,6 +62,9 @@
 
 /* relative tolerance of the active-set test y_i < -tau_i (reading R4) */
 #define BPP_YTOL 1e-11
+/* Gram diagonal (relative to the largest) below which an index is a zero
+   column and stays active (reading R4) */
+#define BPP_DEAD 1e-12
 
 /* ------------------------------------------------------------------------ */
 /* Input matrix: dense row-major or CSR.                                     */
@@ -284,8 +290,12 @@ int or_bpp_solve(const double *G, const double *r, int k, double *x, int max_ite
   double *L = (double *)malloc(sizeof(double) * (size_t)k * (size_t)k);
   if (!L) return OR_E_NOMEM;
   /* start: passive set empty, x = 0, y = G x - r = -r */
+  double gmax = 0.0;
+  for (int i = 0; i < k; ++i) gmax = G[i * k + i] > gmax ? G[i * k + i] : gmax;
+  char dead[1024]; /* zero columns of the fixed factor: kept active */
   for (int i = 0; i < k; ++i) {
     passive[i] = 0;
+    dead[i] = !(G[i * k + i] > BPP_DEAD * gmax);
     x[i] = 0.0;
     y[i] = -r[i];
     tau[i] = BPP_YTOL * fabs(r[i]);
@@ -295,7 +305,7 @@ int or_bpp_solve(const double *G, const double *r, int k, double *x, int max_ite
     /* infeasible set V: passive with x < 0, active with y < 0 (Eq. KKT) */
     int nv = 0, vmax = -1;
     for (int i = 0; i < k; ++i) {
-      const int bad = passive[i] ? (x[i] < 0.0) : (y[i] < -tau[i]);
+      const int bad = passive[i] ? (x[i] < 0.0) : (!dead[i] && y[i] < -tau[i]);
       if (bad) { ++nv; vmax = i; }
     }
     if (nv == 0) { rc = it; break; }
@@ -305,11 +315,11 @@ int or_bpp_solve(const double *G, const double *r, int k, double *x, int max_ite
       beta = nv;
       alpha = 3;
       for (int i = 0; i < k; ++i)
-        if (passive[i] ? (x[i] < 0.0) : (y[i] < -tau[i])) passive[i] = !passive[i];
+        if (passive[i] ? (x[i] < 0.0) : (!dead[i] && y[i] < -tau[i])) passive[i] = !passive[i];
     } else if (alpha >= 1) { /* no progress yet: full exchange, spend backup */
       alpha -= 1;
       for (int i = 0; i < k; ++i)
-        if (passive[i] ? (x[i] < 0.0) : (y[i] < -tau[i])) passive[i] = !passive[i];
+        if (passive[i] ? (x[i] < 0.0) : (!dead[i] && y[i] < -tau[i])) passive[i] = !passive[i];
     } else { /* backup rule: exchange only the largest infeasible index */
       passive[vmax] = !passive[vmax];
     }

@@ -12,6 +12,10 @@ namespace aunmf {
 namespace bpp {
 
 constexpr double kBppYTol = 1e-11;
+// An index whose Gram diagonal is <= kDead of the largest (a zero column of
+// the fixed factor, which ABPP can produce) never becomes passive: the normal
+// equations leave its value undetermined and it stays 0.
+constexpr double kDead = 1e-12;
 // G^{-1} is used for the passive-set solves only when cond_1(G) is below
 // this (FP64 solves through it then keep at least ~8 digits)
 constexpr double kQMaxCond = 1e8;
@@ -152,6 +156,7 @@ __device__ __forceinline__ void gram_inverse_block(const float *__restrict__ G32
 struct BppWarp {
   const double *G, *Q;
   const float *Gabs;
+  double dead_below;  // kDead * max diagonal of G
   bool have_q;
   double *L, *v, *rs;
   int *Fl, *Bl;
@@ -177,6 +182,9 @@ __device__ __forceinline__ BppWarp bpp_stage(const float *__restrict__ G32,
   w.G = G;
   w.Q = Q;
   w.Gabs = Gabs;
+  float gmax = 0.f;
+  for (int i = 0; i < k; ++i) gmax = fmaxf(gmax, G32[i * k + i]);
+  w.dead_below = kDead * (double)gmax;
   w.have_q = *q_ok != 0;
   w.L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
   w.v = w.L + (size_t)lay.kh * lay.ldl;  // small system's right-hand side, then x_F
@@ -209,14 +217,15 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
     int kh;
   } lay{w.kh};
     double rr[KT], x[KT], y[KT], tau[KT];
-    bool pas[KT];
+    bool pas[KT], dead[KT];
     bool any = false;
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
       rr[t] = j < k ? (double)R[row * k + j] : 0.0;
       if (j < k) rs[j] = rr[t];
-      pas[t] = warm && j < k && X[row * k + j] > 0.f;
+      dead[t] = !(j < k && G[j * k + j] > w.dead_below);
+      pas[t] = warm && !dead[t] && X[row * k + j] > 0.f;
       any |= pas[t];
       x[t] = 0.0;
       y[t] = -rr[t];
@@ -326,7 +335,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
         const int j = lane + 32 * t;
-        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (y[t] < -tau[t]));
+        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (!dead[t] && y[t] < -tau[t]));
         bal[t] = __ballot_sync(0xffffffffu, inf[t]);
         nv += __popc(bal[t]);
       }
@@ -373,13 +382,16 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
   const int lane = threadIdx.x & 31;
   const int ldl = k | 1;
   const unsigned lt_mask = (1u << lane) - 1u;
+  double gmax = 0.0;
+  for (int i = 0; i < k; ++i) gmax = fmax(gmax, G[i * k + i]);
     double rr[KT], x[KT], y[KT], tau[KT];
-    bool pas[KT];
+    bool pas[KT], dead[KT];
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
       rr[t] = j < k ? (double)R[row * k + j] : 0.0;
       if (j < k) rs[j] = rr[t];
+      dead[t] = !(j < k && G[j * k + j] > kDead * gmax);
       pas[t] = false;
       x[t] = 0.0;
       y[t] = -rr[t];
@@ -395,7 +407,7 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
         const int j = lane + 32 * t;
-        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (y[t] < -tau[t]));
+        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (!dead[t] && y[t] < -tau[t]));
         bal[t] = __ballot_sync(0xffffffffu, inf[t]);
         nv += __popc(bal[t]);
       }

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256)
       const int tt = tb + threadIdx.x;
       const bool act = tt < ntiles;
       const int ti = act ? tt / nt : 0, tj = act ? tt % nt : 0;
-      float acc[4][4] = {};
+      double acc[4][4] = {};  // FP64 sum of FP32 32-row sums
       for (int64_t c0 = I.r0; c0 < I.r1; c0 += 32) {
         const int nr = (int)min((int64_t)32, I.r1 - c0);
         __syncthreads();
@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256)
           sX[idx] = (rr < nr && cc < k) ? X[(c0 + rr) * k + cc] : 0.f;
         }
         __syncthreads();
-        if (act)
+        if (act) {
+          float part[4][4] = {};
           for (int rr = 0; rr < nr; ++rr) {
             float av[4], bv[4];
 #pragma unroll
@@ -222,8 +223,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(av[a], bv[c], acc[a][c]);
+              for (int c = 0; c < 4; ++c) part[a][c] = fmaf(av[a], bv[c], part[a][c]);
           }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] += (double)part[a][c];
+        }
       }
       if (act)
 #pragma unroll
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int i = 4 * ti + a, j = 4 * tj + c;
-            if (i < k && j < k) out[i * k + j] = acc[a][c];
+            if (i < k && j < k) out[i * k + j] = (float)acc[a][c];
           }
     }
   }

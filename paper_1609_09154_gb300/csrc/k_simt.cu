@@ -15,7 +15,8 @@ namespace aunmf {
 // ------------------------------------------------------------------ Gram
 // Block b accumulates X^T X over rows [b*chunk, (b+1)*chunk) into
 // partials[b] (k x k).  Each thread owns a 4x4 tile of G; rows are staged in
-// shared memory 32 at a time.
+// shared memory 32 at a time, each 32-row sum is taken in FP32 and added in
+// FP64 (the residual's expansion <W^T W, H H^T> needs the Grams to ~1e-7).
 namespace {
 constexpr int kGramRows = 32;
 constexpr int kGramThreads = 256;
@@ -33,11 +34,11 @@ __global__ void __launch_bounds__(kGramThreads)
     const int t = tb + threadIdx.x;
     const bool act = t < ntiles;
     const int ti = act ? t / nt : 0, tj = act ? t % nt : 0;
-    float acc[4][4];
+    double acc[4][4];  // FP64 sum of the FP32 sums of each 32-row chunk
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
     for (int64_t c0 = r0; c0 < r1; c0 += kGramRows) {
       const int nr = (int)min((int64_t)kGramRows, r1 - c0);
       __syncthreads();
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kGramThreads)
       }
       __syncthreads();
       if (act) {
+        float part[4][4] = {};
         for (int rr = 0; rr < nr; ++rr) {
           const float4 a = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * ti]);
           const float4 b = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * tj]);
@@ -54,8 +56,12 @@ __global__ void __launch_bounds__(kGramThreads)
 #pragma unroll
           for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+            for (int q = 0; q < 4; ++q) part[p][q] = fmaf(av[p], bv[q], part[p][q]);
         }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += (double)part[p][q];
       }
     }
     if (act) {
@@ -64,7 +70,7 @@ __global__ void __launch_bounds__(kGramThreads)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int i = 4 * ti + p, j = 4 * tj + q;
-          if (i < k && j < k) out[i * k + j] = acc[p][q];
+          if (i < k && j < k) out[i * k + j] = (float)acc[p][q];
         }
     }
   }

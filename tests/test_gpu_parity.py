@@ -163,6 +163,25 @@ def test_nls_bpp_kkt_and_bruteforce_small(ax):
             assert_bpp(X[r], xr)
 
 
+def test_nls_bpp_zero_column(ax):
+    """A zero column of C (zero Gram diagonal): that entry stays 0 (reading
+    R4) and the rest matches the oracle."""
+    g = np.random.default_rng(8)
+    for k in (5, 40):
+        C = g.random((3 * k, k))
+        C[:, k // 2] = 0.0
+        B = g.random((3 * k, 64))
+        G = (C.T @ C).astype(np.float32).astype(np.float64)
+        R = (C.T @ B).T.astype(np.float32).astype(np.float64)
+        X, piv, nc = ax.nls_bpp(dev(G), dev(R))
+        X = host(X)
+        assert nc == 0 and np.all(X[:, k // 2] == 0.0)
+        for r in range(R.shape[0]):
+            xr, rc = orc.bpp_solve(G, R[r])
+            assert rc >= 0
+            assert_bpp(X[r], xr)
+
+
 def test_relres_step(ax):
     A, W, H = problem(433, 377, 12, seed=9)
     got = ax.relres(dev(A), dev(W), dev(H))

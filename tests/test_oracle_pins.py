@@ -260,10 +260,30 @@ def test_bpp_updates_are_rowwise_and_columnwise_nnls():
         np.testing.assert_allclose(H[:, c], nnls(W0, A[:, c])[0], rtol=1e-8, atol=1e-10)
 
 
-def test_bpp_singular_gram_reports_error():
-    G = np.zeros((3, 3))
-    x, rc = orc.bpp_solve(G, np.array([1.0, 1.0, 1.0]))
+def test_bpp_indefinite_gram_reports_error():
+    """A Gram matrix that is not positive semidefinite has no NLS problem
+    behind it: the passive-set Cholesky meets a non-positive pivot."""
+    G = np.array([[1.0, 2.0], [2.0, 1.0]])
+    x, rc = orc.bpp_solve(G, np.array([1.0, 1.0]))
     assert rc == orc.E_NUMERIC
+
+
+def test_bpp_zero_column_stays_active():
+    """Reading R4: a zero column of C (zero Gram diagonal) leaves its x
+    undetermined; the index stays active (x = 0) and the rest is the NNLS
+    solution of the other columns (scipy NNLS on C agrees)."""
+    from scipy.optimize import nnls
+
+    g = np.random.default_rng(3)
+    C = g.random((9, 4))
+    C[:, 2] = 0.0
+    b = g.random(9)
+    G, r = C.T @ C, C.T @ b
+    x, rc = orc.bpp_solve(G, r)
+    assert rc >= 0 and x[2] == 0.0
+    np.testing.assert_allclose(x, nnls(C, b)[0], rtol=1e-9, atol=1e-12)
+    y = G @ x - r
+    assert np.all(y >= -1e-12) and np.all(np.abs(x * y) <= 1e-12)
 
 
 # ------------------------------------------------------------------ whole runs
