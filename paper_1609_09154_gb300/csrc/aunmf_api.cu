@@ -69,7 +69,7 @@ int fail_cuda(aunmf_handle *h, cudaError_t e, const char *what) {
 
 // FP64 partial sums: residual partials, and the layout pass's per-block partials
 size_t dpart_bytes(const aunmf_handle *h) {
-  const size_t a = (size_t)h->n_dparts + 8, b = (size_t)tc::prepare_blocks();
+  const size_t a = (size_t)h->n_dparts + 8, b = 2 * (size_t)tc::prepare_blocks();
   return sizeof(double) * (a > b ? a : b);
 }
 
@@ -331,7 +331,7 @@ int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   c.ldx = tc::copy_ld(n);
   ENS_TC(h, h->Ax, esz * (size_t)m * c.ldx);
   ENS_TC(h, h->dpart, dpart_bytes(h));
-  ENS_TC(h, h->n2a, sizeof(double));
+  ENS_TC(h, h->n2a, 2 * sizeof(double));
   c.Ax = h->Ax.p;
   c.dpart = P<double>(h->dpart);
   if (!c.n2a) c.n2a = P<double>(h->n2a);
@@ -434,7 +434,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   ENS(h, h->GW, sizeof(float) * k * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
   ENS(h, h->dpart, dpart_bytes(h));
-  ENS(h, h->n2a, sizeof(double));
+  ENS(h, h->n2a, 2 * sizeof(double));
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->relres, sizeof(double) * (iters > 0 ? iters : 1));
   ENS(h, h->last, sizeof(double));
@@ -746,7 +746,7 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   ENS(h, h->GW, sizeof(float) * k * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
   ENS(h, h->dpart, dpart_bytes(h));
-  ENS(h, h->n2a, sizeof(double));
+  ENS(h, h->n2a, 2 * sizeof(double));
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->last, sizeof(double));
   float *Ht = P<float>(h->Ht), *PHt = P<float>(h->PHt);
@@ -793,7 +793,7 @@ int loss_setup(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, co
   ENS(h, h->GW, sizeof(float) * k * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
   ENS(h, h->dpart, dpart_bytes(h));
-  ENS(h, h->n2a, sizeof(double));
+  ENS(h, h->n2a, 2 * sizeof(double));
   c.A = A;
   c.k = k;
   c.prec = prec;
@@ -874,11 +874,27 @@ int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
 namespace {
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Host bytes starting on a 64-byte boundary (tensor-map descriptors).
+struct alignas(64) Block64 {
+  uint8_t b[64];
+};
+struct DescBytes {
+  std::vector<Block64> v;
+  size_t n = 0;
+  void assign(size_t bytes, uint8_t) {
+    v.assign((bytes + 63) / 64, Block64{});
+    n = bytes;
+  }
+  uint8_t *data() { return reinterpret_cast<uint8_t *>(v.data()); }
+  size_t size() const { return n; }
+  uint8_t &operator[](size_t i) { return data()[i]; }
+};
+
 struct BatchPlan {
   std::vector<batched::BInst> inst;
   std::vector<batched::Item> rows_w, rows_h, gram_w, gram_h, dot;
   std::vector<int64_t> tiles_a, tiles_fh, tiles_fw, rows_mx;
-  std::vector<uint8_t> probs_aht, probs_wta;  // grouped GEMM descriptors
+  DescBytes probs_aht, probs_wta;  // grouped GEMM descriptors
   int64_t units_aht = 0, units_wta = 0;
   int bn_aht = 16, bn_wta = 16;
   int kmax = 1;
@@ -975,14 +991,14 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     o_[11] = take(sizeof(double) * kk);                 // Q
     o_[12] = take(sizeof(int));                         // q_ok
     o_[13] = take(mx);                                  // redo
-    o_[14] = take(sizeof(double));                      // n2a
+    o_[14] = take(2 * sizeof(double));                  // n2a
     o_[15] = take(sizeof(double) * b.nr);               // residual partials
   }
   std::vector<int64_t> tiles_prep;
   pl.tiles_a = prefix_of(pl.inst, [](const batched::BInst &b) {
     return ((b.m + 31) / 32) * ((b.n + 31) / 32);
   });
-  const size_t tsq_off = take(sizeof(double) * (size_t)pl.tiles_a[count]);
+  const size_t tsq_off = take(2 * sizeof(double) * (size_t)pl.tiles_a[count]);
   ENS(h, h->batch, top);
   uint8_t *base = P<uint8_t>(h->batch);
   for (int p = 0; p < count; ++p) {

@@ -30,7 +30,7 @@ struct BInst {
   double *Q;              // G^{-1} of the current update (FP64)
   int *q_ok;
   uint8_t *redo;          // rows flagged for the direct BPP fallback
-  double *n2a;            // ||A||^2
+  double *n2a;            // {||A||^2, 2 <round(A) - A, A>}
   double *rpart;          // residual partials
   double *relres;         // per-iteration relative residual (device)
 };

@@ -62,8 +62,9 @@ __device__ __forceinline__ double block_sum(double v, double *ws) {
 }
 
 // ---------------------------------------------------------------- setup
-// Rounded copy Ax, rounded transposed copy At and per-tile sums of squares of
-// each problem's A, 32 x 32 tiles numbered across problems by tile_prefix.
+// Rounded copy Ax, rounded transposed copy At and per-tile sums of a_ij^2
+// and of a_ij (round(a_ij) - a_ij) of each problem's A (tile_sq[2 g],
+// tile_sq[2 g + 1]), 32 x 32 tiles numbered across problems by tile_prefix.
 template <class T>
 __global__ void __launch_bounds__(256)
     g_prepare(const BInst *__restrict__ P, const int64_t *__restrict__ tile_prefix, int count,
@@ -79,39 +80,52 @@ __global__ void __launch_bounds__(256)
     const int64_t r0 = (tl / tcn) * 32, c0 = (tl % tcn) * 32;
     T *X = reinterpret_cast<T *>(b.Ax);
     T *Xt = reinterpret_cast<T *>(b.At);
-    float sq = 0.f;  // this thread's 4 squares of the tile, in FP32
+    float sq = 0.f, sd = 0.f;  // this thread's 4 terms of each sum, in FP32
     __syncthreads();
     for (int y = threadIdx.x >> 5; y < 32; y += 8) {
       const int64_t r = r0 + y, c = c0 + (threadIdx.x & 31);
       float v = 0.f;
       if (r < b.m && c < b.n) {
         v = b.A[r * b.lda + c];
-        X[r * b.ldx + c] = rnd<T>(v);
+        const T rv = rnd<T>(v);
+        X[r * b.ldx + c] = rv;
+        sd = fmaf(v, wid<T>(rv) - v, sd);
       }
       sq = fmaf(v, v, sq);
       t[y][threadIdx.x & 31] = v;
     }
-    const double acc = (double)sq;
+    const double acc = (double)sq, acc_d = (double)sd;
     __syncthreads();
     for (int y = threadIdx.x >> 5; y < 32; y += 8) {
       const int64_t c = c0 + y, r = r0 + (threadIdx.x & 31);
       if (r < b.m && c < b.n) Xt[c * b.ldat + r] = rnd<T>(t[threadIdx.x & 31][y]);
     }
     const double s = block_sum(acc, ws);
-    if (threadIdx.x == 0) tile_sq[g] = s;
+    const double d = block_sum(acc_d, ws);
+    if (threadIdx.x == 0) {
+      tile_sq[2 * g] = s;
+      tile_sq[2 * g + 1] = d;
+    }
   }
 }
 
-// ||A_p||^2 = sum of its tiles' partials in tile order (one block per problem).
+// n2a = {||A_p||^2, 2 <round(A_p) - A_p, A_p>}: sums of the problem's tile
+// partials in tile order (one block per problem).
 __global__ void g_norm_final(const BInst *__restrict__ P, const int64_t *__restrict__ tile_prefix,
                              const double *__restrict__ tile_sq) {
   __shared__ double ws[8];
   const int p = blockIdx.x;
-  double s = 0.0;
-  for (int64_t g = tile_prefix[p] + threadIdx.x; g < tile_prefix[p + 1]; g += blockDim.x)
-    s += tile_sq[g];
+  double s = 0.0, d = 0.0;
+  for (int64_t g = tile_prefix[p] + threadIdx.x; g < tile_prefix[p + 1]; g += blockDim.x) {
+    s += tile_sq[2 * g];
+    d += tile_sq[2 * g + 1];
+  }
   s = block_sum(s, ws);
-  if (threadIdx.x == 0) *P[p].n2a = s;
+  d = block_sum(d, ws);
+  if (threadIdx.x == 0) {
+    P[p].n2a[0] = s;
+    P[p].n2a[1] = 2.0 * d;
+  }
 }
 
 // Ht = H0^T (n x k) and W = 0 for each problem (ABPP starts from H only).
@@ -368,8 +382,10 @@ __global__ void g_dot_partial(const BInst *__restrict__ P, const Item *__restric
   }
 }
 
-// relres[iter] = sqrt(max(0, ||A||^2 - 2 <P, Ht> + <GW, GH>) / ||A||^2), FP64,
-// one block per problem; the iteration index is read from the counters.
+// relres[iter] = sqrt(max(0, ||A||^2 + d - 2 <P, Ht> + <GW, GH>) / ||A||^2),
+// FP64, with d = 2 <round(A) - A, A> correcting for the rounded copy the
+// products read (as in the single-problem residual); one block per problem;
+// the iteration index is read from the counters.
 __global__ void g_relres_final(const BInst *__restrict__ P, DevCounters *ctr, int iters) {
   __shared__ double ws[8];
   const BInst &b = P[blockIdx.x];
@@ -381,8 +397,8 @@ __global__ void g_relres_final(const BInst *__restrict__ P, DevCounters *ctr, in
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)b.GW[e], (double)b.GH[e], quad);
   quad = block_sum(quad, ws);
   if (threadIdx.x == 0) {
-    const double a2 = *b.n2a;
-    double r2 = a2 - 2.0 * cross + quad;
+    const double a2 = b.n2a[0];
+    double r2 = (a2 + b.n2a[1]) - 2.0 * cross + quad;
     if (r2 < 0.0) r2 = 0.0;
     const long long t = ctr->iter;
     if (t < iters) b.relres[t] = a2 > 0.0 ? sqrt(r2 / a2) : 0.0;

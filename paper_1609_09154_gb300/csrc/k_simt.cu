@@ -383,12 +383,16 @@ __global__ void k_norm2_vec_partial(const float *__restrict__ v, int64_t len,
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// out[0] = ||A||^2 from the partials; out[1] = 0: the products read A itself.
 __global__ void k_sum_partials(const double *__restrict__ partials, int nparts,
                                double *__restrict__ out) {
   double s = 0.0;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += partials[b];
   s = block_sum_d(s);
-  if (threadIdx.x == 0) *out = s;
+  if (threadIdx.x == 0) {
+    out[0] = s;
+    out[1] = 0.0;
+  }
 }
 
 __global__ void k_dot_partial(const float *__restrict__ P, const float *__restrict__ Q,
@@ -401,6 +405,15 @@ __global__ void k_dot_partial(const float *__restrict__ P, const float *__restri
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// relres = sqrt(max(0, ||A||^2 + d - 2 <P, Ht> + <GW, GH>) / ||A||^2), FP64
+// (Sec. 5, relative error; trace form).  When P was formed from a rounded
+// copy A~ of A (TF32 / BF16 products), <P, Ht> = <A~, W H> and
+//   ||A - WH||^2 = ||A||^2 - 2 <A~, WH> + ||WH||^2 + 2 <A~ - A, WH>;
+// the last term is taken as d = n2a[1] = 2 <A~ - A, A> (WH ~ A), which is
+// off by 2 <A~ - A, A - WH>, a sum of rounding errors that do not correlate
+// with the fit residual.  Without d, the mean of the rounding errors (not
+// zero on real value distributions: -8e-6 relative for BF16 on uniform
+// low-rank data) would bias the reported residual by ~1e-3 at relres ~1e-2.
 __global__ void k_relres_final(const double *__restrict__ partials, int nparts,
                                const float *__restrict__ GW, const float *__restrict__ GH, int k,
                                const double *__restrict__ n2a, double *__restrict__ relres,
@@ -412,8 +425,8 @@ __global__ void k_relres_final(const double *__restrict__ partials, int nparts,
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
   quad = block_sum_d(quad);
   if (threadIdx.x == 0) {
-    const double a2 = *n2a;
-    double r2 = a2 - 2.0 * cross + quad;
+    const double a2 = n2a[0];
+    double r2 = (a2 + n2a[1]) - 2.0 * cross + quad;
     if (r2 < 0.0) r2 = 0.0;
     const double rr = a2 > 0.0 ? sqrt(r2 / a2) : 0.0;
     if (!isfinite(rr)) ctr->nonfinite += 1;
@@ -422,7 +435,8 @@ __global__ void k_relres_final(const double *__restrict__ partials, int nparts,
     if (last) *last = rr;
   }
 }
-// loss = 0.5 (||A||^2 - 2 <P, Ht> + <GW, GH>), FP64 (not clamped).
+// loss = 0.5 (||A||^2 + d - 2 <P, Ht> + <GW, GH>), FP64 (not clamped); d as
+// for the residual.
 __global__ void k_loss_final(const double *__restrict__ partials, int nparts,
                              const float *__restrict__ GW, const float *__restrict__ GH, int k,
                              const double *__restrict__ n2a, double *__restrict__ loss) {
@@ -432,7 +446,7 @@ __global__ void k_loss_final(const double *__restrict__ partials, int nparts,
   double quad = 0.0;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
   quad = block_sum_d(quad);
-  if (threadIdx.x == 0) *loss = 0.5 * (*n2a - 2.0 * cross + quad);
+  if (threadIdx.x == 0) *loss = 0.5 * ((n2a[0] + n2a[1]) - 2.0 * cross + quad);
 }
 }  // namespace
 

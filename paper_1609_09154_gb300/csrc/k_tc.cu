@@ -14,10 +14,22 @@
 //   warp 1     owns the TMEM allocation; one thread issues tcgen05.mma
 //              (two M = 128 MMAs per K step share the Y tile) and commits
 //              stage releases / accumulator-ready to mbarriers
-//   warps 2-5  epilogue: tcgen05.ld of the FP32 accumulators (one row per
-//              thread per 128-row half), stores to the split's partial C
-// Accumulators are double-buffered in TMEM (2 x 2 x BN columns) when
-// BN <= 128 so that a tile's epilogue overlaps the next tile's main loop.
+//   warps 2-9  epilogue: tcgen05.ld of the FP32 accumulators (one row per
+//              thread), drained into an FP32 accumulator in shared memory,
+//              then stored to the split's partial C
+// The tensor core adds each MMA's result into its FP32 accumulator with a
+// truncating rounding, so a long accumulation chain drifts toward zero: the
+// relative bias grows linearly with the number of MMAs in the chain
+// (-1e-6 after ~50, -1e-4 after ~5000 on nonnegative data).  Each work unit
+// therefore restarts the TMEM accumulator every `chunk_kb` K blocks and the
+// epilogue adds the chunk into its own accumulator with round-to-nearest
+// FP32 additions, whose errors carry no bias.  The residual's trace form
+// (Sec. 5, relative error) takes the difference of numbers near ||A||^2 and
+// needs that: a bias of e in W^T A moves the reported relres by ~e / relres.
+// Chunk accumulators are double-buffered in TMEM (2 x 2 x BN columns) when
+// BN <= 128 so that draining one chunk overlaps the next chunk's MMAs; eight
+// epilogue warps (two per TMEM lane quarter, one per 128-row half) keep a
+// drain shorter than a chunk.
 // Work unit = (256-row tile, K split); splits are summed afterwards in a
 // fixed order, so results do not depend on scheduling.
 //
@@ -36,8 +48,19 @@ namespace {
 
 constexpr int kTileM = 256;          // rows of X per work unit (2 x M=128 MMAs)
 constexpr int kStageBytesK = 128;    // K extent of one stage in bytes (one 128B swizzle row)
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+#ifndef AUNMF_TC_CHUNK_KB
+#define AUNMF_TC_CHUNK_KB 2
+#endif
+// K blocks (4 MMAs each) per TMEM accumulation chain: with the accumulator in
+// shared memory, and when it is added into P in global memory.  Measured
+// bias of <W^T A, H> (relative, nonnegative data): 4 K blocks -6e-7 (TF32)
+// and -2.5e-7 (BF16), 2 K blocks -2.5e-7 and -1e-7, 1 K block -1.1e-7 and
+// -4e-8; the drain of 256 x BN accumulators hides behind a chunk of >= 2
+// K blocks at the HBM rate (2: ~5% slower than 4 on 96000 x 64000, k = 50).
+constexpr int kChunkKB = AUNMF_TC_CHUNK_KB;
+constexpr int kChunkKBGlobal = 4 * AUNMF_TC_CHUNK_KB;
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -136,8 +159,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// 16 columns of the thread's TMEM lane into r[0..15] without waiting; the
+// values may be read only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t *r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -145,9 +169,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+// Waits for the thread's outstanding tcgen05.ld; the empty volatile asm per
+// register orders every later use of r[0..n) after the wait.
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[N]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
 }
 
 // Shared-memory matrix descriptor for a K-major tile in the canonical
@@ -197,6 +226,10 @@ struct GemmLaunch {
   int nstages;
   int nbuf;            // TMEM accumulator buffers (1 or 2)
   uint32_t tmem_cols;  // power of two >= nbuf * 2 * BNmax
+  int chunk_kb;        // K blocks per TMEM accumulation chain
+  int acc_ld;          // row stride (floats, odd, >= BN/2 for pair problems and BN
+                       // otherwise) of the shared-memory accumulator, 256 rows;
+                       // 0: chunks are added into P itself
   int *err;
 };
 
@@ -224,7 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const uint32_t xbytes = kTileM * kStageBytesK;
   const uint32_t sbytes = xbytes + (uint32_t)L.BNmax * kStageBytesK;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)L.nstages * sbytes);
+  float *acc_s = L.acc_ld ? reinterpret_cast<float *>(smem + (size_t)L.nstages * sbytes) : nullptr;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)L.nstages * sbytes +
+                                                (size_t)kTileM * L.acc_ld * sizeof(float));
   uint64_t *full = bars;
   uint64_t *empty = bars + L.nstages;
   uint64_t *tfull = bars + 2 * L.nstages;
@@ -240,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -290,70 +325,135 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t sp = v % p->S;
         const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
         const uint32_t id = idesc(BF16, 128, p->BN);
-        if (!mbar_wait(&tempty[buf], tph ^ 1u, L.err)) break;
-        tc_fence_after();
-        const uint32_t d0 = tbase + (uint32_t)(buf * 2 * L.BNmax);
-        const uint32_t d1 = d0 + (uint32_t)L.BNmax;
-        for (int64_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(&full[st], ph, L.err)) { ok = false; break; }
+        for (int64_t cb0 = kb0; cb0 < kb1 && ok; cb0 += L.chunk_kb) {
+          const int64_t cb1 = min(kb1, cb0 + (int64_t)L.chunk_kb);
+          if (!mbar_wait(&tempty[buf], tph ^ 1u, L.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t xs = su32(smem + (size_t)st * sbytes);
-          const uint32_t ys = xs + xbytes;
+          const uint32_t d0 = tbase + (uint32_t)(buf * 2 * L.BNmax);
+          const uint32_t d1 = d0 + (uint32_t)L.BNmax;
+          for (int64_t kb = cb0; kb < cb1; ++kb) {
+            if (!mbar_wait(&full[st], ph, L.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t xs = su32(smem + (size_t)st * sbytes);
+            const uint32_t ys = xs + xbytes;
 #pragma unroll
-          for (int kk = 0; kk < BKE / KPM; ++kk) {
-            const uint32_t off = (uint32_t)(kk * KPM * ESZ);
-            const uint64_t bd = sdesc(ys + off);
-            const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-            mma<BF16>(d0, sdesc(xs + off), bd, id, acc);
-            mma<BF16>(d1, sdesc(xs + 128 * kStageBytesK + off), bd, id, acc);
+            for (int kk = 0; kk < BKE / KPM; ++kk) {
+              const uint32_t off = (uint32_t)(kk * KPM * ESZ);
+              const uint64_t bd = sdesc(ys + off);
+              const uint32_t acc = (kb > cb0 || kk > 0) ? 1u : 0u;
+              mma<BF16>(d0, sdesc(xs + off), bd, id, acc);
+              mma<BF16>(d1, sdesc(xs + 128 * kStageBytesK + off), bd, id, acc);
+            }
+            mma_commit(&empty[st]);
+            if (++st == L.nstages) { st = 0; ph ^= 1u; }
           }
-          mma_commit(&empty[st]);
-          if (++st == L.nstages) { st = 0; ph ^= 1u; }
+          if (!ok) break;
+          mma_commit(&tfull[buf]);
+          if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
         }
-        if (!ok) break;
-        mma_commit(&tfull[buf]);
-        if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
-    const int q = warp & 3;
+    // ---------------- epilogue: warps 2..9; warp w drains TMEM lane quarter
+    // q = w % 4 of accumulator half (w - 2) / 4.  Row rl = half * 128 +
+    // q * 32 + lane of the unit belongs to one thread for every chunk.
+    // TMEM is read in groups of 64 columns (one wait per group) up to BN
+    // rounded up to 64; shared accumulator rows are padded to match, so the
+    // columns past BN (never copied out) need no guard.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int rl = half * 128 + q * 32 + lane;
+    float *arow = acc_s ? acc_s + (size_t)rl * L.acc_ld : nullptr;
     int buf = 0;
     uint32_t tph = 0;
-    for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
       const GemmProblem *p = find_problem(one, group, L.nprob, u);
       const int64_t v = u - p->unit0;
       const int64_t tile = v / p->S, sp = v % p->S;
+      const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
       const int64_t M = p->M;
       const int k = p->k, BN = p->BN, pair = p->pair;
-      if (!mbar_wait(&tfull[buf], tph, L.err)) break;
-      tc_fence_after();
+      const int W = (BN + 63) & ~63;
+      const int64_t row = tile * kTileM + rl;
       float *Pp = p->P + sp * M * k;
-#pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-        const int64_t row = tile * kTileM + half * 128 + q * 32 + lane;
-        const uint32_t tcol = (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          float vv[16];
-          tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c0, vv);
-          if (row < M) {
+      const bool live = row < M;
+      bool first = true;
+      for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
+        if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr =
+            tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
+        for (int g0 = 0; g0 < W; g0 += 64) {
+          uint32_t r[64];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) tmem_ld16_async(taddr + (uint32_t)(g0 + 16 * t), r + 16 * t);
+          tmem_wait_ld(r);
+          if (arow) {
+            if (pair) {
+              // C_i = acc_2i + acc_2i+1 (hi and lo parts of the factor)
+              float *d = arow + (g0 >> 1);
+              float x[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                x[j] = __uint_as_float(r[2 * j]) + __uint_as_float(r[2 * j + 1]);
+              if (!first) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) x[j] += d[j];
+              }
+#pragma unroll
+              for (int j = 0; j < 32; ++j) d[j] = x[j];
+            } else {
+              float *d = arow + g0;
+              float x[64];
+#pragma unroll
+              for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(r[j]);
+              if (!first) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) x[j] += d[j];
+              }
+#pragma unroll
+              for (int j = 0; j < 64; ++j) d[j] = x[j];
+            }
+          } else if (live) {
+            // accumulate in P itself: per-element guards (k is not padded)
             float *dst = Pp + row * k;
             if (pair) {
-              const int o0 = c0 >> 1;
+              const int o0 = g0 >> 1;
 #pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (o0 + j < k) dst[o0 + j] = vv[2 * j] + vv[2 * j + 1];
+              for (int j = 0; j < 32; ++j)
+                if (o0 + j < k) {
+                  const float x = __uint_as_float(r[2 * j]) + __uint_as_float(r[2 * j + 1]);
+                  dst[o0 + j] = first ? x : dst[o0 + j] + x;
+                }
             } else {
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (c0 + j < k) dst[c0 + j] = vv[j];
+              for (int j = 0; j < 64; ++j)
+                if (g0 + j < k) {
+                  const float x = __uint_as_float(r[j]);
+                  dst[g0 + j] = first ? x : dst[g0 + j] + x;
+                }
             }
           }
         }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
+        first = false;
       }
-      tc_fence_before();
-      mbar_arrive(&tempty[buf]);
-      if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
+      if (!ok) break;
+      if (arow || first) {
+        // copy the warp's 32 rows out (contiguous in P); a unit without K
+        // blocks writes zeros
+        __syncwarp();
+        const int rl0 = half * 128 + q * 32;
+        const int64_t r0 = tile * kTileM + rl0;
+        const int64_t nr = min((int64_t)32, M - r0);
+        float *dg = Pp + r0 * k;
+        for (int64_t rr = 0; rr < nr; ++rr)
+          for (int c = lane; c < k; c += 32)
+            dg[rr * k + c] = first ? 0.f : acc_s[(size_t)(rl0 + rr) * L.acc_ld + c];
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -452,8 +552,8 @@ __global__ void k_split_transpose(const float *__restrict__ in, int64_t rows, in
 
 // One pass over A (m x n, lda) for the tensor-core runs: writes the rounded
 // copy X (m x n, ld ldx), the rounded transposed copy Xt (n x m, ld ldxt) and
-// per-block partial sums of a_ij^2 (FP64; each thread first adds the 16
-// squares it holds in FP32).  64 x 64 tiles: thread (ty, c4) loads the four
+// per-block partial sums of a_ij^2 and of a_ij (round(a_ij) - a_ij) (FP64;
+// each thread first adds the 16 terms it holds in FP32).  64 x 64 tiles: thread (ty, c4) loads the four
 // 16-byte pieces A[r0 + ty + 16 i][c0 + 4 c4 .. +3], i < 4, before storing
 // anything (VEC: rows of A are 16-byte aligned), then the tile is written
 // row-contiguously to X and, through shared memory, to Xt.
@@ -480,7 +580,7 @@ __global__ void __launch_bounds__(256)
   __shared__ float t[64][65];
   const int c4 = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16
   const int64_t tr = (m + 63) / 64, tcn = (n + 63) / 64;
-  double acc = 0.0;
+  double acc = 0.0, acc_d = 0.0;
   for (int64_t tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
     const int64_t r0 = (tile / tcn) * 64, c0 = (tile % tcn) * 64;
     const int64_t c = c0 + 4 * c4;
@@ -497,12 +597,16 @@ __global__ void __launch_bounds__(256)
         for (int u = 0; u < 4; ++u) v[i][u] = (r < m && c + u < n) ? src[u] : 0.f;
       }
     }
-    float sq = 0.f;
+    float sq = 0.f, sd = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sq = fmaf(v[i][u], v[i][u], sq);
+      for (int u = 0; u < 4; ++u) {
+        sq = fmaf(v[i][u], v[i][u], sq);
+        sd = fmaf(v[i][u], widen<T>(cvt<T>(v[i][u])) - v[i][u], sd);  // difference exact
+      }
     acc += (double)sq;
+    acc_d += (double)sd;
     __syncthreads();  // previous tile's transposed reads are done
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -541,24 +645,39 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
-  // block sum in a fixed order
-  __shared__ double ws[8];
+  // block sums in a fixed order
+  __shared__ double ws[2][8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    acc_d += __shfl_xor_sync(0xffffffffu, acc_d, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ws[0][threadIdx.x >> 5] = acc;
+    ws[1][threadIdx.x >> 5] = acc_d;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += ws[w];
-    part[blockIdx.x] = s;
+    double s = 0.0, d = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      s += ws[0][w];
+      d += ws[1][w];
+    }
+    part[2 * blockIdx.x] = s;
+    part[2 * blockIdx.x + 1] = d;
   }
 }
 
+// out[0] = sum of the even partials (||A||^2), out[1] = 2 x the odd ones.
 __global__ void k_sum_partials_d(const double *__restrict__ part, int np, double *__restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < np; ++i) s += part[i];
-    *out = s;
+    double s = 0.0, d = 0.0;
+    for (int i = 0; i < np; ++i) {
+      s += part[2 * i];
+      d += part[2 * i + 1];
+    }
+    out[0] = s;
+    out[1] = 2.0 * d;
   }
 }
 
@@ -751,17 +870,46 @@ bool fill_problem(GemmProblem *p, const void *X, int64_t M, int64_t K, int64_t l
 
 int64_t problem_units(const GemmProblem &p) { return ((p.M + kTileM - 1) / kTileM) * p.S; }
 
-bool launch_shape(GemmLaunch *L, int BNmax, int64_t units, int nprob, int *err) {
+// Accumulator row width that a problem needs in shared memory: its MMA
+// columns rounded up to the 64-column drain group, halved for a pair
+// problem (C_i = acc_2i + acc_2i+1).
+int acc_width(const GemmProblem &p) {
+  const int w = (p.BN + 63) & ~63;
+  return p.pair ? w / 2 : w;
+}
+
+// Shape of a launch whose problems have at most BNmax MMA columns and whose
+// shared accumulator rows need at most accw floats.  The FP32 accumulator
+// (256 x (accw | 1) floats, odd stride so that the 32 rows a warp touches
+// fall in 32 banks) goes to shared memory when two pipeline stages still fit
+// beside it; otherwise chunks are added into P in global memory
+// (L2-resident), with longer chunks.  TMEM holds nbuf chunk accumulators of
+// 2 x BNmax columns; the drain reads up to BN rounded up to 64 columns past
+// the start of the last half, which must stay inside the allocation.
+bool launch_shape(GemmLaunch *L, int BNmax, int accw, int64_t units, int nprob, int *err) {
   L->units = units;
   L->nprob = nprob;
   L->BNmax = BNmax;
-  L->nbuf = (4 * BNmax <= 512) ? 2 : 1;
+  const int wmax = (BNmax + 63) & ~63;
+  L->nbuf = (3 * BNmax + wmax <= 512) ? 2 : 1;
+  const int need = (2 * L->nbuf - 1) * BNmax + wmax;
+  if (need > 512) return false;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(L->nbuf * 2 * BNmax)) cols <<= 1;
+  while (cols < (uint32_t)need) cols <<= 1;
   L->tmem_cols = cols;
   const size_t sbytes = (size_t)(kTileM + BNmax) * kStageBytesK;
   const size_t budget = 225 * 1024 - 1024 - 256;
-  L->nstages = (int)(budget / sbytes);
+  const int ld = accw | 1;
+  const size_t acc = (size_t)kTileM * ld * sizeof(float);
+  if (acc + 2 * sbytes <= budget) {
+    L->acc_ld = ld;
+    L->nstages = (int)((budget - acc) / sbytes);
+    L->chunk_kb = kChunkKB;
+  } else {
+    L->acc_ld = 0;
+    L->nstages = (int)(budget / sbytes);
+    L->chunk_kb = kChunkKBGlobal;
+  }
   if (L->nstages > 8) L->nstages = 8;
   L->err = err;
   return L->nstages >= 2;
@@ -770,7 +918,8 @@ bool launch_shape(GemmLaunch *L, int BNmax, int64_t units, int nprob, int *err) 
 cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, const GemmLaunch &L,
                           bool bf16, cudaStream_t s) {
   const size_t sbytes = (size_t)(kTileM + L.BNmax) * kStageBytesK;
-  const size_t smem = 1024 + (size_t)L.nstages * sbytes + 256;
+  const size_t smem = 1024 + (size_t)L.nstages * sbytes +
+                      (size_t)kTileM * L.acc_ld * sizeof(float) + 256;
   const int grid = (int)(L.units < num_sms() ? L.units : num_sms());
   if (grid < 1) return cudaSuccess;
   if (bf16) {
@@ -791,7 +940,8 @@ cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const 
   if (!fill_problem(&p, X, M, K, ldx, Y, k, ldy, split, bf16, parts, S))
     return cudaErrorInvalidValue;
   GemmLaunch L;
-  if (!launch_shape(&L, p.BN, problem_units(p), 0, err)) return cudaErrorInvalidValue;
+  if (!launch_shape(&L, p.BN, acc_width(p), problem_units(p), 0, err))
+    return cudaErrorInvalidValue;
   return launch_kernel(p, nullptr, L, bf16, s);
 }
 
@@ -810,8 +960,14 @@ bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int
 
 cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
                               int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s) {
+  const GemmProblem *hp = reinterpret_cast<const GemmProblem *>(host_first);
+  int accw = 1;
+  for (int i = 0; i < nprob; ++i) {
+    const int w = acc_width(hp[i]);
+    accw = w > accw ? w : accw;
+  }
   GemmLaunch L;
-  if (!launch_shape(&L, BNmax, units, nprob, err)) return cudaErrorInvalidValue;
+  if (!launch_shape(&L, BNmax, accw, units, nprob, err)) return cudaErrorInvalidValue;
   return launch_kernel(*reinterpret_cast<const GemmProblem *>(host_first),
                        reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
 }

@@ -25,7 +25,8 @@ int splits_for(int64_t M, int64_t K, bool bf16);
 cudaError_t launch_transpose_to(const float *in, int64_t rows, int64_t cols, int64_t ldi, void *out,
                                 int64_t ldo, bool bf16, cudaStream_t s);
 // One pass over A: X = round(A) (m x n, ldx), Xt = round(A)^T (n x m, ldxt),
-// *norm2 = sum a_ij^2 (FP64) via prepare_blocks() partials in part.
+// norm2[0] = sum a_ij^2 and norm2[1] = 2 sum a_ij (round(a_ij) - a_ij) (FP64),
+// via 2 x prepare_blocks() partials in part.
 int prepare_blocks();
 cudaError_t launch_prepare(const float *A, int64_t m, int64_t n, int64_t lda, void *X, int64_t ldx,
                            void *Xt, int64_t ldxt, bool bf16, double *part, double *norm2,

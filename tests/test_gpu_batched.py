@@ -4,9 +4,17 @@ with one launch per phase, against the single-problem path and the oracle.
 Each problem is checked against aunmf_run on the same inputs (the same
 arithmetic, but the single path splits long products and Gram sums
 differently, and each exact NLS solve passes such rounding differences on
-scaled by the conditioning of the Gram matrix: the bar is 1e-4 in the
-relative residual, with m, n >= 500 >> k as in the batched workload) and
-against the FP64 oracle at the mixed-precision bar (1e-3)."""
+scaled by the conditioning of the Gram matrix: the bar on the factors'
+relative residual is 1e-5 for TF32 and 5e-5 for BF16 products, with
+m, n >= 500 >> k as in the batched workload), the reported trace-form
+residual against the factors' own FP64 residual (after the term that the
+rounding of A contributes, computed here: relres^2 within 8e-7, twice the
+bound on the relative bias that the tensor core's truncating accumulation
+leaves in <W^T A, H> with 2-K-block chains, <= 3e-7 measured; at
+relres ~ 2e-3 that is ~1e-4 in relres), and against the
+FP64 oracle at the mixed-precision bar (1e-3) after 30 iterations (TF32:
+at every iteration; BF16 rounds A itself, so its trajectory may leave the
+oracle's by more than the bar mid-descent and is compared at the end)."""
 import numpy as np
 import pytest
 
@@ -30,6 +38,28 @@ def dev(x):
     return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
 
 
+def rounded(A, prec):
+    """A (FP32 values) rounded as the tensor-core products read it: BF16 to
+    nearest even, TF32 to nearest with ties away from zero."""
+    a32 = np.ascontiguousarray(A, dtype=np.float32)
+    if prec == "bf16":
+        return torch.from_numpy(a32).to(torch.bfloat16).to(torch.float64).numpy()
+    bits = a32.view(np.uint32).astype(np.uint64)
+    bits = ((bits + 0x1000) & ~np.uint64(0x1FFF)).astype(np.uint32)
+    return bits.view(np.float32).astype(np.float64)
+
+
+def expected_reported(A, W, H, prec, direct):
+    """The trace form with the rounded copy A~ = A + d and the constant term
+    ||A||^2 + 2 <d, A> measures ||A - WH||^2 + 2 <d, A - WH>: the second
+    term is the part of the rounding noise that the fitted WH absorbs (about
+    k (m + n) / (m n) of ||d||^2; ~1e-6 ||A||^2 for BF16 on the small
+    problems here, ~1e-9 on the large workloads)."""
+    d = rounded(A, prec) - A
+    extra = 2.0 * float((d * (A - W @ H)).sum()) / float((A * A).sum())
+    return float(np.sqrt(max(0.0, direct * direct + extra)))
+
+
 def batch(seed, count, lo=500, hi=900):
     """Uneven problems: m, n uniform in [lo, hi], k from {8, 16, 32, 64},
     planted rank k + noise."""
@@ -47,25 +77,31 @@ def batch(seed, count, lo=500, hi=900):
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
 def test_batched_matches_single_and_oracle(ax, prec):
     """Per problem: the factors' FP64 residual (oracle, entry by entry) equals
-    the single path's to 1e-5; the reported residual is within 1e-4 of it and
-    within 1e-3 of the oracle's own run."""
+    the single path's (1e-5 TF32, 5e-5 BF16); the reported residual matches
+    it (squared, 8e-7, after the rounding term) and is within 1e-3 of the
+    oracle's own run after 30 iterations."""
+    same_bar = 1e-5 if prec == "tf32" else 5e-5
+    iters = 30
     probs = batch(11, 7)
     As = [dev(A) for A, _, _ in probs]
     H0s = [dev(H0) for _, H0, _ in probs]
     ks = [k for _, _, k in probs]
-    Ws, Hs, rel, info = ax.run_batched(As, ks, 8, H0s, prec=prec)
+    Ws, Hs, rel, info = ax.run_batched(As, ks, iters, H0s, prec=prec)
     assert info["bpp_nonconverged"] == 0 and info["bpp_numeric"] == 0
     assert info["tuned_bpp_warps"] > 0 and info["tuned_bpp_rows"] > 0
     host = lambda t: t.cpu().numpy().astype(np.float64)  # noqa: E731
     for p, (A, H0, k) in enumerate(probs):
-        W1, H1, r1, _ = ax.run(As[p], k, "abpp", 8, dev(np.zeros((A.shape[0], k))), H0s[p],
+        W1, H1, r1, _ = ax.run(As[p], k, "abpp", iters, dev(np.zeros((A.shape[0], k))), H0s[p],
                                prec=prec)
         db = orc.relres_direct(A, host(Ws[p]), host(Hs[p]))
         ds = orc.relres_direct(A, host(W1), host(H1))
-        assert abs(db - ds) <= 1e-5, (p, db, ds)
-        assert abs(rel[p][-1] - db) <= 1e-4, (p, rel[p][-1], db)
-        ref = orc.nmf_run(A, k, "abpp", 8, None, H0)
-        assert np.abs(rel[p] - ref["relres"]).max() <= 1e-3
+        assert abs(db - ds) <= same_bar, (p, db, ds)
+        want = expected_reported(A, host(Ws[p]), host(Hs[p]), prec, db)
+        assert abs(rel[p][-1] ** 2 - want ** 2) <= 8e-7, (p, rel[p][-1], want, db)
+        ref = orc.nmf_run(A, k, "abpp", iters, None, H0)
+        assert abs(rel[p][-1] - ref["relres"][-1]) <= 1e-3
+        if prec == "tf32":
+            assert np.abs(rel[p] - ref["relres"]).max() <= 1e-3
         assert bool((Ws[p] >= 0).all()) and bool((Hs[p] >= 0).all())
 
 

@@ -56,7 +56,7 @@ def test_loss_and_gradient_match_oracle(ax, m, n, k):
     loss_ref, dW_ref, dH_ref = orc.loss_grad(A, W, H)
     Ad, Wd, Hd = dev(A), dev(W), dev(H)
     loss, wta = ax.loss_fwd(Ad, Wd, Hd)
-    assert float(loss) == pytest.approx(loss_ref, rel=1e-5)
+    assert float(loss.detach()) == pytest.approx(loss_ref, rel=1e-5)
     dW, dH = ax.loss_bwd(Ad, Wd, Hd, wta=wta)
     tw, th = grad_tols(A, W, H)
     assert (np.abs(host(dW) - dW_ref) <= tw).all()
@@ -96,7 +96,7 @@ def test_autograd_function(ax):
     loss = nmf_loss(Ad, Wd, Hd)
     (3.0 * loss).backward()
     loss_ref, dW_ref, dH_ref = orc.loss_grad(A, W, H)
-    assert float(loss) == pytest.approx(loss_ref, rel=1e-5)
+    assert float(loss.detach()) == pytest.approx(loss_ref, rel=1e-5)
     tw, th = grad_tols(A, W, H)
     assert (np.abs(host(Wd.grad) - 3.0 * dW_ref) <= 3.0 * tw).all()
     assert (np.abs(host(Hd.grad) - 3.0 * dH_ref) <= 3.0 * th).all()

@@ -124,3 +124,22 @@ def test_mixed_run_with_and_without_graph_identical(ax, config_small):
     W1, H1, r1, _ = ax.run(Ad, 10, "hals", 12, dev(W0), dev(H0), prec="tf32", use_graph=True)
     W2, H2, r2, _ = ax.run(Ad, 10, "hals", 12, dev(W0), dev(H0), prec="tf32", use_graph=False)
     assert torch.equal(W1, W2) and torch.equal(H1, H2) and np.array_equal(r1, r2)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_mixed_reported_residual_matches_direct(ax, prec):
+    """The reported relres (trace form, Sec. 5) equals the FP64 residual of
+    the returned factors computed entry by entry, on a product with a long
+    contraction (W^T A sums over m = 40000 rows).  The tensor core rounds
+    each MMA's addition into its FP32 accumulator toward zero, which biases
+    a long accumulation chain low (~-3e-5 relative here without restarts)
+    and moves the trace-form residual by ~bias / relres (~1e-3); the kernel
+    restarts the chain every 2 K blocks and rounds the sums of chains to
+    nearest, and the constant term carries the rounding of A itself.  The
+    bar, 1e-4, is 10x what the residual bias of 2-block chains (<= 3e-7
+    relative in <W^T A, H>) moves it by at relres ~ 0.03."""
+    m, n, k = 40000, 1000, 32
+    A, W0, H0 = problem(m, n, k, seed=77)
+    W, H, rel, _ = ax.run(dev(A), k, "hals", 5, dev(W0), dev(H0), prec=prec)
+    direct = orc.relres_direct(A, host(W), host(H))
+    assert abs(rel[-1] - direct) <= 1e-4, (rel[-1], direct)
