@@ -57,9 +57,15 @@ constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 // shared memory, and when it is added into P in global memory.  Measured
 // bias of <W^T A, H> (relative, nonnegative data): 4 K blocks -6e-7 (TF32)
 // and -2.5e-7 (BF16), 2 K blocks -2.5e-7 and -1e-7, 1 K block -1.1e-7 and
-// -4e-8; the drain of 256 x BN accumulators hides behind a chunk of >= 2
-// K blocks at the HBM rate (2: ~5% slower than 4 on 96000 x 64000, k = 50).
+// -4e-8.  A shared-memory drain of 256 x BN sums per chunk competes with TMA
+// and the MMAs for shared-memory bandwidth, so it takes chunks of 2 K
+// blocks; sums in registers drain after every K block at ~1.5% below the
+// 4-block speed (96000 x 64000, k = 50).
 constexpr int kChunkKB = AUNMF_TC_CHUNK_KB;
+#ifndef AUNMF_TC_CHUNK_KB_REG
+#define AUNMF_TC_CHUNK_KB_REG 1
+#endif
+constexpr int kChunkKBReg = AUNMF_TC_CHUNK_KB_REG;  // sums in registers
 constexpr int kChunkKBGlobal = 4 * AUNMF_TC_CHUNK_KB;
 
 // ------------------------------------------------------------------ PTX
@@ -226,6 +232,7 @@ struct GemmLaunch {
   int nstages;
   int nbuf;            // TMEM accumulator buffers (1 or 2)
   uint32_t tmem_cols;  // power of two >= nbuf * 2 * BNmax
+  int regacc;          // 1: sums in registers (all problems pair, BN <= 128)
   int chunk_kb;        // K blocks per TMEM accumulation chain
   int acc_ld;          // row stride (floats, odd, >= BN/2 for pair problems and BN
                        // otherwise) of the shared-memory accumulator, 256 rows;
@@ -245,7 +252,10 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &on
   return group + lo;
 }
 
-template <bool BF16>
+// REGACC: every problem of the launch is a pair problem with BN <= 128
+// (k <= 64); each epilogue thread keeps its row's <= 64 sums in registers.
+// Otherwise the sums live in shared memory (or in P).
+template <bool BF16, bool REGACC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmProblem one, const GemmProblem *__restrict__ group,
               const GemmLaunch L) {
@@ -377,6 +387,40 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = tile * kTileM + rl;
       float *Pp = p->P + sp * M * k;
       const bool live = row < M;
+      if constexpr (REGACC) {
+        // pair problem, BN <= 128: C_i = acc_2i + acc_2i+1 for i < BN / 2
+        float acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+        for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
+          if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t taddr =
+              tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            if (32 * g >= BN) break;
+            uint32_t r[32];
+            tmem_ld16_async(taddr + (uint32_t)(32 * g), r);
+            tmem_ld16_async(taddr + (uint32_t)(32 * g + 16), r + 16);
+            tmem_wait_ld(r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              acc[16 * g + j] += __uint_as_float(r[2 * j]) + __uint_as_float(r[2 * j + 1]);
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[buf]);
+          if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
+        }
+        if (!ok) break;
+        if (live) {
+          float *dg = Pp + row * k;
+#pragma unroll
+          for (int o = 0; o < 64; ++o)
+            if (o < k) dg[o] = acc[o];
+        }
+        continue;
+      }
       bool first = true;
       for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
         if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
@@ -874,6 +918,7 @@ int64_t problem_units(const GemmProblem &p) { return ((p.M + kTileM - 1) / kTile
 // columns rounded up to the 64-column drain group, halved for a pair
 // problem (C_i = acc_2i + acc_2i+1).
 int acc_width(const GemmProblem &p) {
+  if (p.pair && p.BN <= 128) return 0;  // sums in registers
   const int w = (p.BN + 63) & ~63;
   return p.pair ? w / 2 : w;
 }
@@ -901,7 +946,12 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, int64_t units, int nprob, 
   const size_t budget = 225 * 1024 - 1024 - 256;
   const int ld = accw | 1;
   const size_t acc = (size_t)kTileM * ld * sizeof(float);
-  if (acc + 2 * sbytes <= budget) {
+  L->regacc = accw == 0 ? 1 : 0;
+  if (L->regacc) {
+    L->acc_ld = 0;
+    L->nstages = (int)(budget / sbytes);
+    L->chunk_kb = kChunkKBReg;
+  } else if (acc + 2 * sbytes <= budget) {
     L->acc_ld = ld;
     L->nstages = (int)((budget - acc) / sbytes);
     L->chunk_kb = kChunkKB;
@@ -922,12 +972,14 @@ cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, cons
                       (size_t)kTileM * L.acc_ld * sizeof(float) + 256;
   const int grid = (int)(L.units < num_sms() ? L.units : num_sms());
   if (grid < 1) return cudaSuccess;
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, kThreads, smem, s>>>(one, group, L);
+  };
   if (bf16) {
-    cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemm_tc<true><<<grid, kThreads, smem, s>>>(one, group, L);
+    if (L.regacc) go(k_gemm_tc<true, true>); else go(k_gemm_tc<true, false>);
   } else {
-    cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gemm_tc<false><<<grid, kThreads, smem, s>>>(one, group, L);
+    if (L.regacc) go(k_gemm_tc<false, true>); else go(k_gemm_tc<false, false>);
   }
   g_launches += 1;
   return cudaGetLastError();
@@ -961,7 +1013,7 @@ bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int
 cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
                               int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s) {
   const GemmProblem *hp = reinterpret_cast<const GemmProblem *>(host_first);
-  int accw = 1;
+  int accw = 0;
   for (int i = 0; i < nprob; ++i) {
     const int w = acc_width(hp[i]);
     accw = w > accw ? w : accw;
