@@ -377,26 +377,48 @@ def run_ours(args):
     h = aunmf.Handle()
     W = torch.empty_like(W0)
     H = torch.empty_like(H0)
-    # warm-up (untimed), then the timed K iterations in profile mode so the
-    # library records per-phase CUDA events on its stream
-    h.run(A, k, args.algo, args.warmup, W0, H0, prec=args.prec, out=(W, H),
-          allow_noconverge=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(prec, profile=False):
+        """warm-up (untimed), then `steps` iterations from (W0, H0) timed with
+        CUDA events around the call (the library's stream is the current
+        stream's device; the call returns after its stream synchronises)."""
+        h.run(A, k, args.algo, args.warmup, W0, H0, prec=prec, out=(W, H), allow_noconverge=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record()
+        _, _, r, inf = h.run(A, k, args.algo, args.steps, W0, H0, prec=prec, out=(W, H),
+                             profile=profile, allow_noconverge=True)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        return max_over_ranks(e0.elapsed_time(e1), world), r, inf
+
+    # the timed region of the headline number: the whole run, as a CUDA graph
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    _, _, rel, info = h.run(A, k, args.algo, args.steps, W0, H0, prec=args.prec, out=(W, H),
-                            profile=True, allow_noconverge=True)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier(world)
-    ms_total = e0.elapsed_time(e1)
+    ms_total, rel, info_g = timed(args.prec)
     clk = clocks.stop()
-    ms_total = max_over_ranks(ms_total, world)
     value = world * args.steps / (ms_total / 1e3)
+    # the same run in profile mode (no graph; CUDA events around each phase on
+    # the library's stream) for the per-kernel durations of the roofline
+    _, _, info = timed(args.prec, profile=True)
+    # the three precision forms from the same start: matched residual
+    forms = None
+    if not sparse and not args.no_forms:
+        forms = {}
+        for pr in ("fp32", "tf32", "bf16"):
+            if pr == args.prec:
+                t, r = ms_total, rel
+            else:
+                t, r, _ = timed(pr)
+            forms[pr] = {"iters_per_s": world * args.steps / (t / 1e3),
+                         "ms_per_step": t / args.steps, "relres_last": float(r[-1])}
+        base = forms["fp32"]
+        for pr, f in forms.items():
+            f["speedup_vs_fp32"] = f["iters_per_s"] / base["iters_per_s"]
+            f["relres_gap_vs_fp32"] = abs(f["relres_last"] - base["relres_last"])
 
     # dominant kernel: the product launch with the larger summed time
     pk, pks = peaks()
@@ -478,9 +500,10 @@ def run_ours(args):
             "data": "synthetic", "config": config_dict(args),
             "tflops": f_it * value / 1e12,
             "relres_last": float(rel[-1]) if len(rel) else None,
+            "forms": forms,
             "roofline": roof, "kernels": kern, "phases_ms_per_step": phases,
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(info["launches"]), "clocks": clk,
+            "gpu_launches": int(info_g["launches"]), "clocks": clk,
         }
         print(json.dumps(line))
     if world > 1:
@@ -497,13 +520,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="hals", choices=["mu", "hals", "abpp"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--workload", default="dense", choices=sorted(WORKLOADS))
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--m", type=int, default=None, help="rows of A (profiling cases)")
     ap.add_argument("--n", type=int, default=None, help="columns of A (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 / TF32 / BF16 comparison runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
