@@ -1,9 +1,10 @@
 // k_luc.cu -- local update computations (LUC) for MU and HALS.
 //
 // Both factors are held as row-major "rows x k" matrices (W, and H^T for H),
-// so one kernel serves both updates.  One warp owns one row; lane l holds
-// the entries j = l, l + 32, ... (KT = ceil(k / 32) per lane, k <= 256).
-// The k x k Gram matrix is staged in shared memory when it fits.
+// so one kernel serves both updates.  For k <= 64 one thread owns one row
+// (k_luc_tpr).  Above, one warp owns one row; lane l holds the entries
+// j = l, l + 32, ... (KT = ceil(k / 32) per lane, k <= 256), and the k x k
+// Gram matrix is staged in shared memory when it fits.
 #include <math.h>
 
 #include "internal.cuh"
@@ -14,6 +15,7 @@ namespace {
 constexpr int kLucThreads = 256;
 constexpr int kLucWarps = kLucThreads / kWarp;
 constexpr int kSmemGramMaxK = 108;  // 108*108*4 B < 48 KB default dynamic limit
+constexpr int kTprMaxK = 64;        // thread-per-row forms up to this k
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -194,6 +196,151 @@ __global__ void k_hals_scale_gram(float *__restrict__ GW, int k) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Thread-per-row forms for k <= 64 (the same three updates).  A warp takes 32
+// consecutive rows, copies them into a shared tile (row stride KP + 1, odd:
+// the lanes' rows fall in 32 banks) with asynchronous 4-byte copies, all in
+// flight at once, and each thread then keeps its row in registers and walks
+// the k coordinates itself: no shuffle per coordinate.  The k x k matrix is
+// staged transposed and zero-padded to KP, so (x G)_i = sum_j x_j G_ji reads
+// row i of the staged copy with 16-byte broadcast loads; padded coordinates
+// have G_ii = 0 and stay 0.
+enum LucOp { kOpMu = 0, kOpHals = 1, kOpGrad = 2 };
+constexpr int kTprThreads = 256;
+constexpr int kTprWarps = kTprThreads / kWarp;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  // src-size 0 fills the 4 bytes with zeros and reads nothing
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// tile rows 0..31 = src rows 0..nr-1 (row length k, contiguous), zeros
+// elsewhere; the warp's copies complete before it returns.
+template <int KP>
+__device__ __forceinline__ void tile_in(const float *__restrict__ src, int nr, int k, float *tile,
+                                        int lane) {
+  constexpr int LDT = KP + 1;
+#pragma unroll 8
+  for (int rr = 0; rr < 32; ++rr)
+#pragma unroll
+    for (int c = lane; c < KP; c += 32) {
+      const bool v = rr < nr && c < k;
+      cp_async4(tile + rr * LDT + c, v ? src + (int64_t)rr * k + c : src, v);
+    }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+template <int KP>
+__device__ __forceinline__ void tile_out(float *__restrict__ dst, int nr, int k, const float *tile,
+                                         int lane) {
+  constexpr int LDT = KP + 1;
+  __syncwarp();
+  for (int rr = 0; rr < nr; ++rr)
+    for (int c = lane; c < k; c += 32) dst[(int64_t)rr * k + c] = tile[rr * LDT + c];
+  __syncwarp();
+}
+
+// (x G)_i for the thread's row x (KP registers) and the staged G^T.
+template <int KP>
+__device__ __forceinline__ float xg(const float (&x)[KP], const float *sGt, int i) {
+  const float4 *g4 = reinterpret_cast<const float4 *>(sGt + i * KP);
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < KP / 4; ++q) {
+    const float4 g = g4[q];
+    d0 = fmaf(x[4 * q], g.x, d0);
+    d1 = fmaf(x[4 * q + 1], g.y, d1);
+    d2 = fmaf(x[4 * q + 2], g.z, d2);
+    d3 = fmaf(x[4 * q + 3], g.w, d3);
+  }
+  return (d0 + d1) + (d2 + d3);
+}
+
+template <int KP, int OP>
+__global__ void __launch_bounds__(kTprThreads)
+    k_luc_tpr(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
+              int64_t rows, int k, float eps, const float *__restrict__ gscale,
+              float *__restrict__ out) {
+  constexpr int LDT = KP + 1;
+  extern __shared__ __align__(16) float smt[];
+  float *sGt = smt;  // KP x KP: sGt[i][j] = G[j][i], zero outside k x k
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float *tile = smt + KP * KP + wib * 32 * LDT;
+  for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) {
+    const int i = e / KP, j = e % KP;
+    sGt[e] = (i < k && j < k) ? G[j * k + i] : 0.f;
+  }
+  __syncthreads();
+  const float g = (OP == kOpGrad && gscale) ? *gscale : 1.f;
+  float *dst = OP == kOpGrad ? out : X;
+  const int64_t groups = (rows + 31) / 32;
+  for (int64_t grp = (int64_t)blockIdx.x * kTprWarps + wib; grp < groups;
+       grp += (int64_t)gridDim.x * kTprWarps) {
+    const int64_t r0 = grp * 32;
+    const int nr = (int)min((int64_t)32, rows - r0);
+    tile_in<KP>(X + r0 * k, nr, k, tile, lane);
+    float x[KP];
+    float *t = tile + lane * LDT;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) x[j] = t[j];
+    __syncwarp();
+    tile_in<KP>(P + r0 * k, nr, k, tile, lane);
+    if constexpr (OP == kOpHals) {
+      // x_i <- max(0, x_i + (p_i - (x G)_i) / G_ii), i ascending, with the
+      // entries before i already updated; G_ii <= 0 leaves x_i as it is
+#pragma unroll
+      for (int i = 0; i < KP; ++i) {
+        const float gii = sGt[i * KP + i];
+        if (gii > 0.f) {
+          const float v = x[i] + (t[i] - xg<KP>(x, sGt, i)) / gii;
+          x[i] = v > 0.f ? v : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < KP; ++j) t[j] = x[j];
+    } else {
+      // every entry from the old x: MU x_j p_j / ((x G)_j + eps), gradient
+      // g ((x G)_j - p_j); the result replaces p_j in the tile
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        if (j >= k) break;
+        const float d = xg<KP>(x, sGt, j);
+        t[j] = OP == kOpMu ? x[j] * t[j] / (d + eps) : g * (d - t[j]);
+      }
+    }
+    tile_out<KP>(dst + r0 * k, nr, k, tile, lane);
+  }
+}
+
+template <int KP, int OP>
+cudaError_t launch_tpr(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
+                       const float *gscale, float *out, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)KP * KP + (size_t)kTprWarps * 32 * (KP + 1));
+  cudaFuncSetAttribute(k_luc_tpr<KP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t groups = (rows + 31) / 32;
+  int64_t nb = (groups + kTprWarps - 1) / kTprWarps;
+  if (nb > 152 * 4) nb = 152 * 4;
+  k_luc_tpr<KP, OP><<<(unsigned)nb, kTprThreads, smem, s>>>(X, P, G, rows, k, eps, gscale, out);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t launch_tpr_k(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
+                         const float *gscale, float *out, cudaStream_t s) {
+  if (k <= 16) return launch_tpr<16, OP>(X, P, G, rows, k, eps, gscale, out, s);
+  if (k <= 32) return launch_tpr<32, OP>(X, P, G, rows, k, eps, gscale, out, s);
+  if (k <= 48) return launch_tpr<48, OP>(X, P, G, rows, k, eps, gscale, out, s);
+  return launch_tpr<64, OP>(X, P, G, rows, k, eps, gscale, out, s);
+}
+
 int luc_blocks(int64_t rows) {
   int64_t nb = (rows + kLucWarps - 1) / kLucWarps;
   if (nb > 152 * 8) nb = 152 * 8;
@@ -218,6 +365,7 @@ int luc_blocks(int64_t rows) {
 cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
                       cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  if (k <= kTprMaxK) return launch_tpr_k<kOpMu>(X, P, G, rows, k, eps, nullptr, nullptr, s);
   const int kt = (k + 31) / 32, nb = luc_blocks(rows);
   const bool sm = k <= kSmemGramMaxK;
   const size_t smem = sm ? sizeof(float) * k * k : 0;
@@ -233,6 +381,7 @@ cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, in
 cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, int k,
                         cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  if (k <= kTprMaxK) return launch_tpr_k<kOpHals>(X, P, G, rows, k, 0.f, nullptr, nullptr, s);
   const int kt = (k + 31) / 32, nb = luc_blocks(rows);
   const bool sm = k <= kSmemGramMaxK;
   const size_t smem = sm ? sizeof(float) * k * k : 0;
@@ -248,6 +397,8 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
 cudaError_t launch_xg_minus_p(const float *X, const float *P, const float *G, int64_t rows, int k,
                               const float *gscale, float *out, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  if (k <= kTprMaxK)
+    return launch_tpr_k<kOpGrad>(const_cast<float *>(X), P, G, rows, k, 0.f, gscale, out, s);
   const int kt = (k + 31) / 32, nb = luc_blocks(rows);
   const bool sm = k <= kSmemGramMaxK;
   const size_t smem = sm ? sizeof(float) * k * k : 0;
