@@ -211,12 +211,19 @@ __global__ void __launch_bounds__(256)
     const float *X = side ? b.W : b.Ht;
     float *out = (side ? b.gpart_w : b.gpart_h) + (int64_t)I.chunk * k * k;
     const int kp = (k + 3) & ~3;
-    const int nt = kp / 4, ntiles = nt * nt;
+    const int nt = kp / 4, ntiles = nt * (nt + 1) / 2;  // upper triangle of 4 x 4 tiles
     for (int tb = 0; tb < ntiles; tb += blockDim.x) {
       const int tt = tb + threadIdx.x;
       const bool act = tt < ntiles;
-      const int ti = act ? tt / nt : 0, tj = act ? tt % nt : 0;
-      double acc[4][4] = {};  // FP64 sum of FP32 32-row sums
+      int ti = 0, tj = 0;
+      if (act) {
+        int rem = tt;
+        while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+        tj = ti + rem;
+      }
+      // each 32-row FP32 sum added to the running sum with Kahan's
+      // compensation (FP64 additions are slow on this part)
+      float sum[4][4] = {}, cmp[4][4] = {};
       for (int64_t c0 = I.r0; c0 < I.r1; c0 += 32) {
         const int nr = (int)min((int64_t)32, I.r1 - c0);
         __syncthreads();
@@ -242,7 +249,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][c] += (double)part[a][c];
+            for (int c = 0; c < 4; ++c) {
+              const float y = part[a][c] - cmp[a][c];
+              const float t = sum[a][c] + y;
+              cmp[a][c] = (t - sum[a][c]) - y;
+              sum[a][c] = t;
+            }
         }
       }
       if (act)
@@ -251,7 +263,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int i = 4 * ti + a, j = 4 * tj + c;
-            if (i < k && j < k) out[i * k + j] = (float)acc[a][c];
+            if (i < k && j < k) {
+              const float v = sum[a][c] - cmp[a][c];
+              out[i * k + j] = v;
+              out[j * k + i] = v;
+            }
           }
     }
   }

@@ -15,36 +15,74 @@ namespace aunmf {
 // ------------------------------------------------------------------ Gram
 // Block b accumulates X^T X over rows [b*chunk, (b+1)*chunk) into
 // partials[b] (k x k).  Each thread owns a 4x4 tile of G; rows are staged in
-// shared memory 32 at a time, each 32-row sum is taken in FP32 and added in
-// FP64 (the residual's expansion <W^T W, H H^T> needs the Grams to ~1e-7).
+// shared memory 32 at a time, each 32-row sum is taken in FP32 and added to
+// a Kahan-compensated FP32 running sum (the residual's expansion
+// <W^T W, H H^T> needs the Grams to ~1e-7).
 namespace {
 constexpr int kGramRows = 32;
 constexpr int kGramThreads = 256;
 
+// Per-block partial of G = X^T X over the block's rows, 32-row slabs: the
+// slab is staged in shared memory while the next one is loaded into
+// registers, and each thread computes one 4 x 4 tile of the upper triangle
+// (tile row <= tile column; G is symmetric, the tile is written to both
+// triangles).  A slab's products are summed in a fresh FP32 register and
+// added to the running sum with Kahan's compensation: the running sum of a
+// million rows keeps close to FP32 rounding without FP64 additions, whose
+// rate on this part (~2 per SM per clock) would bound the kernel.
 __global__ void __launch_bounds__(kGramThreads)
     k_gram_partial(const float *__restrict__ X, int64_t rows, int k, int64_t ldx, int64_t chunk,
                    float *__restrict__ partials) {
   extern __shared__ float sX[];  // [kGramRows][kp]
+  constexpr int kPre = (kGramRows * 64 + kGramThreads - 1) / kGramThreads;  // k <= 64 prefetch
   const int kp = (k + 3) & ~3;
-  const int nt = kp / 4, ntiles = nt * nt;
+  const int nt = kp / 4, ntiles = nt * (nt + 1) / 2;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(rows, r0 + chunk);
   float *out = partials + (int64_t)blockIdx.x * k * k;
+  const int slab = kGramRows * kp;
+  const bool pre = slab <= kPre * kGramThreads;
   for (int tb = 0; tb < ntiles; tb += kGramThreads) {
     const int t = tb + threadIdx.x;
     const bool act = t < ntiles;
-    const int ti = act ? t / nt : 0, tj = act ? t % nt : 0;
-    double acc[4][4];  // FP64 sum of the FP32 sums of each 32-row chunk
+    // t -> (ti, tj), ti <= tj, row-major over the upper triangle
+    int ti = 0, tj = 0;
+    if (act) {
+      int rem = t;
+      while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+      tj = ti + rem;
+    }
+    float sum[4][4], cmp[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+      for (int b = 0; b < 4; ++b) sum[a][b] = cmp[a][b] = 0.f;
+    float nxt[kPre];
+    auto fetch = [&](int64_t c0) {
+      const int nr = (int)min((int64_t)kGramRows, r1 - c0);
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int idx = threadIdx.x + q * kGramThreads;
+        const int rr = idx / kp, cc = idx - rr * kp;
+        nxt[q] = (idx < slab && rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+      }
+    };
+    if (pre && r0 < r1) fetch(r0);
     for (int64_t c0 = r0; c0 < r1; c0 += kGramRows) {
       const int nr = (int)min((int64_t)kGramRows, r1 - c0);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < kGramRows * kp; idx += kGramThreads) {
-        const int rr = idx / kp, cc = idx % kp;
-        sX[idx] = (rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+      if (pre) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+          const int idx = threadIdx.x + q * kGramThreads;
+          if (idx < slab) sX[idx] = nxt[q];
+        }
+        if (c0 + kGramRows < r1) fetch(c0 + kGramRows);
+      } else {
+        for (int idx = threadIdx.x; idx < slab; idx += kGramThreads) {
+          const int rr = idx / kp, cc = idx - rr * kp;
+          sX[idx] = (rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+        }
       }
       __syncthreads();
       if (act) {
@@ -61,7 +99,12 @@ __global__ void __launch_bounds__(kGramThreads)
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] += (double)part[p][q];
+          for (int q = 0; q < 4; ++q) {
+            const float y = part[p][q] - cmp[p][q];
+            const float tt = sum[p][q] + y;
+            cmp[p][q] = (tt - sum[p][q]) - y;
+            sum[p][q] = tt;
+          }
       }
     }
     if (act) {
@@ -70,7 +113,11 @@ __global__ void __launch_bounds__(kGramThreads)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int i = 4 * ti + p, j = 4 * tj + q;
-          if (i < k && j < k) out[i * k + j] = (float)acc[p][q];
+          if (i < k && j < k) {
+            const float v = sum[p][q] - cmp[p][q];
+            out[i * k + j] = v;
+            out[j * k + i] = v;
+          }
         }
     }
   }
