@@ -170,11 +170,15 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
  * GH = H H^T (k x k) [device].  MU: Eq. muupdate with eps; HALS: the
  * column sweep of Eq. halsupdate, then unit-normalised columns with H's rows
  * (H k x n, may be NULL) scaled by the norms; ABPP: each row of W solves
- * SolveBPP(GH, row of PW) in FP64.  eps <= 0 selects 1e-16. */
+ * SolveBPP(GH, row of PW) in FP64 from a cold start (GH widened from FP32;
+ * aunmf_run forms its Grams in FP64 instead), and the call synchronises and
+ * returns AUNMF_E_NUMERIC / AUNMF_E_NOCONVERGE if a row failed (W still
+ * written).  eps <= 0 selects 1e-16. */
 int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const float *GH,
                    int64_t m, int k, float *H, int64_t n, double eps);
 /* Local update of H (Alg. 1 line 4) in place: H k x n, PH = W^T A (k x n),
- * GW = W^T W [device].  MU / HALS row sweep / ABPP on each column. */
+ * GW = W^T W [device].  MU / HALS row sweep / ABPP on each column (ABPP
+ * reports failures as aunmf_update_w does). */
 int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const float *GW,
                    int k, int64_t n, double eps);
 

@@ -26,9 +26,14 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_NOCONVERGE, E_TIMEOUT, E_UNSUPPORTED 
 
 
 class AunmfError(RuntimeError):
-    def __init__(self, code, msg):
+    """A non-zero status.  For whole runs (run, run_batched) the library has
+    still written its outputs; they are attached as `result`
+    (W, H, relres, info) when available."""
+
+    def __init__(self, code, msg, result=None):
         super().__init__(msg)
         self.code = code
+        self.result = result
 
 
 class Matrix(ctypes.Structure):
@@ -165,12 +170,12 @@ class Handle:
         self._h = ctypes.c_void_p()
         self._check(self._lib.aunmf_create(ctypes.byref(self._h), ctypes.c_void_p(s.cuda_stream)))
 
-    def _check(self, rc, allow=()):
+    def _check(self, rc, allow=(), result=None):
         if rc != OK and rc not in allow:
             msg = strerror(rc)
             if rc == E_CUDA and getattr(self, "_h", None):
                 msg += ": " + self._lib.aunmf_last_cuda_error(self._h).decode()
-            raise AunmfError(rc, msg)
+            raise AunmfError(rc, msg, result)
         return rc
 
     def set_stream(self, stream):
@@ -209,8 +214,9 @@ class Handle:
         rc = self._lib.aunmf_run(self._h, ctypes.byref(M), k, algo, iters, _ptr(W0), _ptr(H0),
                                  _ptr(W), _ptr(H), rel.ctypes.data_as(ctypes.c_void_p),
                                  ctypes.byref(opt), ctypes.byref(info))
-        self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else ())
-        return W, H, rel[:iters], info.as_dict()
+        result = (W, H, rel[:iters], info.as_dict())
+        self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else (), result=result)
+        return result
 
     def run_batched(self, As, ks, iters, H0s, *, prec="tf32", use_graph=True, bpp_max_pivots=0,
                     allow_noconverge=False):
@@ -234,8 +240,9 @@ class Handle:
                                          parr(H0s), parr(Ws), parr(Hs),
                                          rel.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opt),
                                          ctypes.byref(info))
-        self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else ())
-        return Ws, Hs, rel[:, :iters], info.as_dict()
+        result = (Ws, Hs, rel[:, :iters], info.as_dict())
+        self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else (), result=result)
+        return result
 
     def run_host(self, A, k, algo, iters, W0, H0, *, prec="fp32", use_graph=True,
                  profile=False, W=None, H=None):

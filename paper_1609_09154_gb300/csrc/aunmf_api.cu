@@ -39,7 +39,7 @@ struct aunmf_handle {
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   std::string cuda_err;
   // workspace
-  Buf Ht, PW, PHt, GH, GW, gpart, dpart, n2a, ctr, relres, last;
+  Buf Ht, PW, PHt, GH, GW, G64, gpart, dpart, n2a, ctr, relres, last;
   Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
   Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
   Buf bppq;                            // BPP: G^{-1} in FP64
@@ -117,6 +117,7 @@ struct RunCtx {
   int warm;        // BPP starts from the previous iterate's support
   void *bppq;      // BPP scratch (G^{-1})
   float *W, *Ht, *PW, *PHt, *GH, *GW, *gpart;
+  double *GH64, *GW64;  // ABPP: the Grams in FP64 (GH / GW hold them rounded)
   double *dpart, *n2a, *relres_dev, *last;
   DevCounters *ctr;
   // tensor-core path (prec != FP32): X operands of the two products (A or its
@@ -242,13 +243,23 @@ int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s);
 // CSC copy of a sparse A (setup of the W^T A product).
 int prepare_sparse(aunmf_handle *h, RunCtx &c, cudaStream_t s);
 
-cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, int64_t rows,
-                   cudaStream_t s) {
+cudaError_t update(RunCtx &c, float *X, const float *Pm, const float *G, const double *G64,
+                   int64_t rows, cudaStream_t s) {
   switch (c.algo) {
     case AUNMF_MU: return launch_mu(X, Pm, G, rows, c.k, c.mu_eps, s);
     case AUNMF_HALS: return launch_hals(X, Pm, G, rows, c.k, s);
-    default: return launch_bpp(G, Pm, rows, c.k, X, c.max_piv, c.warm, c.ctr, c.bppq, s);
+    default: return launch_bpp(G64, Pm, rows, c.k, X, c.max_piv, c.warm, c.ctr, c.bppq, s);
   }
+}
+
+// G = X^T X: FP32 for MU and HALS; for ABPP in FP64 (its solves need the
+// small eigenvalues that an FP32 sum loses) with the FP32 rounding beside it.
+cudaError_t gram(aunmf_handle *h, RunCtx &c, const float *X, int64_t rows, float *G32,
+                 double *G64, cudaStream_t s) {
+  if (c.algo == AUNMF_ABPP)
+    return launch_gram_d(X, rows, c.k, c.k, G64, G32, reinterpret_cast<double *>(c.gpart),
+                         h->max_gram_blocks, s);
+  return launch_gram(X, rows, c.k, c.k, G32, c.gpart, h->max_gram_blocks, s);
 }
 
 // One AU-NMF iteration (see the file header).
@@ -257,20 +268,20 @@ cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const int k = c.k;
   cudaError_t e;
   if ((e = product_aht(h, c, s)) != cudaSuccess) return e;
-  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.W, c.PW, c.GH, m, s)) != cudaSuccess) return e; }
+  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.W, c.PW, c.GH, c.GH64, m, s)) != cudaSuccess) return e; }
   {
     PhaseTimer t(c, s, kPhGram);
-    if ((e = launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s)) != cudaSuccess) return e;
+    if ((e = gram(h, c, c.W, m, c.GW, c.GW64, s)) != cudaSuccess) return e;
   }
   if (c.algo == AUNMF_HALS) {
     PhaseTimer t(c, s, kPhUpdate);
     if ((e = launch_hals_normalise(c.W, m, c.Ht, n, c.GW, k, s)) != cudaSuccess) return e;
   }
   if ((e = product_wta(h, c, s)) != cudaSuccess) return e;
-  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.Ht, c.PHt, c.GW, n, s)) != cudaSuccess) return e; }
+  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.Ht, c.PHt, c.GW, c.GW64, n, s)) != cudaSuccess) return e; }
   {
     PhaseTimer t(c, s, kPhGram);
-    if ((e = launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s)) != cudaSuccess) return e;
+    if ((e = gram(h, c, c.Ht, n, c.GH, c.GH64, s)) != cudaSuccess) return e;
   }
   {
     PhaseTimer t(c, s, kPhOther);
@@ -403,7 +414,7 @@ int aunmf_set_stream(aunmf_handle *h, void *stream) {
 int aunmf_destroy(aunmf_handle *h) {
   if (!h) return AUNMF_E_INVAL;
   cudaStreamSynchronize(h->stream);
-  Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->gpart, &h->dpart, &h->n2a,
+  Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->G64, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
                  &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
                  &h->batch, &h->batch_meta, &h->hA, &h->hW, &h->hH};
@@ -432,7 +443,8 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   ENS(h, h->PHt, sizeof(float) * n * k);
   ENS(h, h->GH, sizeof(float) * k * k);
   ENS(h, h->GW, sizeof(float) * k * k);
-  ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  ENS(h, h->G64, 2 * sizeof(double) * k * k);
+  ENS(h, h->gpart, sizeof(double) * (size_t)h->max_gram_blocks * k * k);
   ENS(h, h->dpart, dpart_bytes(h));
   ENS(h, h->n2a, 2 * sizeof(double));
   ENS(h, h->ctr, sizeof(DevCounters));
@@ -455,6 +467,8 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   c.PHt = P<float>(h->PHt);
   c.GH = P<float>(h->GH);
   c.GW = P<float>(h->GW);
+  c.GH64 = P<double>(h->G64);
+  c.GW64 = c.GH64 + (size_t)k * k;
   c.gpart = P<float>(h->gpart);
   c.dpart = P<double>(h->dpart);
   c.n2a = P<double>(h->n2a);
@@ -495,7 +509,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     int prc = prepare_sparse(h, c, s);
     if (prc != AUNMF_OK) return prc;
   }
-  CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+  CK(h, gram(h, c, c.Ht, n, c.GH, c.GH64, s));
 
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -658,6 +672,25 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
   return AUNMF_OK;
 }
 
+namespace {
+// ABPP step calls: the caller's FP32 Gram widened into the handle's FP64 slot.
+int widen_gram(aunmf_handle *h, const float *G, int k, double **G64) {
+  ENS(h, h->G64, 2 * sizeof(double) * k * k);
+  *G64 = P<double>(h->G64);
+  CK(h, launch_widen(G, k, *G64, h->stream));
+  return AUNMF_OK;
+}
+// Status of an ABPP step from the device counters (synchronises).
+int bpp_status(aunmf_handle *h, DevCounters *ctr) {
+  DevCounters hc{};
+  CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
+  if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;
+  return AUNMF_OK;
+}
+}  // namespace
+
 int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const float *GH,
                    int64_t m, int k, float *H, int64_t n, double eps) {
   if (!h || !W || !PW || !GH || m < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
@@ -673,8 +706,14 @@ int aunmf_update_w(aunmf_handle *h, int algo, float *W, const float *PW, const f
   c.max_piv = 10 * k;
   c.ctr = P<DevCounters>(h->ctr);
   c.bppq = h->bppq.p;
+  double *G64 = nullptr;
+  if (algo == AUNMF_ABPP) {
+    int rc = widen_gram(h, GH, k, &G64);
+    if (rc != AUNMF_OK) return rc;
+  }
   CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
-  CK(h, update(c, W, PW, GH, m, s));
+  CK(h, update(c, W, PW, GH, G64, m, s));
+  if (algo == AUNMF_ABPP) return bpp_status(h, c.ctr);
   if (algo == AUNMF_HALS) {
     ENS(h, h->GW, sizeof(float) * k * k);
     ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
@@ -708,11 +747,17 @@ int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const f
   c.max_piv = 10 * k;
   c.ctr = P<DevCounters>(h->ctr);
   c.bppq = h->bppq.p;
+  double *G64 = nullptr;
+  if (algo == AUNMF_ABPP) {
+    int rc = widen_gram(h, GW, k, &G64);
+    if (rc != AUNMF_OK) return rc;
+  }
   CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
   CK(h, launch_transpose(H, k, n, P<float>(h->Ht), s));
   CK(h, launch_transpose(PH, k, n, P<float>(h->PHt), s));
-  CK(h, update(c, P<float>(h->Ht), P<float>(h->PHt), GW, n, s));
+  CK(h, update(c, P<float>(h->Ht), P<float>(h->PHt), GW, G64, n, s));
   CK(h, launch_transpose(P<float>(h->Ht), n, k, H, s));
+  if (algo == AUNMF_ABPP) return bpp_status(h, c.ctr);
   return AUNMF_OK;
 }
 
@@ -723,8 +768,11 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
   ENS(h, h->ctr, sizeof(DevCounters));
   ENS(h, h->bppq, bpp_scratch_bytes(k, nrhs));
   DevCounters *ctr = P<DevCounters>(h->ctr);
+  double *G64 = nullptr;
+  int rc = widen_gram(h, G, k, &G64);
+  if (rc != AUNMF_OK) return rc;
   CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
-  CK(h, launch_bpp(G, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, 0, ctr, h->bppq.p, s));
+  CK(h, launch_bpp(G64, R, nrhs, k, X, max_pivots > 0 ? max_pivots : 10 * k, 0, ctr, h->bppq.p, s));
   DevCounters hc{};
   CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
@@ -980,10 +1028,10 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     o_[0] = take(sizeof(float) * b.n * b.k);            // Ht
     o_[1] = take(sizeof(float) * b.m * b.k);            // PW
     o_[2] = take(sizeof(float) * b.n * b.k);            // PHt
-    o_[3] = take(sizeof(float) * kk);                   // GH
-    o_[4] = take(sizeof(float) * kk);                   // GW
-    o_[5] = take(sizeof(float) * kk * b.ngw);           // Gram partials (W)
-    o_[6] = take(sizeof(float) * kk * b.ngh);           // Gram partials (Ht)
+    o_[3] = take(sizeof(double) * kk);                  // GH
+    o_[4] = take(sizeof(double) * kk);                  // GW
+    o_[5] = take(sizeof(double) * kk * b.ngw);          // Gram partials (W)
+    o_[6] = take(sizeof(double) * kk * b.ngh);          // Gram partials (Ht)
     o_[7] = take(esz * (size_t)b.m * b.ldx);            // Ax
     o_[8] = take(esz * (size_t)b.n * b.ldat);           // At
     o_[9] = take(esz * 2 * (size_t)b.k * b.ldh);        // Hk
@@ -1009,10 +1057,10 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     b.Ht = reinterpret_cast<float *>(base + o_[0]);
     b.PW = reinterpret_cast<float *>(base + o_[1]);
     b.PHt = reinterpret_cast<float *>(base + o_[2]);
-    b.GH = reinterpret_cast<float *>(base + o_[3]);
-    b.GW = reinterpret_cast<float *>(base + o_[4]);
-    b.gpart_w = reinterpret_cast<float *>(base + o_[5]);
-    b.gpart_h = reinterpret_cast<float *>(base + o_[6]);
+    b.GH = reinterpret_cast<double *>(base + o_[3]);
+    b.GW = reinterpret_cast<double *>(base + o_[4]);
+    b.gpart_w = reinterpret_cast<double *>(base + o_[5]);
+    b.gpart_h = reinterpret_cast<double *>(base + o_[6]);
     b.Ax = base + o_[7];
     b.At = base + o_[8];
     b.Hk = base + o_[9];

@@ -22,8 +22,8 @@ struct BInst {
   int64_t lda;
   float *W;               // m x k (the caller's output array)
   float *Ht, *PW, *PHt;   // n x k, m x k, n x k
-  float *GH, *GW;         // k x k
-  float *gpart_w, *gpart_h;
+  double *GH, *GW;        // k x k, FP64 (products formed exactly, FP64 sums)
+  double *gpart_w, *gpart_h;
   int ngw, ngh;           // Gram partial slots for the m rows of W / n rows of Ht
   void *Ax, *At, *Hk, *Wt;  // rounded copies of A, A^T; split factor copies
   int64_t ldx, ldat, ldh, ldw;

@@ -93,12 +93,12 @@ __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n,
 // Q = G^{-1} in FP64 (one block): Cholesky of G in shared memory, then each
 // thread solves G q_j = e_j for its column j.  *ok = 0 if G is not positive
 // definite or cond_1(G) >= kQMaxCond (the Q-based solves are then not used).
-__device__ __forceinline__ void gram_inverse_block(const float *__restrict__ G32, int k,
+__device__ __forceinline__ void gram_inverse_block(const double *__restrict__ Gd, int k,
                                                    double *__restrict__ Q, int *__restrict__ ok,
                                                    double *sm, int &good) {
   double *L = sm;            // k x k
   double *tmp = sm + k * k;  // one column of k per thread
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) L[e] = (double)G32[e];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) L[e] = Gd[e];
   if (threadIdx.x == 0) good = 1;
   __syncthreads();
   for (int c = 0; c < k; ++c) {  // right-looking, lower triangle
@@ -141,7 +141,7 @@ __device__ __forceinline__ void gram_inverse_block(const float *__restrict__ G32
     for (int j = 0; j < k; ++j) {
       double cg = 0.0, cq = 0.0;
       for (int i = 0; i < k; ++i) {
-        cg += fabs((double)G32[i * k + j]);
+        cg += fabs(Gd[i * k + j]);
         cq += fabs(Q[i * k + j]);
       }
       ng = cg > ng ? cg : ng;
@@ -166,7 +166,7 @@ struct BppWarp {
 
 // Stage G (FP64), Q and |G| (FP32) of one problem into shared memory (block-
 // wide; the caller synchronises) and return warp wib's view.
-__device__ __forceinline__ BppWarp bpp_stage(const float *__restrict__ G32,
+__device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
                                              const double *__restrict__ Qg, const int *q_ok, int k,
                                              double *sm, int wib) {
   const BppLayout lay = bpp_layout(k);
@@ -174,17 +174,17 @@ __device__ __forceinline__ BppWarp bpp_stage(const float *__restrict__ G32,
   double *Q = sm + lay.g_dbl;
   float *Gabs = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    G[e] = (double)G32[e];
+    G[e] = Gd[e];
     Q[e] = Qg[e];
-    Gabs[e] = fabsf(G32[e]);
+    Gabs[e] = (float)fabs(Gd[e]);
   }
   BppWarp w;
   w.G = G;
   w.Q = Q;
   w.Gabs = Gabs;
-  float gmax = 0.f;
-  for (int i = 0; i < k; ++i) gmax = fmaxf(gmax, G32[i * k + i]);
-  w.dead_below = kDead * (double)gmax;
+  double gmax = 0.0;
+  for (int i = 0; i < k; ++i) gmax = fmax(gmax, Gd[i * k + i]);
+  w.dead_below = kDead * gmax;
   w.have_q = *q_ok != 0;
   w.L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
   w.v = w.L + (size_t)lay.kh * lay.ldl;  // small system's right-hand side, then x_F

@@ -28,11 +28,33 @@ struct DevCounters {
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return cudaGetLastError().
 
+// hi + lo += a * b with the product formed exactly (FMA gives its rounding
+// error) and the sum's rounding error kept (Knuth's two-sum): a pair of FP32
+// numbers carrying ~48 bits, at a few FP32 operations per term.
+// The _rn intrinsics keep the compiler from contracting a product and a sum
+// into one FMA, which would break the error terms.
+__device__ __forceinline__ void two_fma_acc(float a, float b, float &hi, float &lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float z = __fsub_rn(s, hi);
+  const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));
+  lo = __fadd_rn(lo, __fadd_rn(t, e));
+  hi = s;
+}
+
 // Gram: partial[b] = sum over rows of block b of X^T X (X rows x k, row-major,
 // leading dimension ldx); then G = sum_b partial[b] in FP64, fixed order.
 cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
                         float *partials, int max_blocks, cudaStream_t s);
 int gram_partial_blocks(int64_t rows, int max_blocks);
+// The same Gram with every product formed exactly in FP64 (FP32 x FP32 fits a
+// double) and summed in FP64: G64 (k x k, FP64) for the BPP solves, and G32 =
+// G64 rounded to FP32 (may be null).  partials: max_blocks * k * k doubles.
+cudaError_t launch_gram_d(const float *X, int64_t rows, int k, int64_t ldx, double *G64,
+                          float *G32, double *partials, int max_blocks, cudaStream_t s);
+// G64 = G32 widened (k x k).
+cudaError_t launch_widen(const float *G32, int k, double *G64, cudaStream_t s);
 
 // SIMT FP32 products.
 //   aht: P_W (m x k, ld k) = A (m x n, lda) * Ht (n x k, ld k)
@@ -67,12 +89,12 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
 // may be null, rows_y rows); GW_ij /= s_i s_j.  Zero norms leave column i as is.
 cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t rows_y, float *GW,
                                   int k, cudaStream_t s);
-// BPP: X(r, :) = argmin_{x>=0} ||C x - b|| given G = C^T C and R(r, :) = C^T b,
-// in FP64.  warm != 0 starts each row from the support of X's current row.
-// scratch: bpp_scratch_bytes(k, rows) bytes of device memory (G^{-1} and a
-// per-row flag for the direct fallback).
+// BPP: X(r, :) = argmin_{x>=0} ||C x - b|| given G = C^T C (FP64) and
+// R(r, :) = C^T b, in FP64.  warm != 0 starts each row from the support of
+// X's current row.  scratch: bpp_scratch_bytes(k, rows) bytes of device
+// memory (G^{-1} and a per-row flag for the direct fallback).
 size_t bpp_scratch_bytes(int k, int64_t rows);
-cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
+cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, float *X,
                        int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s);
 
 // Reductions for the relative residual.

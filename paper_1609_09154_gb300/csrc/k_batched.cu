@@ -199,7 +199,12 @@ __global__ void __launch_bounds__(256)
 }
 
 // Gram partials: item (p, chunk, r0, r1) adds X^T X over rows [r0, r1) of
-// the problem's X (side 0: Ht, side 1: W) into partial slot `chunk`.
+// the problem's X (side 0: Ht, side 1: W) into partial slot `chunk`.  Each
+// thread owns a 4 x 4 tile of the upper triangle (mirrored on output); each
+// 32-row slab's exact products are summed in FP32 pairs (two_fma_acc) and
+// added to FP64 sums, so the Gram keeps the small eigenvalues that the BPP
+// solves need when the factor is ill-conditioned (an FP32 sum would leave
+// them as rounding noise).
 __global__ void __launch_bounds__(256)
     g_gram_partial(const BInst *__restrict__ P, const Item *__restrict__ items, int nitems,
                    int side) {
@@ -209,9 +214,9 @@ __global__ void __launch_bounds__(256)
     const BInst &b = P[I.p];
     const int k = b.k;
     const float *X = side ? b.W : b.Ht;
-    float *out = (side ? b.gpart_w : b.gpart_h) + (int64_t)I.chunk * k * k;
+    double *out = (side ? b.gpart_w : b.gpart_h) + (int64_t)I.chunk * k * k;
     const int kp = (k + 3) & ~3;
-    const int nt = kp / 4, ntiles = nt * (nt + 1) / 2;  // upper triangle of 4 x 4 tiles
+    const int nt = kp / 4, ntiles = nt * (nt + 1) / 2;
     for (int tb = 0; tb < ntiles; tb += blockDim.x) {
       const int tt = tb + threadIdx.x;
       const bool act = tt < ntiles;
@@ -221,9 +226,7 @@ __global__ void __launch_bounds__(256)
         while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
         tj = ti + rem;
       }
-      // each 32-row FP32 sum added to the running sum with Kahan's
-      // compensation (FP64 additions are slow on this part)
-      float sum[4][4] = {}, cmp[4][4] = {};
+      double acc[4][4] = {};
       for (int64_t c0 = I.r0; c0 < I.r1; c0 += 32) {
         const int nr = (int)min((int64_t)32, I.r1 - c0);
         __syncthreads();
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
         if (act) {
-          float part[4][4] = {};
+          float hi[4][4] = {}, lo[4][4] = {};
           for (int rr = 0; rr < nr; ++rr) {
             float av[4], bv[4];
 #pragma unroll
@@ -244,17 +247,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) part[a][c] = fmaf(av[a], bv[c], part[a][c]);
+              for (int c = 0; c < 4; ++c) two_fma_acc(av[a], bv[c], hi[a][c], lo[a][c]);
           }
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const float y = part[a][c] - cmp[a][c];
-              const float t = sum[a][c] + y;
-              cmp[a][c] = (t - sum[a][c]) - y;
-              sum[a][c] = t;
-            }
+            for (int c = 0; c < 4; ++c) acc[a][c] += (double)hi[a][c] + (double)lo[a][c];
         }
       }
       if (act)
@@ -264,9 +262,8 @@ __global__ void __launch_bounds__(256)
           for (int c = 0; c < 4; ++c) {
             const int i = 4 * ti + a, j = 4 * tj + c;
             if (i < k && j < k) {
-              const float v = sum[a][c] - cmp[a][c];
-              out[i * k + j] = v;
-              out[j * k + i] = v;
+              out[i * k + j] = acc[a][c];
+              out[j * k + i] = acc[a][c];
             }
           }
     }
@@ -278,12 +275,12 @@ __global__ void g_gram_reduce(const BInst *__restrict__ P, int side) {
   const BInst &b = P[blockIdx.x];
   const int k = b.k;
   const int nparts = side ? b.ngw : b.ngh;
-  const float *part = side ? b.gpart_w : b.gpart_h;
-  float *G = side ? b.GW : b.GH;
+  const double *part = side ? b.gpart_w : b.gpart_h;
+  double *G = side ? b.GW : b.GH;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += (double)part[(int64_t)c * k * k + e];
-    G[e] = (float)s;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * k * k + e];
+    G[e] = s;
   }
 }
 
@@ -351,8 +348,8 @@ __global__ void __launch_bounds__(256)
     if (!__syncthreads_or(any)) continue;
     const int ldl = k | 1;
     double *G = sm;
-    const float *G32 = side ? b.GW : b.GH;
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = (double)G32[e];
+    const double *Gd = side ? b.GW : b.GH;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = Gd[e];
     __syncthreads();
     double *L = sm + (size_t)k * k + (size_t)wib * ((size_t)k * ldl + 3 * (size_t)k);
     double *v = L + (size_t)k * ldl;
@@ -410,7 +407,7 @@ __global__ void g_relres_final(const BInst *__restrict__ P, DevCounters *ctr, in
   cross = block_sum(cross, ws);
   const int k = b.k;
   double quad = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)b.GW[e], (double)b.GH[e], quad);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma(b.GW[e], b.GH[e], quad);
   quad = block_sum(quad, ws);
   if (threadIdx.x == 0) {
     const double a2 = b.n2a[0];

@@ -39,13 +39,13 @@ using namespace bpp;
 
 template <int KT>
 __global__ void __launch_bounds__(32 * kBppWarps, 1)
-    k_bpp(const float *__restrict__ G32, const double *__restrict__ Qg, const int *__restrict__ q_ok,
+    k_bpp(const double *__restrict__ Gd, const double *__restrict__ Qg, const int *__restrict__ q_ok,
           const float *__restrict__ R, int64_t rows, int k, float *__restrict__ X, int warm,
           int max_piv, DevCounters *ctr, uint8_t *__restrict__ redo) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
-  const BppWarp w = bpp_stage(G32, Qg, q_ok, k, sm, wib);
+  const BppWarp w = bpp_stage(Gd, Qg, q_ok, k, sm, wib);
   __syncthreads();
   long long piv_total = 0, nonconv = 0;
   for (int64_t row = (int64_t)blockIdx.x * nwb + wib; row < rows;
@@ -67,22 +67,22 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
   }
 }
 
-__global__ void k_gram_inverse(const float *__restrict__ G32, int k, double *__restrict__ Q,
+__global__ void k_gram_inverse(const double *__restrict__ Gd, int k, double *__restrict__ Q,
                                int *__restrict__ ok) {
   extern __shared__ double sm[];
   __shared__ int good;
-  gram_inverse_block(G32, k, Q, ok, sm, good);
+  gram_inverse_block(Gd, k, Q, ok, sm, good);
 }
 
 template <int KT>
 __global__ void __launch_bounds__(256)
-    k_bpp_direct(const float *__restrict__ G32, const float *__restrict__ R, int64_t rows, int k,
+    k_bpp_direct(const double *__restrict__ Gd, const float *__restrict__ R, int64_t rows, int k,
                  float *__restrict__ X, int max_piv, DevCounters *ctr,
                  const uint8_t *__restrict__ redo) {
   extern __shared__ double sm[];
   const int ldl = k | 1;
   double *G = sm;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = (double)G32[e];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = Gd[e];
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
@@ -128,7 +128,7 @@ size_t bpp_scratch_bytes(int k, int64_t rows) {
   return sizeof(double) * (size_t)k * k + 256 + (size_t)rows;
 }
 
-cudaError_t launch_bpp(const float *G, const float *R, int64_t rows, int k, float *X,
+cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, float *X,
                        int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
   if (k < 1 || k > AUNMF_BPP_K_MAX) return cudaErrorInvalidValue;

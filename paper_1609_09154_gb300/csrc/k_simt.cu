@@ -123,6 +123,127 @@ __global__ void __launch_bounds__(kGramThreads)
   }
 }
 
+// FP64-accurate Gram partials: the same tiles and slabs; within a 32-row
+// slab each product is formed exactly and summed in an FP32 pair (hi, lo)
+// (two_fma_acc), and the slab's pair is added to an FP64 running sum.  The
+// result is accurate to ~1e-14 relative, so a Gram whose smallest
+// eigenvalues sit below FP32's resolution of its largest (condition beyond
+// ~1e7, which ABPP's factors reach on uniform low-rank data) stays positive
+// definite; FP64 FMAs per term would run at the FP64 pipe's rate (~1/64 of
+// FP32 on this part).
+__global__ void __launch_bounds__(kGramThreads)
+    k_gram_partial_d(const float *__restrict__ X, int64_t rows, int k, int64_t ldx, int64_t chunk,
+                     double *__restrict__ partials) {
+  extern __shared__ float sX[];  // [kGramRows][kp]
+  constexpr int kPre = (kGramRows * 64 + kGramThreads - 1) / kGramThreads;
+  const int kp = (k + 3) & ~3;
+  const int nt = kp / 4, ntiles = nt * (nt + 1) / 2;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(rows, r0 + chunk);
+  double *out = partials + (int64_t)blockIdx.x * k * k;
+  const int slab = kGramRows * kp;
+  const bool pre = slab <= kPre * kGramThreads;
+  for (int tb = 0; tb < ntiles; tb += kGramThreads) {
+    const int t = tb + threadIdx.x;
+    const bool act = t < ntiles;
+    int ti = 0, tj = 0;
+    if (act) {
+      int rem = t;
+      while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+      tj = ti + rem;
+    }
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    float nxt[kPre];
+    auto fetch = [&](int64_t c0) {
+      const int nr = (int)min((int64_t)kGramRows, r1 - c0);
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) {
+        const int idx = threadIdx.x + q * kGramThreads;
+        const int rr = idx / kp, cc = idx - rr * kp;
+        nxt[q] = (idx < slab && rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+      }
+    };
+    if (pre && r0 < r1) fetch(r0);
+    for (int64_t c0 = r0; c0 < r1; c0 += kGramRows) {
+      const int nr = (int)min((int64_t)kGramRows, r1 - c0);
+      __syncthreads();
+      if (pre) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+          const int idx = threadIdx.x + q * kGramThreads;
+          if (idx < slab) sX[idx] = nxt[q];
+        }
+        if (c0 + kGramRows < r1) fetch(c0 + kGramRows);
+      } else {
+        for (int idx = threadIdx.x; idx < slab; idx += kGramThreads) {
+          const int rr = idx / kp, cc = idx - rr * kp;
+          sX[idx] = (rr < nr && cc < k) ? X[(c0 + rr) * ldx + cc] : 0.f;
+        }
+      }
+      __syncthreads();
+      if (act) {
+        float hi[4][4] = {}, lo[4][4] = {};
+        for (int rr = 0; rr < nr; ++rr) {
+          const float4 a = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * ti]);
+          const float4 b = *reinterpret_cast<const float4 *>(&sX[rr * kp + 4 * tj]);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) two_fma_acc(av[p], bv[q], hi[p][q], lo[p][q]);
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += (double)hi[p][q] + (double)lo[p][q];
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = 4 * ti + p, j = 4 * tj + q;
+          if (i < k && j < k) {
+            out[i * k + j] = acc[p][q];
+            out[j * k + i] = acc[p][q];
+          }
+        }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_gram_reduce_d(const double *__restrict__ partials, int nb, int k, double *__restrict__ G64,
+                    float *__restrict__ G32) {
+  __shared__ double sw[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kk = k * k;
+  const int e = blockIdx.x * 32 + lane;
+  const int per = (nb + 7) / 8;
+  const int b0 = w * per, b1 = min(nb, b0 + per);
+  double acc = 0.0;
+  if (e < kk)
+    for (int b = b0; b < b1; ++b) acc += partials[(int64_t)b * kk + e];
+  sw[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && e < kk) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += sw[q][lane];
+    G64[e] = s;
+    if (G32) G32[e] = (float)s;
+  }
+}
+
+__global__ void k_widen(const float *__restrict__ G32, int kk, double *__restrict__ G64) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kk; e += gridDim.x * blockDim.x)
+    G64[e] = (double)G32[e];
+}
+
 // G_e = sum_b partials[b]_e in FP64: 32 entries per block; warp w sums the
 // w-th eighth of the blocks (b ascending), and the eight sums are added in
 // warp order, so the result does not depend on scheduling.
@@ -163,6 +284,24 @@ cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float 
   k_gram_partial<<<nb, kGramThreads, smem, s>>>(X, rows, k, ldx, chunk, partials);
   k_gram_reduce<<<(k * k + 31) / 32, 256, 0, s>>>(partials, nb, k, G);
   g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_d(const float *X, int64_t rows, int k, int64_t ldx, double *G64,
+                          float *G32, double *partials, int max_blocks, cudaStream_t s) {
+  const int nb = gram_partial_blocks(rows, max_blocks);
+  const int64_t chunk = (rows + nb - 1) / nb;
+  const int kp = (k + 3) & ~3;
+  const size_t smem = sizeof(float) * kGramRows * kp;
+  k_gram_partial_d<<<nb, kGramThreads, smem, s>>>(X, rows, k, ldx, chunk, partials);
+  k_gram_reduce_d<<<(k * k + 31) / 32, 256, 0, s>>>(partials, nb, k, G64, G32);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float *G32, int k, double *G64, cudaStream_t s) {
+  k_widen<<<(k * k + 255) / 256, 256, 0, s>>>(G32, k * k, G64);
+  g_launches += 1;
   return cudaGetLastError();
 }
 
