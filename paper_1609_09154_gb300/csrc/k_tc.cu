@@ -254,7 +254,8 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &on
 
 // REGACC: every problem of the launch is a pair problem with BN <= 128
 // (k <= 64); each epilogue thread keeps its row's <= 64 sums in registers.
-// Otherwise the sums live in shared memory (or in P).
+// Otherwise (one TMEM column per output) the first 64 sums of a row stay in
+// registers and the rest live in shared memory (or in P).
 template <bool BF16, bool REGACC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmProblem one, const GemmProblem *__restrict__ group,
@@ -367,8 +368,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: warps 2..9; warp w drains TMEM lane quarter
     // q = w % 4 of accumulator half (w - 2) / 4.  Row rl = half * 128 +
     // q * 32 + lane of the unit belongs to one thread for every chunk.
-    // TMEM is read in groups of 64 columns (one wait per group) up to BN
-    // rounded up to 64; shared accumulator rows are padded to match, so the
+    // TMEM is read in groups of 32 columns (one wait per group) up to BN
+    // rounded up to 32; shared accumulator rows are padded to match, so the
     // columns past BN (never copied out) need no guard.
     const int q = warp & 3, half = (warp - 2) >> 2;
     const int rl = half * 128 + q * 32 + lane;
@@ -382,8 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t tile = v / p->S, sp = v % p->S;
       const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
       const int64_t M = p->M;
-      const int k = p->k, BN = p->BN, pair = p->pair;
-      const int W = (BN + 63) & ~63;
+      const int k = p->k, BN = p->BN;
       const int64_t row = tile * kTileM + rl;
       float *Pp = p->P + sp * M * k;
       const bool live = row < M;
@@ -421,62 +421,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         continue;
       }
+      // one TMEM column per output (no split): columns 0..63 summed in
+      // registers, the rest in the shared accumulator (row stride acc_ld,
+      // column c at c - 64) or, without one, in P itself
+      const int W32 = (BN + 31) & ~31;
+      float racc[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) racc[j] = 0.f;
       bool first = true;
       for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
         if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr =
             tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
-        for (int g0 = 0; g0 < W; g0 += 64) {
-          uint32_t r[64];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) tmem_ld16_async(taddr + (uint32_t)(g0 + 16 * t), r + 16 * t);
+        for (int g = 0; g < 2; ++g) {
+          if (32 * g >= BN) break;
+          uint32_t r[32];
+          tmem_ld16_async(taddr + (uint32_t)(32 * g), r);
+          tmem_ld16_async(taddr + (uint32_t)(32 * g + 16), r + 16);
+          tmem_wait_ld(r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) racc[32 * g + j] += __uint_as_float(r[j]);
+        }
+        for (int g0 = 64; g0 < W32; g0 += 32) {
+          uint32_t r[32];
+          tmem_ld16_async(taddr + (uint32_t)g0, r);
+          tmem_ld16_async(taddr + (uint32_t)(g0 + 16), r + 16);
           tmem_wait_ld(r);
           if (arow) {
-            if (pair) {
-              // C_i = acc_2i + acc_2i+1 (hi and lo parts of the factor)
-              float *d = arow + (g0 >> 1);
-              float x[32];
+            // padded rows: whole 32-column groups, a group's loads before its
+            // stores (a guard per element serialises load -> add -> store)
+            float *d = arow + (g0 - 64);
+            float x[32];
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                x[j] = __uint_as_float(r[2 * j]) + __uint_as_float(r[2 * j + 1]);
-              if (!first) {
+            for (int jj = 0; jj < 32; ++jj) x[jj] = __uint_as_float(r[jj]);
+            if (!first) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) x[j] += d[j];
-              }
-#pragma unroll
-              for (int j = 0; j < 32; ++j) d[j] = x[j];
-            } else {
-              float *d = arow + g0;
-              float x[64];
-#pragma unroll
-              for (int j = 0; j < 64; ++j) x[j] = __uint_as_float(r[j]);
-              if (!first) {
-#pragma unroll
-                for (int j = 0; j < 64; ++j) x[j] += d[j];
-              }
-#pragma unroll
-              for (int j = 0; j < 64; ++j) d[j] = x[j];
+              for (int jj = 0; jj < 32; ++jj) x[jj] += d[jj];
             }
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) d[jj] = x[jj];
           } else if (live) {
-            // accumulate in P itself: per-element guards (k is not padded)
             float *dst = Pp + row * k;
-            if (pair) {
-              const int o0 = g0 >> 1;
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (o0 + j < k) {
-                  const float x = __uint_as_float(r[2 * j]) + __uint_as_float(r[2 * j + 1]);
-                  dst[o0 + j] = first ? x : dst[o0 + j] + x;
-                }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 64; ++j)
-                if (g0 + j < k) {
-                  const float x = __uint_as_float(r[j]);
-                  dst[g0 + j] = first ? x : dst[g0 + j] + x;
-                }
-            }
+            for (int jj = 0; jj < 32; ++jj)
+              if (g0 + jj < k) {
+                const float x = __uint_as_float(r[jj]);
+                dst[g0 + jj] = first ? x : dst[g0 + jj] + x;
+              }
           }
         }
         tc_fence_before();
@@ -485,18 +478,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         first = false;
       }
       if (!ok) break;
-      if (arow || first) {
-        // copy the warp's 32 rows out (contiguous in P); a unit without K
-        // blocks writes zeros
-        __syncwarp();
-        const int rl0 = half * 128 + q * 32;
-        const int64_t r0 = tile * kTileM + rl0;
-        const int64_t nr = min((int64_t)32, M - r0);
-        float *dg = Pp + r0 * k;
-        for (int64_t rr = 0; rr < nr; ++rr)
-          for (int c = lane; c < k; c += 32)
-            dg[rr * k + c] = first ? 0.f : acc_s[(size_t)(rl0 + rr) * L.acc_ld + c];
-        __syncwarp();
+      if (live) {
+        float *dg = Pp + row * k;
+#pragma unroll
+        for (int o = 0; o < 64; ++o)
+          if (o < k) dg[o] = racc[o];
+        if (arow || first)
+          for (int o = 64; o < k; ++o) dg[o] = first ? 0.f : arow[o - 64];
       }
     }
   }
@@ -914,14 +902,16 @@ bool fill_problem(GemmProblem *p, const void *X, int64_t M, int64_t K, int64_t l
 
 int64_t problem_units(const GemmProblem &p) { return ((p.M + kTileM - 1) / kTileM) * p.S; }
 
-// Accumulator row width that a problem needs in shared memory: its MMA
-// columns rounded up to the 64-column drain group, halved for a pair
-// problem (C_i = acc_2i + acc_2i+1).
+// Accumulator row width that a problem needs in shared memory: none for a
+// pair problem (its <= 64 sums stay in registers); otherwise its MMA columns
+// past the first 64 (kept in registers), rounded up to the 32-column drain
+// group.
 int acc_width(const GemmProblem &p) {
-  if (p.pair && p.BN <= 128) return 0;  // sums in registers
-  const int w = (p.BN + 63) & ~63;
-  return p.pair ? w / 2 : w;
+  if (p.pair && p.BN <= 128) return 0;
+  const int w = ((p.BN + 31) & ~31) - 64;
+  return w > 0 ? w : 0;
 }
+bool all_pair(const GemmProblem &p) { return p.pair && p.BN <= 128; }
 
 // Shape of a launch whose problems have at most BNmax MMA columns and whose
 // shared accumulator rows need at most accw floats.  The FP32 accumulator
@@ -931,7 +921,8 @@ int acc_width(const GemmProblem &p) {
 // (L2-resident), with longer chunks.  TMEM holds nbuf chunk accumulators of
 // 2 x BNmax columns; the drain reads up to BN rounded up to 64 columns past
 // the start of the last half, which must stay inside the allocation.
-bool launch_shape(GemmLaunch *L, int BNmax, int accw, int64_t units, int nprob, int *err) {
+bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units, int nprob,
+                  int *err) {
   L->units = units;
   L->nprob = nprob;
   L->BNmax = BNmax;
@@ -946,8 +937,8 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, int64_t units, int nprob, 
   const size_t budget = 225 * 1024 - 1024 - 256;
   const int ld = accw | 1;
   const size_t acc = (size_t)kTileM * ld * sizeof(float);
-  L->regacc = accw == 0 ? 1 : 0;
-  if (L->regacc) {
+  L->regacc = pairs ? 1 : 0;
+  if (accw == 0) {
     L->acc_ld = 0;
     L->nstages = (int)(budget / sbytes);
     L->chunk_kb = kChunkKBReg;
@@ -992,7 +983,7 @@ cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const 
   if (!fill_problem(&p, X, M, K, ldx, Y, k, ldy, split, bf16, parts, S))
     return cudaErrorInvalidValue;
   GemmLaunch L;
-  if (!launch_shape(&L, p.BN, acc_width(p), problem_units(p), 0, err))
+  if (!launch_shape(&L, p.BN, acc_width(p), all_pair(p), problem_units(p), 0, err))
     return cudaErrorInvalidValue;
   return launch_kernel(p, nullptr, L, bf16, s);
 }
@@ -1014,12 +1005,14 @@ cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, 
                               int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s) {
   const GemmProblem *hp = reinterpret_cast<const GemmProblem *>(host_first);
   int accw = 0;
+  bool pairs = true;
   for (int i = 0; i < nprob; ++i) {
     const int w = acc_width(hp[i]);
     accw = w > accw ? w : accw;
+    pairs = pairs && all_pair(hp[i]);
   }
   GemmLaunch L;
-  if (!launch_shape(&L, BNmax, accw, units, nprob, err)) return cudaErrorInvalidValue;
+  if (!launch_shape(&L, BNmax, accw, pairs, units, nprob, err)) return cudaErrorInvalidValue;
   return launch_kernel(*reinterpret_cast<const GemmProblem *>(host_first),
                        reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
 }
