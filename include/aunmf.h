@@ -95,6 +95,8 @@ typedef struct {
   int64_t launches;         /* kernels this call launched (graph replays counted per kernel) */
   int tuned_bpp_warps;      /* aunmf_run_batched: autotuned BPP work tile (warps per block, */
   int tuned_bpp_rows;       /*   rows per warp per item)                                    */
+  int64_t bpp_redone;       /* right-hand sides the fast BPP solver handed to the direct    */
+                            /*   (cold-start, full-size Cholesky) fallback                  */
 } aunmf_info;
 
 /* ---- handle -------------------------------------------------------------- */

@@ -61,6 +61,7 @@ class Info(ctypes.Structure):
         ("ms_gram", ctypes.c_float), ("ms_other", ctypes.c_float),
         ("n_aht", ctypes.c_int), ("n_wta", ctypes.c_int), ("launches", ctypes.c_int64),
         ("tuned_bpp_warps", ctypes.c_int), ("tuned_bpp_rows", ctypes.c_int),
+        ("bpp_redone", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -549,6 +549,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     info->bpp_pivots = hc.bpp_pivots;
     info->bpp_nonconverged = hc.bpp_nonconv;
     info->bpp_numeric = hc.bpp_numeric;
+    info->bpp_redone = hc.bpp_redo;
     info->iters_done = iters;
     info->launches = g_launches - launches0 + graph_launches;
     cudaEventElapsedTime(&info->ms_total, t0, t1);
@@ -1037,7 +1038,8 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     o_[9] = take(esz * 2 * (size_t)b.k * b.ldh);        // Hk
     o_[10] = take(esz * 2 * (size_t)b.k * b.ldw);       // Wt
     o_[11] = take(sizeof(double) * kk);                 // Q
-    o_[12] = take(sizeof(int));                         // q_ok
+    o_[12] = take(2 * sizeof(int));                     // q_ok, factorisation flag
+    o_[16] = take(sizeof(double) * (kk + 2 * b.k));     // L, 1 / diag(L), column sums
     o_[13] = take(mx);                                  // redo
     o_[14] = take(2 * sizeof(double));                  // n2a
     o_[15] = take(sizeof(double) * b.nr);               // residual partials
@@ -1067,6 +1069,7 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     b.Wt = base + o_[10];
     b.Q = reinterpret_cast<double *>(base + o_[11]);
     b.q_ok = reinterpret_cast<int *>(base + o_[12]);
+    b.Lq = reinterpret_cast<double *>(base + o_[16]);
     b.redo = base + o_[13];
     b.n2a = reinterpret_cast<double *>(base + o_[14]);
     b.rpart = reinterpret_cast<double *>(base + o_[15]);
@@ -1291,6 +1294,7 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     info->bpp_pivots = hc.bpp_pivots;
     info->bpp_nonconverged = hc.bpp_nonconv;
     info->bpp_numeric = hc.bpp_numeric;
+    info->bpp_redone = hc.bpp_redo;
     info->iters_done = iters;
     cudaEventElapsedTime(&info->ms_total, t0, t1);
     info->launches = g_launches - launches0 + graph_launches;

@@ -28,7 +28,8 @@ struct BInst {
   void *Ax, *At, *Hk, *Wt;  // rounded copies of A, A^T; split factor copies
   int64_t ldx, ldat, ldh, ldw;
   double *Q;              // G^{-1} of the current update (FP64)
-  int *q_ok;
+  double *Lq;             // its Cholesky factor (k x k), 1 / diag (k), column sums of |Q| (k)
+  int *q_ok;              // [0]: Q usable; [1]: the factorisation succeeded
   uint8_t *redo;          // rows flagged for the direct BPP fallback
   double *n2a;            // {||A||^2, 2 <round(A) - A, A>}
   double *rpart;          // residual partials

@@ -11,6 +11,11 @@
 namespace aunmf {
 namespace bpp {
 
+// G and Q = G^{-1} are symmetric; the loops below read them as G[l][j] with
+// the lane on j (consecutive addresses) rather than G[j][l], whose stride of
+// k elements puts a warp's reads in a few shared-memory banks (32-way
+// conflicts at k = 64).
+
 constexpr double kBppYTol = 1e-11;
 // An index whose Gram diagonal is <= kDead of the largest (a zero column of
 // the fixed factor, which ABPP can produce) never becomes passive: the normal
@@ -60,7 +65,7 @@ __device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int
     if (!(d > 0.0)) return false;
     const double inv = rsqrt(d);
     for (int a = c + 1 + lane; a < n; a += 32) {
-      double s = Mg[I[a] * k + I[c]];
+      double s = Mg[I[c] * k + I[a]];  // symmetric: lanes read along a row
       for (int t = 0; t < c; ++t) s = fma(-L[a * ldl + t], L[c * ldl + t], s);
       L[a * ldl + c] = s * inv;
     }
@@ -90,67 +95,112 @@ __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n,
   }
 }
 
-// Q = G^{-1} in FP64 (one block): Cholesky of G in shared memory, then each
-// thread solves G q_j = e_j for its column j.  *ok = 0 if G is not positive
-// definite or cond_1(G) >= kQMaxCond (the Q-based solves are then not used).
-__device__ __forceinline__ void gram_inverse_block(const double *__restrict__ Gd, int k,
-                                                   double *__restrict__ Q, int *__restrict__ ok,
-                                                   double *sm, int &good) {
-  double *L = sm;            // k x k
-  double *tmp = sm + k * k;  // one column of k per thread
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) L[e] = Gd[e];
+// Q = G^{-1} in three steps, spread over the GPU (a single block doing it
+// serially spent ~0.5 ms per update in FP64 latency):
+//   chol_block:   L = chol(G) (lower, row-major k x k) and invd = 1 / diag(L),
+//                 one block; ok = 0 on a non-positive pivot;
+//   inv_col_warp: column j of Q by forward and back substitution against
+//                 e_j, one warp per column (lane i owns rows i, i + 32), and
+//                 the column's sum of |Q_ij|;
+//   inv_check:    q_ok = ok and cond_1(G) = ||G||_1 ||Q||_1 < kQMaxCond.
+__device__ __forceinline__ void chol_block(const double *__restrict__ G, int k,
+                                           double *__restrict__ Lg, double *__restrict__ invd,
+                                           int *__restrict__ ok, double *A) {
+  __shared__ int good;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) A[e] = G[e];
   if (threadIdx.x == 0) good = 1;
   __syncthreads();
-  for (int c = 0; c < k; ++c) {  // right-looking, lower triangle
+  for (int c = 0; c < k; ++c) {
     if (threadIdx.x == 0) {
-      const double d = L[c * k + c];
+      const double d = A[c * k + c];
       if (!(d > 0.0)) good = 0;
-      L[c * k + c] = d > 0.0 ? sqrt(d) : 1.0;
+      const double r = d > 0.0 ? rsqrt(d) : 1.0;
+      A[c * k + c] = r;  // reciprocal of L_cc
     }
     __syncthreads();
-    const double lcc = L[c * k + c];
-    for (int a = c + 1 + threadIdx.x; a < k; a += blockDim.x) L[a * k + c] /= lcc;
+    const double r = A[c * k + c];
+    for (int a = c + 1 + threadIdx.x; a < k; a += blockDim.x) A[a * k + c] *= r;
     __syncthreads();
     const int w = k - c - 1;
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
       const int a = c + 1 + e / w, b = c + 1 + e % w;
-      if (b <= a) L[a * k + b] -= L[a * k + c] * L[b * k + c];
+      if (b <= a) A[a * k + b] = fma(-A[a * k + c], A[b * k + c], A[a * k + b]);
     }
     __syncthreads();
   }
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double *v = tmp + (size_t)threadIdx.x * k;
-    for (int i = 0; i < k; ++i) v[i] = (i == j) ? 1.0 : 0.0;
-    for (int i = 0; i < k; ++i) {  // L v' = e_j
-      double s = v[i];
-      for (int t = 0; t < i; ++t) s -= L[i * k + t] * v[t];
-      v[i] = s / L[i * k + i];
-    }
-    for (int i = k - 1; i >= 0; --i) {  // L^T q = v'
-      double s = v[i];
-      for (int t = i + 1; t < k; ++t) s -= L[t * k + i] * v[t];
-      v[i] = s / L[i * k + i];
-    }
-    for (int i = 0; i < k; ++i) Q[i * k + j] = v[i];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e / k, b = e % k;
+    Lg[e] = b < a ? A[e] : 0.0;
+    if (a == b) invd[a] = A[e];
   }
-  __syncthreads();
-  // cond_1(G) = ||G||_1 ||Q||_1 (max column sums): solves through Q lose
-  // about log10(cond) digits, so Q is used only for well-conditioned G
-  if (threadIdx.x == 0) {
-    double ng = 0.0, nq = 0.0;
-    for (int j = 0; j < k; ++j) {
-      double cg = 0.0, cq = 0.0;
-      for (int i = 0; i < k; ++i) {
-        cg += fabs(Gd[i * k + j]);
-        cq += fabs(Q[i * k + j]);
-      }
-      ng = cg > ng ? cg : ng;
-      nq = cq > nq ? cq : nq;
-    }
-    *ok = (good && ng * nq < kQMaxCond) ? 1 : 0;
-  }
+  if (threadIdx.x == 0) *ok = good;
 }
 
+__device__ __forceinline__ void inv_col_warp(const double *__restrict__ Lg,
+                                             const double *__restrict__ invd, int k, int j,
+                                             double *__restrict__ Q, double *__restrict__ colsum) {
+  const int lane = threadIdx.x & 31;
+  double w[2], acc[2] = {0.0, 0.0};
+  // forward: w_i = (e_ij - sum_{t < i} L_it w_t) / L_ii
+  for (int t = 0; t < k; ++t) {
+    const int o = t >> 5, ol = t & 31;
+    double wt = 0.0;
+    if (lane == ol) {
+      const double e = t == j ? 1.0 : 0.0;
+      wt = (e - acc[o]) * invd[t];
+      w[o] = wt;
+    }
+    wt = __shfl_sync(0xffffffffu, wt, ol);
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int i = lane + 32 * s2;
+      if (i > t && i < k) acc[s2] = fma(Lg[i * k + t], wt, acc[s2]);
+    }
+  }
+  // back: q_i = (w_i - sum_{t > i} L_ti q_t) / L_ii
+  double q[2];
+  acc[0] = acc[1] = 0.0;
+  for (int t = k - 1; t >= 0; --t) {
+    const int o = t >> 5, ol = t & 31;
+    double qt = 0.0;
+    if (lane == ol) {
+      qt = (w[o] - acc[o]) * invd[t];
+      q[o] = qt;
+    }
+    qt = __shfl_sync(0xffffffffu, qt, ol);
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int i = lane + 32 * s2;
+      if (i < t) acc[s2] = fma(Lg[t * k + i], qt, acc[s2]);
+    }
+  }
+  double cs = 0.0;
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    const int i = lane + 32 * s2;
+    if (i < k) {
+      Q[i * k + j] = q[s2];
+      cs += fabs(q[s2]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+  if (lane == 0) colsum[j] = cs;
+}
+
+__device__ __forceinline__ void inv_check(const double *__restrict__ G,
+                                          const double *__restrict__ colsum, int k, const int *ok,
+                                          int *__restrict__ q_ok) {
+  if (threadIdx.x != 0) return;
+  double ng = 0.0, nq = 0.0;
+  for (int c = 0; c < k; ++c) {
+    double cg = 0.0;
+    for (int i = 0; i < k; ++i) cg += fabs(G[i * k + c]);
+    ng = cg > ng ? cg : ng;
+    nq = colsum[c] > nq ? colsum[c] : nq;
+  }
+  *q_ok = (*ok && ng * nq < kQMaxCond) ? 1 : 0;
+}
 
 // Shared-memory view of one warp's BPP state (fast kernel).
 struct BppWarp {
@@ -232,16 +282,11 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
       tau[t] = kBppYTol * fabs(rr[t]);
     }
     __syncwarp();
-    // z = G^{-1} r, shared by every exchange of this right-hand side
+    // z = G^{-1} r, shared by every exchange of this right-hand side that
+    // takes the Q route; formed on the first such exchange (k^2 FP64 FMAs,
+    // as many as a k/2-sized factorisation)
     double z[KT];
-#pragma unroll
-    for (int t = 0; t < KT; ++t) {
-      const int j = lane + 32 * t;
-      double acc = 0.0;
-      if (have_q && j < k)
-        for (int l = 0; l < k; ++l) acc = fma(Q[j * k + l], rs[l], acc);
-      z[t] = acc;
-    }
+    bool have_z = false;
     int alpha = 3, beta = k + 1, it = 0;
     bool failed_numeric = false, failed_cap = false;
     bool need_solve = __any_sync(0xffffffffu, any);
@@ -279,6 +324,17 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
         } else {
           // ---- through Q = G^{-1} and z = Q r: the constrained solution has
           // Q_BB y_B = -z_B and x_F = z_F + Q_FB y_B (y_F = 0, x_B = 0)
+          if (!have_z) {
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              double acc = 0.0;
+              if (j < k)
+                for (int l = 0; l < k; ++l) acc = fma(Q[l * k + j], rs[l], acc);
+              z[t] = acc;
+            }
+            have_z = true;
+          }
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
@@ -292,7 +348,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             const int j = lane + 32 * t;
             double s = z[t];
             if (j < k && pas[t])
-              for (int b = 0; b < nb; ++b) s = fma(-Q[j * k + Bl[b]], v[b], s);
+              for (int b = 0; b < nb; ++b) s = fma(-Q[Bl[b] * k + j], v[b], s);
             x[t] = (j < k && pas[t]) ? s : 0.0;
             if (j < k && !pas[t]) y[t] = -v[posb[t]];
           }
@@ -317,11 +373,11 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             tau[t] = 0.0;
           } else {
             float mag = fabsf((float)rr[t]);
-            for (int a = 0; a < nf; ++a) mag = fmaf(Gabs[j * k + Fl[a]], xa[a], mag);
+            for (int a = 0; a < nf; ++a) mag = fmaf(Gabs[Fl[a] * k + j], xa[a], mag);
             tau[t] = kBppYTol * (double)mag;
             if (direct) {
               double s = -rr[t];
-              for (int a = 0; a < nf; ++a) s = fma(G[j * k + Fl[a]], v[a], s);
+              for (int a = 0; a < nf; ++a) s = fma(G[Fl[a] * k + j], v[a], s);
               y[t] = s;
             }
           }
@@ -358,10 +414,14 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
       }
       need_solve = true;
     }
+    // a row handed to the fallback keeps its previous iterate, whose support
+    // the fallback starts from
+    if (!failed_numeric) {
 #pragma unroll
-    for (int t = 0; t < KT; ++t) {
-      const int j = lane + 32 * t;
-      if (j < k) X[row * k + j] = (float)x[t];
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        if (j < k) X[row * k + j] = (float)x[t];
+      }
     }
     *failed_numeric_out = failed_numeric;
     *failed_cap_out = failed_cap;
@@ -371,12 +431,13 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
 // Fallback for the rows the fast kernel flagged (a non-positive pivot in a
 // k/2-sized factorisation, or a passive set too large for it while Q is not
 // in use because G is not numerically positive definite or is badly
-// conditioned): the same exchange rule from a cold start, every passive
-// system solved by a Cholesky factorisation of G_FF of any size.
+// conditioned): the same exchange rule, from the support of the row's
+// previous iterate when warm (else from the empty passive set), every
+// passive system solved by a Cholesky factorisation of G_FF of any size.
 template <int KT>
 __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, double *L, double *v,
                                               double *rs, int *Fl, const float *__restrict__ R,
-                                              int64_t row, int k, float *__restrict__ X,
+                                              int64_t row, int k, float *__restrict__ X, int warm,
                                               int max_piv, bool *failed_numeric_out,
                                               bool *failed_cap_out) {
   const int lane = threadIdx.x & 31;
@@ -384,50 +445,34 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
   const unsigned lt_mask = (1u << lane) - 1u;
   double gmax = 0.0;
   for (int i = 0; i < k; ++i) gmax = fmax(gmax, G[i * k + i]);
-    double rr[KT], x[KT], y[KT], tau[KT];
-    bool pas[KT], dead[KT];
+  double rr[KT], x[KT], y[KT], tau[KT];
+  bool pas[KT], dead[KT];
+  int it = 0;
+  bool failed_numeric = false, failed_cap = false;
+  // a warm start whose first factorisation fails is retried from the empty
+  // passive set
+  for (int attempt = warm ? 0 : 1; attempt < 2; ++attempt) {
+  bool any = false;
 #pragma unroll
-    for (int t = 0; t < KT; ++t) {
-      const int j = lane + 32 * t;
-      rr[t] = j < k ? (double)R[row * k + j] : 0.0;
-      if (j < k) rs[j] = rr[t];
-      dead[t] = !(j < k && G[j * k + j] > kDead * gmax);
-      pas[t] = false;
-      x[t] = 0.0;
-      y[t] = -rr[t];
-      tau[t] = kBppYTol * fabs(rr[t]);
-    }
-    __syncwarp();
-    int alpha = 3, beta = k + 1, it = 0;
-    bool failed_numeric = false, failed_cap = false;
-    for (;;) {
-      bool inf[KT];
-      unsigned bal[KT];
-      int nv = 0;
-#pragma unroll
-      for (int t = 0; t < KT; ++t) {
-        const int j = lane + 32 * t;
-        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (!dead[t] && y[t] < -tau[t]));
-        bal[t] = __ballot_sync(0xffffffffu, inf[t]);
-        nv += __popc(bal[t]);
-      }
-      if (nv == 0) break;
-      if (it >= max_piv) { failed_cap = true; break; }
-      ++it;
-      if (nv < beta || alpha >= 1) {
-        if (nv < beta) { beta = nv; alpha = 3; } else { alpha -= 1; }
-#pragma unroll
-        for (int t = 0; t < KT; ++t)
-          if (inf[t]) pas[t] = !pas[t];
-      } else {
-        int vmax = -1;
-#pragma unroll
-        for (int t = KT - 1; t >= 0; --t)
-          if (vmax < 0 && bal[t]) vmax = 32 * t + 31 - __clz(bal[t]);
-#pragma unroll
-        for (int t = 0; t < KT; ++t)
-          if (lane + 32 * t == vmax) pas[t] = !pas[t];
-      }
+  for (int t = 0; t < KT; ++t) {
+    const int j = lane + 32 * t;
+    rr[t] = j < k ? (double)R[row * k + j] : 0.0;
+    if (j < k) rs[j] = rr[t];
+    dead[t] = !(j < k && G[j * k + j] > kDead * gmax);
+    pas[t] = attempt == 0 && !dead[t] && X[row * k + j] > 0.f;
+    any |= pas[t];
+    x[t] = 0.0;
+    y[t] = -rr[t];
+    tau[t] = kBppYTol * fabs(rr[t]);
+  }
+  __syncwarp();
+  int alpha = 3, beta = k + 1;
+  it = 0;
+  failed_numeric = false;
+  failed_cap = false;
+  bool need_solve = __any_sync(0xffffffffu, any);
+  for (;;) {
+    if (need_solve) {
       int nf = 0, pos[KT];
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
@@ -456,7 +501,7 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
           x[t] = 0.0;
           double s = -rr[t], mag = fabs(rr[t]);
           for (int a = 0; a < nf; ++a) {
-            const double g = G[j * k + Fl[a]] * v[a];
+            const double g = G[Fl[a] * k + j] * v[a];
             s += g;
             mag += fabs(g);
           }
@@ -466,14 +511,45 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
       }
       __syncwarp();
     }
+    bool inf[KT];
+    unsigned bal[KT];
+    int nv = 0;
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
-      if (j < k) X[row * k + j] = (float)x[t];
+      inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (!dead[t] && y[t] < -tau[t]));
+      bal[t] = __ballot_sync(0xffffffffu, inf[t]);
+      nv += __popc(bal[t]);
     }
-    *failed_numeric_out = failed_numeric;
-    *failed_cap_out = failed_cap;
-    return it;
+    if (nv == 0) break;
+    if (it >= max_piv) { failed_cap = true; break; }
+    ++it;
+    if (nv < beta || alpha >= 1) {
+      if (nv < beta) { beta = nv; alpha = 3; } else { alpha -= 1; }
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (inf[t]) pas[t] = !pas[t];
+    } else {
+      int vmax = -1;
+#pragma unroll
+      for (int t = KT - 1; t >= 0; --t)
+        if (vmax < 0 && bal[t]) vmax = 32 * t + 31 - __clz(bal[t]);
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (lane + 32 * t == vmax) pas[t] = !pas[t];
+    }
+    need_solve = true;
+  }
+  if (!(failed_numeric && it == 0)) break;
+  }
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int j = lane + 32 * t;
+    if (j < k) X[row * k + j] = (float)x[t];
+  }
+  *failed_numeric_out = failed_numeric;
+  *failed_cap_out = failed_cap;
+  return it;
 }
 
 }  // namespace bpp

@@ -21,8 +21,9 @@ struct DevCounters {
   long long bpp_nonconv;
   long long bpp_numeric;
   long long nonfinite;
-  long long iter;  // index of the next relres slot
-  long long pad[3];
+  long long iter;      // index of the next relres slot
+  long long bpp_redo;  // right-hand sides re-solved by the direct fallback
+  long long pad[2];
 };
 
 // ---------------------------------------------------------------- launchers

@@ -284,12 +284,27 @@ __global__ void g_gram_reduce(const BInst *__restrict__ P, int side) {
   }
 }
 
-// G^{-1} (FP64) per problem, one block each.  side 0: of H H^T; 1: of W^T W.
-__global__ void g_gram_inverse(const BInst *__restrict__ P, int side) {
+// G^{-1} (FP64) per problem (side 0: of H H^T; 1: of W^T W): Cholesky, one
+// block per problem; column solves, one warp per (problem, column); check.
+__global__ void __launch_bounds__(256) g_chol(const BInst *__restrict__ P, int side) {
   extern __shared__ double sm[];
-  __shared__ int good;
   const BInst &b = P[blockIdx.x];
-  bpp::gram_inverse_block(side ? b.GW : b.GH, b.k, b.Q, b.q_ok, sm, good);
+  const int k = b.k;
+  bpp::chol_block(side ? b.GW : b.GH, k, b.Lq, b.Lq + (size_t)k * k, b.q_ok + 1, sm);
+}
+
+__global__ void g_inv_cols(const BInst *__restrict__ P, int kmax) {
+  const BInst &b = P[blockIdx.x / kmax];
+  const int j = blockIdx.x % kmax, k = b.k;
+  if (j >= k) return;
+  const double *L = b.Lq, *invd = b.Lq + (size_t)k * k;
+  bpp::inv_col_warp(L, invd, k, j, b.Q, b.Lq + (size_t)k * k + k);
+}
+
+__global__ void g_inv_check(const BInst *__restrict__ P, int side) {
+  const BInst &b = P[blockIdx.x];
+  const int k = b.k;
+  bpp::inv_check(side ? b.GW : b.GH, b.Lq + (size_t)k * k + k, k, b.q_ok + 1, b.q_ok);
 }
 
 // BPP: items (p, -, r0, r1) of rows of W (side 0: against H H^T, R = A H^T)
@@ -338,7 +353,7 @@ __global__ void __launch_bounds__(256)
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
-  long long piv_total = 0, nonconv = 0, numeric = 0;
+  long long piv_total = 0, nonconv = 0, numeric = 0, redone = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item I = items[it];
     const BInst &b = P[I.p];
@@ -360,15 +375,18 @@ __global__ void __launch_bounds__(256)
     for (int64_t row = I.r0 + wib; row < I.r1; row += nwb) {
       if (!b.redo[row]) continue;
       bool fnum, fcap;
-      const int n_ex = bpp::bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, max_piv, &fnum, &fcap);
+      const int n_ex = bpp::bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, 1, max_piv, &fnum, &fcap);
       piv_total += n_ex;
       nonconv += fcap;
       numeric += fnum;
+      redone += 1;
       __syncwarp();
     }
     __syncthreads();
   }
   if (lane == 0) {
+    if (redone) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_redo),
+                          (unsigned long long)redone);
     if (piv_total) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_pivots),
                              (unsigned long long)piv_total);
     if (nonconv) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_nonconv),
@@ -485,9 +503,11 @@ cudaError_t launch_gram(const BInst *P, const Item *items, int nitems, int count
 
 cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count, int side,
                        int kmax, int max_piv, DevCounters *ctr, int wpb, cudaStream_t s) {
-  const size_t inv_smem = sizeof(double) * ((size_t)kmax * kmax + (size_t)kmax * 64);
-  cudaFuncSetAttribute(g_gram_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
-  g_gram_inverse<<<count, 64, inv_smem, s>>>(P, side);
+  const size_t chol_smem = sizeof(double) * (size_t)kmax * kmax;
+  cudaFuncSetAttribute(g_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
+  g_chol<<<count, 256, chol_smem, s>>>(P, side);
+  g_inv_cols<<<count * kmax, 32, 0, s>>>(P, kmax);
+  g_inv_check<<<count, 32, 0, s>>>(P, side);
   const bpp::BppLayout lay = bpp::bpp_layout(kmax);
   const size_t smem = sizeof(double) * (2 * lay.g_dbl + lay.gf_dbl + (size_t)wpb * lay.warp_dbl);
   const int grid = nitems < sms() * 2 ? nitems : sms() * 2;
@@ -506,7 +526,7 @@ cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count,
     cudaFuncSetAttribute(g_bpp_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem);
     g_bpp_direct<2><<<grid, 32 * fbw, fb_smem, s>>>(P, items, nitems, side, max_piv, ctr);
   }
-  g_launches += 3;
+  g_launches += 5;
   return cudaGetLastError();
 }
 

@@ -67,17 +67,27 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
   }
 }
 
-__global__ void k_gram_inverse(const double *__restrict__ Gd, int k, double *__restrict__ Q,
-                               int *__restrict__ ok) {
+__global__ void __launch_bounds__(256)
+    k_chol(const double *__restrict__ Gd, int k, double *__restrict__ L, double *__restrict__ invd,
+           int *__restrict__ ok) {
   extern __shared__ double sm[];
-  __shared__ int good;
-  gram_inverse_block(Gd, k, Q, ok, sm, good);
+  chol_block(Gd, k, L, invd, ok, sm);
+}
+
+__global__ void k_inv_cols(const double *__restrict__ L, const double *__restrict__ invd, int k,
+                           double *__restrict__ Q, double *__restrict__ colsum) {
+  inv_col_warp(L, invd, k, blockIdx.x, Q, colsum);
+}
+
+__global__ void k_inv_check(const double *__restrict__ Gd, const double *__restrict__ colsum,
+                            int k, const int *__restrict__ ok, int *__restrict__ q_ok) {
+  inv_check(Gd, colsum, k, ok, q_ok);
 }
 
 template <int KT>
 __global__ void __launch_bounds__(256)
     k_bpp_direct(const double *__restrict__ Gd, const float *__restrict__ R, int64_t rows, int k,
-                 float *__restrict__ X, int max_piv, DevCounters *ctr,
+                 float *__restrict__ X, int warm, int max_piv, DevCounters *ctr,
                  const uint8_t *__restrict__ redo) {
   extern __shared__ double sm[];
   const int ldl = k | 1;
@@ -90,18 +100,21 @@ __global__ void __launch_bounds__(256)
   double *v = L + (size_t)k * ldl;
   double *rs = v + k;
   int *Fl = reinterpret_cast<int *>(rs + k);
-  long long piv_total = 0, nonconv = 0, numeric = 0;
+  long long piv_total = 0, nonconv = 0, numeric = 0, redone = 0;
   for (int64_t row = (int64_t)blockIdx.x * nwb + wib; row < rows;
        row += (int64_t)gridDim.x * nwb) {
     if (!redo[row]) continue;
     bool fnum, fcap;
-    const int it = bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, max_piv, &fnum, &fcap);
+    const int it = bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, warm, max_piv, &fnum, &fcap);
     piv_total += it;
     nonconv += fcap;
     numeric += fnum;
+    redone += 1;
     __syncwarp();
   }
   if (lane == 0) {
+    if (redone) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_redo),
+                          (unsigned long long)redone);
     if (piv_total) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_pivots),
                              (unsigned long long)piv_total);
     if (nonconv) atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->bpp_nonconv),
@@ -124,8 +137,10 @@ int sm_count() {
 
 }  // namespace
 
+// scratch: Q (k x k), L (k x k), 1 / diag(L) (k), column sums of |Q| (k) in
+// FP64, two flags, then one byte per row (redo flags)
 size_t bpp_scratch_bytes(int k, int64_t rows) {
-  return sizeof(double) * (size_t)k * k + 256 + (size_t)rows;
+  return sizeof(double) * (2 * (size_t)k * k + 2 * (size_t)k) + 256 + (size_t)rows;
 }
 
 cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, float *X,
@@ -133,11 +148,18 @@ cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, flo
   if (rows == 0) return cudaSuccess;
   if (k < 1 || k > AUNMF_BPP_K_MAX) return cudaErrorInvalidValue;
   double *Q = reinterpret_cast<double *>(scratch);
-  int *q_ok = reinterpret_cast<int *>(Q + (size_t)k * k);
-  uint8_t *redo = reinterpret_cast<uint8_t *>(scratch) + sizeof(double) * (size_t)k * k + 256;
-  const size_t inv_smem = sizeof(double) * ((size_t)k * k + (size_t)k * 64);
-  cudaFuncSetAttribute(k_gram_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
-  k_gram_inverse<<<1, 64, inv_smem, s>>>(G, k, Q, q_ok);
+  double *L = Q + (size_t)k * k;
+  double *invd = L + (size_t)k * k;
+  double *colsum = invd + k;
+  int *chol_ok = reinterpret_cast<int *>(colsum + k);
+  int *q_ok = chol_ok + 1;
+  uint8_t *redo = reinterpret_cast<uint8_t *>(scratch) +
+                  sizeof(double) * (2 * (size_t)k * k + 2 * (size_t)k) + 256;
+  const size_t chol_smem = sizeof(double) * (size_t)k * k;
+  cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
+  k_chol<<<1, 256, chol_smem, s>>>(G, k, L, invd, chol_ok);
+  k_inv_cols<<<k, 32, 0, s>>>(L, invd, k, Q, colsum);
+  k_inv_check<<<1, 32, 0, s>>>(G, colsum, k, chol_ok, q_ok);
   const BppLayout lay = bpp_layout(k);
   const size_t budget = 200 * 1024;
   int wpb = (int)((budget / sizeof(double) - 2 * lay.g_dbl - lay.gf_dbl) / lay.warp_dbl);
@@ -160,7 +182,7 @@ cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, flo
                                                   ctr, redo);
     cudaFuncSetAttribute(k_bpp_direct<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fb_smem);
-    k_bpp_direct<1><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, max_pivots, ctr,
+    k_bpp_direct<1><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, warm, max_pivots, ctr,
                                                              redo);
   } else {
     cudaFuncSetAttribute(k_bpp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -168,10 +190,10 @@ cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, flo
                                                   ctr, redo);
     cudaFuncSetAttribute(k_bpp_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fb_smem);
-    k_bpp_direct<2><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, max_pivots, ctr,
+    k_bpp_direct<2><<<(unsigned)nbf, 32 * fbw, fb_smem, s>>>(G, R, rows, k, X, warm, max_pivots, ctr,
                                                              redo);
   }
-  g_launches += 3;
+  g_launches += 5;
   return cudaGetLastError();
 }
 

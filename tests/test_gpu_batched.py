@@ -127,3 +127,27 @@ def test_batched_rejects_unsupported(ax):
     with pytest.raises(aunmf.AunmfError) as e:
         ax.run_batched([A], [4], 2, [dev(np.ones((4, 40)))], prec="fp32")
     assert e.value.code == aunmf.E_UNSUPPORTED
+
+
+def test_abpp_ill_conditioned_factor_keeps_gram_definite(ax):
+    """ABPP's factors on uniform low-rank data can reach cond(W^T W) ~ 1e9
+    (a 2522 x 5235, k = 32 instance of the batched recipe does at its second
+    W update).  A Gram summed in FP32 is then indefinite and the FP64
+    Cholesky of the passive set fails; the library forms ABPP's Grams to
+    ~FP64 accuracy.  The TF32 run must complete, and match the FP32 run."""
+    m, n, k, seed = 2522, 5235, 32, 1609 + 31 * 128
+    A, _, _ = synth.dense_lowrank_torch(m, n, k, seed=seed, device="cuda")
+    _, H0 = synth.init_factors_torch(m, n, k, seed=seed, device="cuda")
+    Z = torch.zeros((m, k), device="cuda")
+    rels = {}
+    for prec in ("tf32", "fp32"):
+        W, H, rel, info = ax.run(A, k, "abpp", 5, Z, H0, prec=prec)
+        assert info["bpp_numeric"] == 0
+        rels[prec] = rel
+    assert np.abs(rels["tf32"] - rels["fp32"]).max() <= 1e-3
+    # the factor really is ill-conditioned: after the second W update its
+    # Gram's smallest eigenvalue is below FP32's resolution of the largest
+    W2, _, _, _ = ax.run(A, k, "abpp", 2, Z, H0, prec="tf32")
+    Wd = W2.double()
+    ev = torch.linalg.eigvalsh(Wd.T @ Wd)
+    assert float(ev[0] / ev[-1]) < 2.0 ** -24
