@@ -54,22 +54,41 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
 // into L (lower, ld ldl); the diagonal slot holds 1 / L_cc instead of L_cc
 // (one reciprocal square root per column, then only multiplications: the
 // FP64 pipe is the bottleneck, and each FP64 division or square root costs
-// it several instructions).  Returns false (warp-uniform) on a non-positive
-// pivot.
+// it several instructions).  Right-looking: after column c is scaled, the
+// warp's lanes share the entries of the trailing lower triangle (w (w + 1) / 2
+// of them, w = n - c - 1), so a factorisation costs ~n^3 / 192 FP64 warp
+// instructions plus ~10 per column, where one lane per row would cost
+// ~n^2 / 2 (each lane running the longest dot product of its column).
+// Returns false (warp-uniform) on a non-positive pivot.
 __device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int *I, int n,
                                               double *L, int ldl, int lane) {
+  // lower triangle of M_FF into L; entry e of the triangle is (a, b) with
+  // a (a + 1) / 2 <= e < (a + 1) (a + 2) / 2
+  const int tri = n * (n + 1) / 2;
+  for (int e = lane; e < tri; e += 32) {
+    int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if ((a + 1) * (a + 2) / 2 <= e) ++a;
+    if (a * (a + 1) / 2 > e) --a;
+    const int b = e - a * (a + 1) / 2;
+    L[a * ldl + b] = Mg[I[b] * k + I[a]];
+  }
+  __syncwarp();
   for (int c = 0; c < n; ++c) {
-    double part = 0.0;
-    for (int t = lane; t < c; t += 32) part = fma(L[c * ldl + t], L[c * ldl + t], part);
-    const double d = Mg[I[c] * k + I[c]] - warp_sum_d(part);
+    const double d = L[c * ldl + c];
     if (!(d > 0.0)) return false;
-    const double inv = rsqrt(d);
-    for (int a = c + 1 + lane; a < n; a += 32) {
-      double s = Mg[I[c] * k + I[a]];  // symmetric: lanes read along a row
-      for (int t = 0; t < c; ++t) s = fma(-L[a * ldl + t], L[c * ldl + t], s);
-      L[a * ldl + c] = s * inv;
+    const double r = rsqrt(d);
+    for (int a = c + 1 + lane; a < n; a += 32) L[a * ldl + c] *= r;
+    __syncwarp();
+    if (lane == 0) L[c * ldl + c] = r;
+    const int w = n - c - 1, tw = w * (w + 1) / 2;
+    for (int e = lane; e < tw; e += 32) {
+      int a = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      if ((a + 1) * (a + 2) / 2 <= e) ++a;
+      if (a * (a + 1) / 2 > e) --a;
+      const int b = e - a * (a + 1) / 2;
+      const int ra = c + 1 + a, rb = c + 1 + b;
+      L[ra * ldl + rb] = fma(-L[ra * ldl + c], L[rb * ldl + c], L[ra * ldl + rb]);
     }
-    if (lane == 0) L[c * ldl + c] = inv;
     __syncwarp();
   }
   return true;
