@@ -27,7 +27,7 @@ struct BInst {
   int ngw, ngh;           // Gram partial slots for the m rows of W / n rows of Ht
   void *Ax, *At, *Hk, *Wt;  // rounded copies of A, A^T; split factor copies
   int64_t ldx, ldat, ldh, ldw;
-  double *Q;              // G^{-1} of the current update (FP64)
+  double *Q;              // G^{-1} of the current update as an FP32 pair (2 k^2 floats)
   double *Lq;             // its Cholesky factor (k x k), 1 / diag (k), column sums of |Q| (k)
   int *q_ok;              // [0]: Q usable; [1]: the factorisation succeeded
   uint8_t *redo;          // rows flagged for the direct BPP fallback

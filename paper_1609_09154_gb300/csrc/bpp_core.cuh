@@ -37,7 +37,8 @@ struct BppLayout {
   int ldl;         // leading dimension of L (odd)
   size_t g_dbl;    // doubles for G and for Q (each)
   size_t gf_dbl;   // doubles holding |G| in FP32 (tolerance scales)
-  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k)
+  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k),
+                   // r in FP32 (k)
 };
 
 __host__ __device__ inline BppLayout bpp_layout(int k) {
@@ -46,7 +47,7 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
   l.ldl = l.kh | 1;
   l.g_dbl = (size_t)k * k;
   l.gf_dbl = ((size_t)k * k + 1) / 2;
-  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + ((size_t)k + 1) / 2;
+  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + 2 * (((size_t)k + 1) / 2);
   return l;
 }
 
@@ -60,8 +61,9 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
 // instructions plus ~10 per column, where one lane per row would cost
 // ~n^2 / 2 (each lane running the longest dot product of its column).
 // Returns false (warp-uniform) on a non-positive pivot.
-__device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int *I, int n,
-                                              double *L, int ldl, int lane) {
+template <class Acc>
+__device__ __forceinline__ bool warp_cholesky(Acc M, const int *I, int n, double *L, int ldl,
+                                              int lane) {
   // lower triangle of M_FF into L; entry e of the triangle is (a, b) with
   // a (a + 1) / 2 <= e < (a + 1) (a + 2) / 2
   const int tri = n * (n + 1) / 2;
@@ -70,7 +72,7 @@ __device__ __forceinline__ bool warp_cholesky(const double *Mg, int k, const int
     if ((a + 1) * (a + 2) / 2 <= e) ++a;
     if (a * (a + 1) / 2 > e) --a;
     const int b = e - a * (a + 1) / 2;
-    L[a * ldl + b] = Mg[I[b] * k + I[a]];
+    L[a * ldl + b] = M(I[b], I[a]);
   }
   __syncwarp();
   for (int c = 0; c < n; ++c) {
@@ -119,8 +121,9 @@ __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n,
 //   chol_block:   L = chol(G) (lower, row-major k x k) and invd = 1 / diag(L),
 //                 one block; ok = 0 on a non-positive pivot;
 //   inv_col_warp: column j of Q by forward and back substitution against
-//                 e_j, one warp per column (lane i owns rows i, i + 32), and
-//                 the column's sum of |Q_ij|;
+//                 e_j, one warp per column (lane i owns rows i, i + 32),
+//                 stored as an FP32 pair Qs[e] = hi, Qs[k^2 + e] = lo with
+//                 hi + lo = Q_e to ~2^-48, and the column's sum of |Q_ij|;
 //   inv_check:    q_ok = ok and cond_1(G) = ||G||_1 ||Q||_1 < kQMaxCond.
 __device__ __forceinline__ void chol_block(const double *__restrict__ G, int k,
                                            double *__restrict__ Lg, double *__restrict__ invd,
@@ -157,7 +160,7 @@ __device__ __forceinline__ void chol_block(const double *__restrict__ G, int k,
 
 __device__ __forceinline__ void inv_col_warp(const double *__restrict__ Lg,
                                              const double *__restrict__ invd, int k, int j,
-                                             double *__restrict__ Q, double *__restrict__ colsum) {
+                                             float *__restrict__ Qs, double *__restrict__ colsum) {
   const int lane = threadIdx.x & 31;
   double w[2], acc[2] = {0.0, 0.0};
   // forward: w_i = (e_ij - sum_{t < i} L_it w_t) / L_ii
@@ -198,7 +201,9 @@ __device__ __forceinline__ void inv_col_warp(const double *__restrict__ Lg,
   for (int s2 = 0; s2 < 2; ++s2) {
     const int i = lane + 32 * s2;
     if (i < k) {
-      Q[i * k + j] = q[s2];
+      const float hi = (float)q[s2];
+      Qs[i * k + j] = hi;
+      Qs[k * k + i * k + j] = (float)(q[s2] - (double)hi);
       cs += fabs(q[s2]);
     }
   }
@@ -223,33 +228,37 @@ __device__ __forceinline__ void inv_check(const double *__restrict__ G,
 
 // Shared-memory view of one warp's BPP state (fast kernel).
 struct BppWarp {
-  const double *G, *Q;
+  const double *G;
+  const float *Qh, *Ql;  // G^{-1} = Qh + Ql (FP32 pair)
   const float *Gabs;
   double dead_below;  // kDead * max diagonal of G
   bool have_q;
   double *L, *v, *rs;
   int *Fl, *Bl;
   float *xa;
+  float *rsf;  // r in FP32, by index
   int ldl, kh;
 };
 
 // Stage G (FP64), Q and |G| (FP32) of one problem into shared memory (block-
 // wide; the caller synchronises) and return warp wib's view.
 __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
-                                             const double *__restrict__ Qg, const int *q_ok, int k,
+                                             const float *__restrict__ Qsg, const int *q_ok, int k,
                                              double *sm, int wib) {
   const BppLayout lay = bpp_layout(k);
   double *G = sm;
-  double *Q = sm + lay.g_dbl;
+  float *Qs = reinterpret_cast<float *>(sm + lay.g_dbl);  // hi (k^2), lo (k^2)
   float *Gabs = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     G[e] = Gd[e];
-    Q[e] = Qg[e];
+    Qs[e] = Qsg[e];
+    Qs[k * k + e] = Qsg[k * k + e];
     Gabs[e] = (float)fabs(Gd[e]);
   }
   BppWarp w;
   w.G = G;
-  w.Q = Q;
+  w.Qh = Qs;
+  w.Ql = Qs + k * k;
   w.Gabs = Gabs;
   double gmax = 0.0;
   for (int i = 0; i < k; ++i) gmax = fmax(gmax, Gd[i * k + i]);
@@ -261,6 +270,7 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   w.Fl = reinterpret_cast<int *>(w.rs + k);  // passive indices, ascending
   w.Bl = w.Fl + k;                           // active indices, ascending
   w.xa = reinterpret_cast<float *>(w.Bl + k);  // |x_F| in FP32, F order
+  w.rsf = w.xa + 2 * ((k + 1) / 2);
   w.ldl = lay.ldl;
   w.kh = lay.kh;
   return w;
@@ -275,12 +285,15 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
                                             bool *failed_cap_out) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const double *G = w.G, *Q = w.Q;
+  const double *G = w.G;
+  const float *Qh = w.Qh, *Ql = w.Ql;
+  auto Gat = [G, k](int a, int b) { return G[a * k + b]; };
+  auto Qat = [Qh, Ql, k](int a, int b) { return (double)Qh[a * k + b] + (double)Ql[a * k + b]; };
   const float *Gabs = w.Gabs;
   const bool have_q = w.have_q;
   double *L = w.L, *v = w.v, *rs = w.rs;
   int *Fl = w.Fl, *Bl = w.Bl;
-  float *xa = w.xa;
+  float *xa = w.xa, *rsf = w.rsf;
   const int ldl = w.ldl;
   struct {
     int kh;
@@ -291,8 +304,12 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int j = lane + 32 * t;
-      rr[t] = j < k ? (double)R[row * k + j] : 0.0;
-      if (j < k) rs[j] = rr[t];
+      const float rf = j < k ? R[row * k + j] : 0.f;
+      rr[t] = (double)rf;
+      if (j < k) {
+        rs[j] = rr[t];
+        rsf[j] = rf;
+      }
       dead[t] = !(j < k && G[j * k + j] > w.dead_below);
       pas[t] = warm && !dead[t] && X[row * k + j] > 0.f;
       any |= pas[t];
@@ -334,7 +351,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
         if (nf <= nb || !have_q) {
           // ---- direct: G_FF x_F = r_F; v[0..nf) ends as x_F in F order
           if (nf > lay.kh) { failed_numeric = true; break; }
-          if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+          if (!warp_cholesky(Gat, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
           for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
           __syncwarp();
           warp_chol_solve(L, ldl, nf, v, lane);
@@ -346,11 +363,19 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
           if (!have_z) {
 #pragma unroll
             for (int t = 0; t < KT; ++t) {
+              // z_j = sum_l (Qh + Ql)_lj r_l: each Qh r product exact (two
+              // FP32 numbers), summed in an FP32 pair with the rounding errors
+              // kept; r_l is an FP32 value.  ~10 FP32 operations per term,
+              // where one FP64 FMA costs the FP64 pipe ~60x as much.
               const int j = lane + 32 * t;
-              double acc = 0.0;
+              float hi = 0.f, lo = 0.f;
               if (j < k)
-                for (int l = 0; l < k; ++l) acc = fma(Q[l * k + j], rs[l], acc);
-              z[t] = acc;
+                for (int l = 0; l < k; ++l) {
+                  const float rl = rsf[l];
+                  two_fma_acc(Qh[l * k + j], rl, hi, lo);
+                  lo = fmaf(Ql[l * k + j], rl, lo);
+                }
+              z[t] = (double)hi + (double)lo;
             }
             have_z = true;
           }
@@ -360,14 +385,14 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             if (j < k && !pas[t]) v[posb[t]] = z[t];
           }
           __syncwarp();
-          if (!warp_cholesky(Q, k, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
+          if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
           warp_chol_solve(L, ldl, nb, v, lane);  // v = Q_BB^{-1} z_B = -y_B
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
             double s = z[t];
             if (j < k && pas[t])
-              for (int b = 0; b < nb; ++b) s = fma(-Q[Bl[b] * k + j], v[b], s);
+              for (int b = 0; b < nb; ++b) s = fma(-Qat(Bl[b], j), v[b], s);
             x[t] = (j < k && pas[t]) ? s : 0.0;
             if (j < k && !pas[t]) y[t] = -v[posb[t]];
           }
@@ -504,7 +529,10 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
       for (int t = 0; t < KT; ++t)
         if (pas[t]) Fl[pos[t]] = lane + 32 * t;
       __syncwarp();
-      if (!warp_cholesky(G, k, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+      if (!warp_cholesky([G, k](int a, int b) { return G[a * k + b]; }, Fl, nf, L, ldl, lane)) {
+        failed_numeric = true;
+        break;
+      }
       for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
       __syncwarp();
       warp_chol_solve(L, ldl, nf, v, lane);

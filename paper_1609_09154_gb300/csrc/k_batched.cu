@@ -298,7 +298,7 @@ __global__ void g_inv_cols(const BInst *__restrict__ P, int kmax) {
   const int j = blockIdx.x % kmax, k = b.k;
   if (j >= k) return;
   const double *L = b.Lq, *invd = b.Lq + (size_t)k * k;
-  bpp::inv_col_warp(L, invd, k, j, b.Q, b.Lq + (size_t)k * k + k);
+  bpp::inv_col_warp(L, invd, k, j, reinterpret_cast<float *>(b.Q), b.Lq + (size_t)k * k + k);
 }
 
 __global__ void g_inv_check(const BInst *__restrict__ P, int side) {
@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
     const BInst &b = P[I.p];
     const int k = b.k;
     __syncthreads();
-    const bpp::BppWarp w = bpp::bpp_stage(side ? b.GW : b.GH, b.Q, b.q_ok, k, sm, wib);
+    const bpp::BppWarp w =
+        bpp::bpp_stage(side ? b.GW : b.GH, reinterpret_cast<const float *>(b.Q), b.q_ok, k, sm, wib);
     __syncthreads();
     const float *R = side ? b.PHt : b.PW;
     float *X = side ? b.Ht : b.W;

@@ -39,7 +39,7 @@ using namespace bpp;
 
 template <int KT>
 __global__ void __launch_bounds__(32 * kBppWarps, 1)
-    k_bpp(const double *__restrict__ Gd, const double *__restrict__ Qg, const int *__restrict__ q_ok,
+    k_bpp(const double *__restrict__ Gd, const float *__restrict__ Qg, const int *__restrict__ q_ok,
           const float *__restrict__ R, int64_t rows, int k, float *__restrict__ X, int warm,
           int max_piv, DevCounters *ctr, uint8_t *__restrict__ redo) {
   extern __shared__ double sm[];
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void k_inv_cols(const double *__restrict__ L, const double *__restrict__ invd, int k,
-                           double *__restrict__ Q, double *__restrict__ colsum) {
+                           float *__restrict__ Q, double *__restrict__ colsum) {
   inv_col_warp(L, invd, k, blockIdx.x, Q, colsum);
 }
 
@@ -147,8 +147,8 @@ cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, flo
                        int max_pivots, int warm, DevCounters *ctr, void *scratch, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
   if (k < 1 || k > AUNMF_BPP_K_MAX) return cudaErrorInvalidValue;
-  double *Q = reinterpret_cast<double *>(scratch);
-  double *L = Q + (size_t)k * k;
+  float *Q = reinterpret_cast<float *>(scratch);  // G^{-1} as an FP32 pair (2 k^2 floats)
+  double *L = reinterpret_cast<double *>(scratch) + (size_t)k * k;
   double *invd = L + (size_t)k * k;
   double *colsum = invd + k;
   int *chol_ok = reinterpret_cast<int *>(colsum + k);
