@@ -168,17 +168,25 @@ __global__ void __launch_bounds__(kLucThreads)
 
 // HALS normalisation (Eq. halsupdate, w^i / ||w^i||, compensated in H):
 // s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i; GW_ij /= s_i s_j.
+// The column of element e is e mod k, taken in 32-bit arithmetic when the
+// element count allows (a 64-bit remainder costs ~40 instructions and bound
+// the pass); the column scales are staged once per block.
+template <bool WIDE>
 __global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
                                   const float *__restrict__ GW, bool divide) {
+  __shared__ float sc[AUNMF_K_MAX];
+  __shared__ bool ok[AUNMF_K_MAX];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const float g = GW[i * k + i];
+    ok[i] = g > 0.f;
+    sc[i] = g > 0.f ? sqrtf(g) : 1.f;
+  }
+  __syncthreads();
   const int64_t total = rows * k;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % k);
-    const float g = GW[i * k + i];
-    if (g > 0.f) {
-      const float s = sqrtf(g);
-      X[e] = divide ? X[e] / s : X[e] * s;
-    }
+    const int i = WIDE ? (int)(e % k) : (int)((uint32_t)e % (uint32_t)k);
+    if (ok[i]) X[e] = divide ? X[e] / sc[i] : X[e] * sc[i];
   }
 }
 
@@ -418,8 +426,14 @@ cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t ro
     if (b > 152 * 16) b = 152 * 16;
     return (int)(b < 1 ? 1 : b);
   };
-  if (rows_x > 0) k_hals_scale_rows<<<nb(rows_x * k), 256, 0, s>>>(X, rows_x, k, GW, true);
-  if (Y && rows_y > 0) k_hals_scale_rows<<<nb(rows_y * k), 256, 0, s>>>(Y, rows_y, k, GW, false);
+  auto scale = [&](float *Z, int64_t rows, bool divide) {
+    if (rows * k + 256LL * 152 * 16 < 0xFFFFFFFFLL)
+      k_hals_scale_rows<false><<<nb(rows * k), 256, 0, s>>>(Z, rows, k, GW, divide);
+    else
+      k_hals_scale_rows<true><<<nb(rows * k), 256, 0, s>>>(Z, rows, k, GW, divide);
+  };
+  if (rows_x > 0) scale(X, rows_x, true);
+  if (Y && rows_y > 0) scale(Y, rows_y, false);
   k_hals_scale_gram<<<1, 256, 0, s>>>(GW, k);
   g_launches += 1 + (rows_x > 0) + (Y && rows_y > 0);
   return cudaGetLastError();
