@@ -215,15 +215,22 @@ __device__ __forceinline__ void inv_col_warp(const double *__restrict__ Lg,
 __device__ __forceinline__ void inv_check(const double *__restrict__ G,
                                           const double *__restrict__ colsum, int k, const int *ok,
                                           int *__restrict__ q_ok) {
-  if (threadIdx.x != 0) return;
+  // one warp: lane l takes columns l, l + 32 (k <= 64), then max-reduce
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   double ng = 0.0, nq = 0.0;
-  for (int c = 0; c < k; ++c) {
+  for (int c = lane; c < k; c += 32) {
     double cg = 0.0;
     for (int i = 0; i < k; ++i) cg += fabs(G[i * k + c]);
-    ng = cg > ng ? cg : ng;
-    nq = colsum[c] > nq ? colsum[c] : nq;
+    ng = fmax(ng, cg);
+    nq = fmax(nq, colsum[c]);
   }
-  *q_ok = (*ok && ng * nq < kQMaxCond) ? 1 : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ng = fmax(ng, __shfl_xor_sync(0xffffffffu, ng, o));
+    nq = fmax(nq, __shfl_xor_sync(0xffffffffu, nq, o));
+  }
+  if (lane == 0) *q_ok = (*ok && ng * nq < kQMaxCond) ? 1 : 0;
 }
 
 // Shared-memory view of one warp's BPP state (fast kernel).
