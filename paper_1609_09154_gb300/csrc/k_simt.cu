@@ -318,8 +318,16 @@ cudaError_t launch_widen(const float *G32, int k, double *G64, cudaStream_t s) {
 // subtracts nearly equal terms and needs the products close to FP32
 // rounding).
 namespace {
+// two resident blocks per SM (at most 128 registers a thread): measured 8-12 %
+// faster than one at 96000 x 64000, k = 50, despite a few spilled registers
+#ifndef AUNMF_SIMT_MINB
+#define AUNMF_SIMT_MINB 2
+#endif
+#ifndef AUNMF_SIMT_BM
+#define AUNMF_SIMT_BM 128
+#endif
 template <int BM, int BN, int BK, bool AK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
     k_gemm_simt(const float *__restrict__ A, int64_t lda, int64_t M, int64_t K,
                 const float *__restrict__ B, int ldb, int N, float *__restrict__ C, int ldc) {
   constexpr int TM = BM / 16, TN = BN / 16;
@@ -440,7 +448,7 @@ __global__ void __launch_bounds__(256)
 template <bool AK>
 cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const float *B, int N,
                       float *C, cudaStream_t s) {
-  constexpr int BM = 128, BK = 16;
+  constexpr int BM = AUNMF_SIMT_BM, BK = 16;
   const unsigned gx = (unsigned)((M + BM - 1) / BM);
   if (N <= 16) {
     k_gemm_simt<BM, 16, BK, AK><<<dim3(gx, 1), 256, 0, s>>>(A, lda, M, K, B, N, N, C, N);

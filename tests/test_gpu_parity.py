@@ -57,8 +57,10 @@ def assert_product(got, ref, absprod, K, extra_rel=0.0):
 
 
 # shapes spanning several 128-row tiles with ragged tails, and k across the
-# 16 / 32 / 64-wide product tiles and the 32-wide lane groups of the updates
-SHAPES = [(300, 200, 10), (517, 389, 50), (129, 1031, 33), (64, 48, 1), (700, 260, 100)]
+# 16 / 32 / 64-wide product tiles, the thread-per-row updates' padded widths
+# (16, 32, 48, 64 for k <= 64) and the warp-per-row updates above 64
+SHAPES = [(300, 200, 10), (517, 389, 50), (129, 1031, 33), (64, 48, 1), (700, 260, 100),
+          (257, 300, 24), (200, 150, 64)]
 
 
 @pytest.mark.parametrize("m,n,k", SHAPES)
@@ -180,6 +182,28 @@ def test_nls_bpp_zero_column(ax):
             xr, rc = orc.bpp_solve(G, R[r])
             assert rc >= 0
             assert_bpp(X[r], xr)
+
+
+def test_update_abpp_reports_numeric_failure(ax):
+    """An ABPP step whose Gram is not positive definite (here indefinite)
+    reports AUNMF_E_NUMERIC after synchronising, instead of returning OK
+    with rows left unsolved; the oracle rejects the same system."""
+    from paper_1609_09154_gb300 import aunmf
+
+    k = 4
+    G = np.array([[1.0, 2.0, 0.0, 0.0], [2.0, 1.0, 0.0, 0.0],
+                  [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]])  # eigenvalues -1, 1, 1, 3
+    R = np.full((8, k), 1.0)
+    _, rc = orc.bpp_solve(G, R[0])
+    assert rc < 0
+    W = dev(np.zeros((8, k)))
+    with pytest.raises(aunmf.AunmfError) as e:
+        ax.update_w("abpp", W, dev(R), dev(G))
+    assert e.value.code == aunmf.E_NUMERIC
+    Ht = dev(np.zeros((k, 8)))
+    with pytest.raises(aunmf.AunmfError) as e:
+        ax.update_h("abpp", Ht, dev(R.T), dev(G))
+    assert e.value.code == aunmf.E_NUMERIC
 
 
 def test_relres_step(ax):
