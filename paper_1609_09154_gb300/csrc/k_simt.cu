@@ -333,11 +333,17 @@ __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BK * BN / 256;
   constexpr int PADA = 4;  // row pad: spreads the transposed stores over banks
-  constexpr int SLAB = 32; // K elements per compensated partial
+  constexpr int SLAB = 128;  // K elements per compensated partial
+  constexpr int LDK = TM * TN + 1;  // odd row stride of the per-thread running sums
   static_assert(LA >= 1 && LB >= 1 && TM % 4 == 0, "tile too small");
   static_assert(SLAB % BK == 0, "slab must be a multiple of BK");
   __shared__ __align__(16) float sA[2][BK][BM + PADA];
   __shared__ __align__(16) float sB[2][BK][BN];
+  // Kahan running sum and correction of each thread's TM x TN outputs, in a
+  // row of its own (touched once per slab): keeping them in registers would
+  // triple the accumulator registers and halve the resident warps
+  extern __shared__ float sKahan[];
+  float *kh = sKahan + (size_t)threadIdx.x * LDK * 2, *kc = kh + LDK;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
@@ -378,20 +384,23 @@ __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
     }
   };
 
-  float acc[TM][TN], hi[TM][TN], cor[TM][TN];
+  float acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = hi[i][j] = cor[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  for (int e = 0; e < TM * TN; ++e) kh[e] = kc[e] = 0.f;
   auto fold = [&]() {  // hi += acc with Kahan's compensation; acc = 0
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const float y = acc[i][j] - cor[i][j];
-        const float t = hi[i][j] + y;
-        cor[i][j] = (t - hi[i][j]) - y;
-        hi[i][j] = t;
+        const int e = i * TN + j;
+        const float hi = kh[e], cor = kc[e];
+        const float y = acc[i][j] - cor;
+        const float t = hi + y;
+        kc[e] = (t - hi) - y;
+        kh[e] = t;
         acc[i][j] = 0.f;
       }
   };
@@ -440,9 +449,14 @@ __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx * TN + j;
-      if (gn < N) C[gm * ldc + gn] = hi[i][j] - cor[i][j];
+      if (gn < N) C[gm * ldc + gn] = kh[i * TN + j] - kc[i * TN + j];
     }
   }
+}
+
+template <int BM, int BN>
+constexpr size_t simt_kahan_bytes() {
+  return sizeof(float) * 256 * 2 * ((BM / 16) * (BN / 16) + 1);
 }
 
 template <bool AK>
@@ -451,12 +465,18 @@ cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const f
   constexpr int BM = AUNMF_SIMT_BM, BK = 16;
   const unsigned gx = (unsigned)((M + BM - 1) / BM);
   if (N <= 16) {
-    k_gemm_simt<BM, 16, BK, AK><<<dim3(gx, 1), 256, 0, s>>>(A, lda, M, K, B, N, N, C, N);
+    constexpr size_t sm = simt_kahan_bytes<BM, 16>();
+    cudaFuncSetAttribute(k_gemm_simt<BM, 16, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemm_simt<BM, 16, BK, AK><<<dim3(gx, 1), 256, sm, s>>>(A, lda, M, K, B, N, N, C, N);
   } else if (N <= 32) {
-    k_gemm_simt<BM, 32, BK, AK><<<dim3(gx, 1), 256, 0, s>>>(A, lda, M, K, B, N, N, C, N);
+    constexpr size_t sm = simt_kahan_bytes<BM, 32>();
+    cudaFuncSetAttribute(k_gemm_simt<BM, 32, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemm_simt<BM, 32, BK, AK><<<dim3(gx, 1), 256, sm, s>>>(A, lda, M, K, B, N, N, C, N);
   } else {
-    k_gemm_simt<BM, 64, BK, AK><<<dim3(gx, (N + 63) / 64), 256, 0, s>>>(A, lda, M, K, B, N, N,
-                                                                          C, N);
+    constexpr size_t sm = simt_kahan_bytes<BM, 64>();
+    cudaFuncSetAttribute(k_gemm_simt<BM, 64, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemm_simt<BM, 64, BK, AK><<<dim3(gx, (N + 63) / 64), 256, sm, s>>>(A, lda, M, K, B, N, N,
+                                                                           C, N);
   }
   return cudaGetLastError();
 }
