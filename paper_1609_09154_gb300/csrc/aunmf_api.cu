@@ -177,7 +177,7 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhAht);
-    return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, s);
+    return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, c.parts, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
   const bool split = use_split(c.k);
@@ -211,7 +211,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhWta);
-    return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, s);
+    return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, c.parts, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
   const bool split = use_split(c.k);
@@ -504,6 +504,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   if (o.prec != AUNMF_FP32) {
     int prc = prepare_tc(h, c, s);
     if (prc != AUNMF_OK) return prc;
+  } else if (A->dense) {
+    ENS(h, h->parts, simt_parts_bytes(m > n ? m : n, k));
+    c.parts = P<float>(h->parts);
   }
   if (!A->dense) {
     int prc = prepare_sparse(h, c, s);
@@ -639,6 +642,9 @@ int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int
   if (prec != AUNMF_FP32) {
     int rc = prepare_tc(h, c, h->stream);
     if (rc != AUNMF_OK) return rc;
+  } else if (A->dense) {
+    ENS(h, h->parts, simt_parts_bytes(A->m, k));
+    c.parts = P<float>(h->parts);
   }
   CK(h, product_aht(h, c, h->stream));
   return AUNMF_OK;
@@ -663,6 +669,9 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
   if (prec != AUNMF_FP32) {
     int rc = prepare_tc(h, c, h->stream);
     if (rc != AUNMF_OK) return rc;
+  } else if (A->dense) {
+    ENS(h, h->parts, simt_parts_bytes(n, k));
+    c.parts = P<float>(h->parts);
   }
   if (!A->dense) {
     int rc = prepare_sparse(h, c, h->stream);
@@ -804,7 +813,8 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   CK(h, launch_transpose(H, k, n, Ht, s));
   if (A->dense) {
     CK(h, launch_norm2(A->dense, m, n, A->lda, dp, h->n_dparts, P<double>(h->n2a), s));
-    CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, s));
+    ENS(h, h->parts, simt_parts_bytes(n, k));
+    CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, P<float>(h->parts), s));
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, dp, h->n_dparts, P<double>(h->n2a), s));
     RunCtx c{};
@@ -862,6 +872,8 @@ int loss_setup(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, co
     if (rc != AUNMF_OK) return rc;
   } else if (A->dense) {
     CK(h, launch_norm2(A->dense, m, n, A->lda, c.dpart, h->n_dparts, c.n2a, s));
+    ENS(h, h->parts, simt_parts_bytes(m > n ? m : n, k));
+    c.parts = P<float>(h->parts);
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
   }

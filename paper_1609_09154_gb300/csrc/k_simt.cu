@@ -329,7 +329,10 @@ namespace {
 template <int BM, int BN, int BK, bool AK>
 __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
     k_gemm_simt(const float *__restrict__ A, int64_t lda, int64_t M, int64_t K,
-                const float *__restrict__ B, int ldb, int N, float *__restrict__ C, int ldc) {
+                const float *__restrict__ B, int ldb, int N, float *__restrict__ C, int ldc,
+                int64_t kchunk) {
+  // blockIdx.z: K split [kz0, kz1) (kchunk a multiple of the slab); its
+  // partial C goes to C + z * M * ldc
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BK * BN / 256;
   constexpr int PADA = 4;  // row pad: spreads the transposed stores over banks
@@ -405,12 +408,14 @@ __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
       }
   };
 
-  load(0);
+  const int64_t kz0 = (int64_t)blockIdx.z * kchunk, kz1 = min(K, kz0 + kchunk);
+  C += (int64_t)blockIdx.z * M * ldc;
+  load(kz0);
   store(0);
   __syncthreads();
   int buf = 0;
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
-    const bool more = k0 + BK < K;
+  for (int64_t k0 = kz0; k0 < kz1; k0 += BK) {
+    const bool more = k0 + BK < kz1;
     if (more) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -459,38 +464,81 @@ constexpr size_t simt_kahan_bytes() {
   return sizeof(float) * 256 * 2 * ((BM / 16) * (BN / 16) + 1);
 }
 
+// K splits: the smallest S in 1..4 whose block count fills the resident
+// slots (2 blocks per SM) most evenly, each split at least 8 slabs long.
+int simt_splits(int64_t tiles, int64_t K) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t slots = 2LL * (sms > 0 ? sms : 148);
+  int best = 1;
+  double best_eff = 0.0;
+  for (int S = 1; S <= 4; ++S) {
+    if (S > 1 && K / S < 8 * 128) break;
+    const int64_t u = tiles * S;
+    const double eff = ((double)u / slots) / (double)((u + slots - 1) / slots);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = S; }
+  }
+  return best;
+}
+
+__global__ void k_sum_parts(const float *__restrict__ parts, int S, int64_t len,
+                            float *__restrict__ C) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < S; ++z) s += parts[z * len + e];
+    C[e] = s;
+  }
+}
+
 template <bool AK>
 cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const float *B, int N,
-                      float *C, cudaStream_t s) {
-  constexpr int BM = AUNMF_SIMT_BM, BK = 16;
+                      float *C, float *parts, cudaStream_t s) {
+  constexpr int BM = AUNMF_SIMT_BM, BK = 16, SLAB = 128;
   const unsigned gx = (unsigned)((M + BM - 1) / BM);
-  if (N <= 16) {
+  const int BN = N <= 16 ? 16 : (N <= 32 ? 32 : 64);
+  const unsigned gy = (unsigned)((N + BN - 1) / BN);
+  const int S = parts ? simt_splits((int64_t)gx * gy, K) : 1;
+  const int64_t kchunk = ((K + S - 1) / S + SLAB - 1) / SLAB * SLAB;
+  float *out = S > 1 ? parts : C;
+  const dim3 grid(gx, gy, (unsigned)S);
+  if (BN == 16) {
     constexpr size_t sm = simt_kahan_bytes<BM, 16>();
     cudaFuncSetAttribute(k_gemm_simt<BM, 16, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemm_simt<BM, 16, BK, AK><<<dim3(gx, 1), 256, sm, s>>>(A, lda, M, K, B, N, N, C, N);
-  } else if (N <= 32) {
+    k_gemm_simt<BM, 16, BK, AK><<<grid, 256, sm, s>>>(A, lda, M, K, B, N, N, out, N, kchunk);
+  } else if (BN == 32) {
     constexpr size_t sm = simt_kahan_bytes<BM, 32>();
     cudaFuncSetAttribute(k_gemm_simt<BM, 32, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemm_simt<BM, 32, BK, AK><<<dim3(gx, 1), 256, sm, s>>>(A, lda, M, K, B, N, N, C, N);
+    k_gemm_simt<BM, 32, BK, AK><<<grid, 256, sm, s>>>(A, lda, M, K, B, N, N, out, N, kchunk);
   } else {
     constexpr size_t sm = simt_kahan_bytes<BM, 64>();
     cudaFuncSetAttribute(k_gemm_simt<BM, 64, BK, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemm_simt<BM, 64, BK, AK><<<dim3(gx, (N + 63) / 64), 256, sm, s>>>(A, lda, M, K, B, N, N,
-                                                                           C, N);
+    k_gemm_simt<BM, 64, BK, AK><<<grid, 256, sm, s>>>(A, lda, M, K, B, N, N, out, N, kchunk);
+  }
+  g_launches += 1;
+  if (S > 1) {
+    const int64_t len = M * (int64_t)N;
+    int64_t nb = (len + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    k_sum_parts<<<(unsigned)nb, 256, 0, s>>>(parts, S, len, C);
+    g_launches += 1;
   }
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *Ht,
-                            int k, float *P, cudaStream_t s) {
-  return gemm_simt<true>(A, lda, m, n, Ht, k, P, s);
+                            int k, float *P, float *parts, cudaStream_t s) {
+  return gemm_simt<true>(A, lda, m, n, Ht, k, P, parts, s);
 }
 
 cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
-                            int k, float *P, cudaStream_t s) {
-  return gemm_simt<false>(A, lda, n, m, W, k, P, s);
+                            int k, float *P, float *parts, cudaStream_t s) {
+  return gemm_simt<false>(A, lda, n, m, W, k, P, parts, s);
 }
+
+size_t simt_parts_bytes(int64_t rows, int k) { return sizeof(float) * 4 * (size_t)rows * k; }
 
 // ------------------------------------------------------------------ transpose
 namespace {

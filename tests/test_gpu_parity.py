@@ -81,6 +81,18 @@ def test_products_fp32(ax, m, n, k):
     assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
 
 
+@pytest.mark.parametrize("m,n,k", [(300, 9000, 50), (9000, 300, 20)])
+def test_products_fp32_long_contraction(ax, m, n, k):
+    """Few output tiles and a long contraction: the FP32 product splits K
+    into up to 4 ranges (each with its own compensated sums) and adds the
+    partials in split order."""
+    A, W, H = problem(m, n, k, seed=m + 7)
+    PW = host(ax.aht(dev(A), dev(H)))
+    PH = host(ax.wta(dev(A), dev(W)))
+    assert_product(PW, orc.aht(A, H), np.abs(A) @ np.abs(H).T, n)
+    assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
+
+
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_mu_updates(ax, m, n, k):
     A, W, H = problem(m, n, k, seed=m + 2)
