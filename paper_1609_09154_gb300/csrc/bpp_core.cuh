@@ -23,7 +23,12 @@ constexpr double kBppYTol = 1e-11;
 constexpr double kDead = 1e-12;
 // G^{-1} is used for the passive-set solves only when cond_1(G) is below
 // this (FP64 solves through it then keep at least ~8 digits)
-constexpr double kQMaxCond = 1e8;
+// G^{-1} is used while cond_1(G) < kQMaxCond; from kQRefineCond on, each
+// solve through it takes one step of iterative refinement.  (ABPP's factors
+// on uniform low-rank data reach cond ~1e9: without the refinement those
+// rows would need full-size factorisations of G_FF.)
+constexpr double kQRefineCond = 1e8;
+constexpr double kQMaxCond = 1e12;
 constexpr int kBppWarps = 16;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -124,7 +129,8 @@ __device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n,
 //                 e_j, one warp per column (lane i owns rows i, i + 32),
 //                 stored as an FP32 pair Qs[e] = hi, Qs[k^2 + e] = lo with
 //                 hi + lo = Q_e to ~2^-48, and the column's sum of |Q_ij|;
-//   inv_check:    q_ok = ok and cond_1(G) = ||G||_1 ||Q||_1 < kQMaxCond.
+//   inv_check:    q_ok = 0 unless ok and cond_1(G) = ||G||_1 ||Q||_1 <
+//                 kQMaxCond; 2 when cond_1(G) >= kQRefineCond, else 1.
 __device__ __forceinline__ void chol_block(const double *__restrict__ G, int k,
                                            double *__restrict__ Lg, double *__restrict__ invd,
                                            int *__restrict__ ok, double *A) {
@@ -230,7 +236,10 @@ __device__ __forceinline__ void inv_check(const double *__restrict__ G,
     ng = fmax(ng, __shfl_xor_sync(0xffffffffu, ng, o));
     nq = fmax(nq, __shfl_xor_sync(0xffffffffu, nq, o));
   }
-  if (lane == 0) *q_ok = (*ok && ng * nq < kQMaxCond) ? 1 : 0;
+  if (lane == 0) {
+    const double cond = ng * nq;
+    *q_ok = (*ok && cond < kQMaxCond) ? (cond < kQRefineCond ? 1 : 2) : 0;
+  }
 }
 
 // Shared-memory view of one warp's BPP state (fast kernel).
@@ -240,6 +249,7 @@ struct BppWarp {
   const float *Gabs;
   double dead_below;  // kDead * max diagonal of G
   bool have_q;
+  bool refine;  // solves through G^{-1} take a refinement step
   double *L, *v, *rs;
   int *Fl, *Bl;
   float *xa;
@@ -271,6 +281,7 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   for (int i = 0; i < k; ++i) gmax = fmax(gmax, Gd[i * k + i]);
   w.dead_below = kDead * gmax;
   w.have_q = *q_ok != 0;
+  w.refine = *q_ok == 2;
   w.L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
   w.v = w.L + (size_t)lay.kh * lay.ldl;  // small system's right-hand side, then x_F
   w.rs = w.v + k;                        // r, by index
@@ -407,6 +418,69 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
 #pragma unroll
           for (int t = 0; t < KT; ++t)
             if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the tolerance scales
+          if (w.refine) {
+            // one step of iterative refinement: the passive system's residual
+            // rho_F = r_F - G_FF x_F in FP64, its correction through the same
+            // Q route (z' = Q [rho_F; 0] from the FP32 pair of Q, rho rounded to
+            // FP32: a correction needs no more), and y_B = G_BF x_F - r_B
+            // formed directly; the error of the route drops from ~cond u to
+            // ~(cond u)^2.  r in FP32 is no longer needed (z is formed).
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              double rho = 0.0;
+              if (j < k && pas[t]) {
+                rho = rr[t];
+                for (int a = 0; a < nf; ++a) rho = fma(-G[Fl[a] * k + j], v[a], rho);
+              }
+              if (j < k) rsf[j] = (float)rho;
+            }
+            __syncwarp();
+            double zr[KT];
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              float hi = 0.f, lo = 0.f;
+              if (j < k)
+                for (int l = 0; l < k; ++l) {
+                  const float rl = rsf[l];
+                  two_fma_acc(Qh[l * k + j], rl, hi, lo);
+                  lo = fmaf(Ql[l * k + j], rl, lo);
+                }
+              zr[t] = (double)hi + (double)lo;
+            }
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              if (j < k && !pas[t]) v[posb[t]] = zr[t];
+            }
+            __syncwarp();
+            warp_chol_solve(L, ldl, nb, v, lane);
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              if (j < k && pas[t]) {
+                double s = zr[t];
+                for (int b = 0; b < nb; ++b) s = fma(-Qat(Bl[b], j), v[b], s);
+                x[t] += s;
+              }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < KT; ++t)
+              if (pas[t]) v[posf[t]] = x[t];
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+              const int j = lane + 32 * t;
+              if (j < k && !pas[t]) {
+                double s = -rr[t];
+                for (int a = 0; a < nf; ++a) s = fma(G[Fl[a] * k + j], v[a], s);
+                y[t] = s;
+              }
+            }
+          }
         }
         __syncwarp();
         for (int a = lane; a < nf; a += 32) xa[a] = fabsf((float)v[a]);

@@ -143,9 +143,9 @@ def test_abpp_ill_conditioned_factor_keeps_gram_definite(ax):
     for prec in ("tf32", "fp32"):
         W, H, rel, info = ax.run(A, k, "abpp", 5, Z, H0, prec=prec)
         assert info["bpp_numeric"] == 0
-        # G^-1 is not used at cond(G) >= 1e8, so rows with passive sets above
-        # k / 2 are re-solved by the full-size fallback (and counted)
-        assert info["bpp_redone"] > 0
+        # at cond(G) ~ 1e9 the solves go through G^-1 with a refinement step,
+        # so (almost) no row needs the full-size fallback
+        assert 0 <= info["bpp_redone"] <= 0.01 * 5 * (m + n)
         rels[prec] = rel
     assert np.abs(rels["tf32"] - rels["fp32"]).max() <= 1e-3
     # the factor really is ill-conditioned: after the second W update its
