@@ -32,7 +32,13 @@ WORKLOADS = {
     "scale": {"m": 172_800, "n": 115_200, "k": 100, "rank": 100},
     # 256 problems, m and n uniform in [500, 8000], k from {8, 16, 32, 64}, ABPP
     "batched": {"m": 8000, "n": 8000, "k": 64, "count": 256},
+    # the dense matrix factorised at ranks from 10 to 512 (Sec. 6.3's sweep of k,
+    # carried past the rank where the products leave the HBM roof)
+    "ksweep": {"m": M_FULL, "n": N_FULL, "k": 512, "rank": RANK_FULL,
+               "ks": [10, 20, 30, 40, 50, 64, 100, 128, 192, 256, 320, 384, 448, 512]},
 }
+# dense tensor rate of TF32 relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -353,6 +359,85 @@ def run_batched(args):
     return 0
 
 
+# --------------------------------------------------------------------- k sweep
+def run_ksweep(args):
+    """HALS on the dense matrix at each rank of the sweep, TF32 and BF16
+    products: iterations/s (CUDA graph) and the product launches' average
+    times (profile mode), with the fraction of the HBM roof (algorithmic
+    bytes) and of the tensor roof (2 m n k flop per product) each reaches."""
+    import torch
+
+    from paper_1609_09154_gb300 import aunmf, synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n = args.m, args.n
+    A, _, _ = synth.dense_lowrank_torch(m, n, args.rank, seed=SEED + rank, device=dev)
+    h = aunmf.Handle()
+    pk, pks = peaks()
+    tensor_peak = {"tf32": pk["bf16_tflops"] * TF32_PER_BF16, "bf16": pk["bf16_tflops"]}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    clocks.start()
+    rows, launches = [], 0
+    for k in WORKLOADS["ksweep"]["ks"]:
+        W0, H0 = synth.init_factors_torch(m, n, k, seed=SEED + rank, device=dev)
+        W, H = torch.empty_like(W0), torch.empty_like(H0)
+        for prec in ("tf32", "bf16"):
+            h.run(A, k, "hals", args.warmup, W0, H0, prec=prec, out=(W, H))
+            barrier(world)
+            torch.cuda.synchronize()
+            e0.record()
+            _, _, rel, inf_t = h.run(A, k, "hals", args.steps, W0, H0, prec=prec, out=(W, H))
+            e1.record()
+            launches += int(inf_t["launches"])
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world)
+            _, _, _, inf = h.run(A, k, "hals", args.steps, W0, H0, prec=prec, out=(W, H),
+                                 profile=True)
+            t_aht = inf["ms_aht"] / max(1, inf["n_aht"])
+            t_wta = inf["ms_wta"] / max(1, inf["n_wta"])
+            t = max(t_aht, t_wta) / 1e3
+            gbs = product_bytes(m, n, k, prec) / t / 1e9
+            tfs = 2.0 * m * n * k / t / 1e12
+            fh, ft = gbs / pk["hbm_gbs"], tfs / tensor_peak[prec]
+            rows.append({"k": k, "prec": prec, "iters_per_s": world * args.steps / (ms / 1e3),
+                         "relres_last": float(rel[-1]), "ms_aht": round(t_aht, 4),
+                         "ms_wta": round(t_wta, 4), "product_gbs": round(gbs, 1),
+                         "product_tflops": round(tfs, 1), "frac_hbm": round(fh, 4),
+                         "frac_tensor": round(ft, 4), "bound": "hbm" if fh >= ft else "tensor"})
+        del W0, H0, W, H
+    clk = clocks.stop()
+    if rank == 0:
+        top = [r for r in rows if r["k"] == args.k and r["prec"] == args.prec] or rows[-1:]
+        top = top[0]
+        ach = top["product_tflops"]
+        line = {
+            "metric": METRIC, "value": top["iters_per_s"], "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": world * 1e3 / top["iters_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": top["prec"], "data": "synthetic",
+            "config": {"workload": f"k sweep: dense {m}x{n} FP32, planted rank {args.rank} + "
+                                   f"|N(0,0.01^2)|, HALS at k in {WORKLOADS['ksweep']['ks']}, "
+                                   f"TF32 and BF16 products; value at k={top['k']} "
+                                   f"{top['prec'].upper()}",
+                       "m": m, "n": n, "k": top["k"], "algo": "hals", "prec": top["prec"],
+                       "l2": "inputs larger than the 129 MB L2, no flush needed",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": top["bound"], "achieved": ach,
+                         "peak": round(tensor_peak[top["prec"]], 1), "unit": "TFLOP/s",
+                         "frac": ach / tensor_peak[top["prec"]], "traffic": None,
+                         "kernel": "k_gemm_tc (the slower product launch)",
+                         "peak_note": f"bf16_tflops of {pks} peaks"
+                                      + (" x 1.1/2.25 (nominal TF32/BF16 ratio)"
+                                         if top["prec"] == "tf32" else "")},
+            "sweep": rows, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -546,6 +631,10 @@ def main():
         if args.prec == "fp32":
             args.prec = "tf32"
         return run_batched(args)
+    if args.workload == "ksweep":
+        if args.prec == "fp32":
+            args.prec = "tf32"
+        return run_ksweep(args)
     return run_ours(args)
 
 

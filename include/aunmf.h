@@ -51,7 +51,7 @@ extern "C" {
 #define AUNMF_TF32 1 /* products with A on tensor cores (tcgen05 kind::tf32), FP32 accumulation */
 #define AUNMF_BF16 2 /* products with A on tensor cores from a BF16 copy of A, FP32 accumulation */
 
-#define AUNMF_K_MAX 256
+#define AUNMF_K_MAX 512
 #define AUNMF_BPP_K_MAX 64
 
 typedef struct aunmf_handle aunmf_handle;

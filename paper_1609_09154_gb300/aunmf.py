@@ -19,7 +19,7 @@ MU, HALS, ABPP = 0, 1, 2
 FP32, TF32, BF16 = 0, 1, 2
 ALGOS = {"mu": MU, "hals": HALS, "abpp": ABPP}
 PRECS = {"fp32": FP32, "tf32": TF32, "bf16": BF16}
-K_MAX, BPP_K_MAX = 256, 64
+K_MAX, BPP_K_MAX = 512, 64
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_NOCONVERGE, E_TIMEOUT, E_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6, -7)

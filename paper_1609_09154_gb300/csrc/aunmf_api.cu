@@ -41,6 +41,7 @@ struct aunmf_handle {
   // workspace
   Buf Ht, PW, PHt, GH, GW, G64, gpart, dpart, n2a, ctr, relres, last;
   Buf Ax, At, Hk, Wt, parts, err;  // tensor-core path: layout copies, split partials, error flag
+  Buf tcacc;                       // tensor-core path, k > 64: partial sums of wide products
   Buf colptr, rowidx, cval, cscratch;  // sparse path: CSC copy of A
   Buf bppq;                            // BPP: G^{-1} in FP64
   Buf dHt;                             // loss backward: (dL/dH)^T
@@ -128,6 +129,7 @@ struct RunCtx {
   void *Hk, *Wt;
   int64_t ldh, ldw;
   float *parts;
+  float *tcacc;  // k > 64: the products' per-CTA partial sums (null: added into parts)
   int *err;
   // sparse path: CSC form of A
   const int64_t *colptr;
@@ -192,7 +194,7 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   {
     PhaseTimer t(c, s, kPhAht);
     e = tc::launch_gemm(c.Ax, A->m, A->n, c.ldx, c.Hk, c.k, c.ldh, split, bf,
-                        S == 1 ? c.PW : c.parts, S, c.err, s);
+                        S == 1 ? c.PW : c.parts, S, c.tcacc, c.err, s);
     if (e != cudaSuccess) return e;
   }
   if (S > 1) {
@@ -226,7 +228,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   {
     PhaseTimer t(c, s, kPhWta);
     e = tc::launch_gemm(c.At, A->n, A->m, c.ldat, c.Wt, c.k, c.ldw, split, bf,
-                        S == 1 ? c.PHt : c.parts, S, c.err, s);
+                        S == 1 ? c.PHt : c.parts, S, c.tcacc, c.err, s);
     if (e != cudaSuccess) return e;
   }
   if (S > 1) {
@@ -330,6 +332,10 @@ int prepare_tc(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const size_t parts = tc::parts_elems(m > n ? m : n, k);
   ENS_TC(h, h->parts, sizeof(float) * parts);
   ENS_TC(h, h->err, sizeof(int));
+  if (!use_split(k)) {
+    ENS_TC(h, h->tcacc, sizeof(float) * tc::scratch_elems());
+    c.tcacc = P<float>(h->tcacc);
+  }
   c.Hk = h->Hk.p;
   c.Wt = h->Wt.p;
   c.At = h->At.p;
@@ -416,7 +422,7 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->G64, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
+                 &h->err, &h->tcacc, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
                  &h->batch, &h->batch_meta, &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);

@@ -3,7 +3,8 @@
 // Both factors are held as row-major "rows x k" matrices (W, and H^T for H),
 // so one kernel serves both updates.  For k <= 64 one thread owns one row
 // (k_luc_tpr).  Above, one warp owns one row; lane l holds the entries
-// j = l, l + 32, ... (KT = ceil(k / 32) per lane, k <= 256), and the k x k
+// j = l, l + 32, ... (KT = ceil(k / 32) per lane, rounded up to 12 or 16
+// above 256; k <= 512), and the k x k
 // Gram matrix is staged in shared memory when it fits.
 #include <math.h>
 
@@ -365,7 +366,12 @@ int luc_blocks(int64_t rows) {
     case 5: CALL(5); break;           \
     case 6: CALL(6); break;           \
     case 7: CALL(7); break;           \
-    default: CALL(8); break;          \
+    case 8: CALL(8); break;           \
+    case 9:                           \
+    case 10:                          \
+    case 11:                          \
+    case 12: CALL(12); break;         \
+    default: CALL(16); break;         \
   }
 
 }  // namespace

@@ -281,6 +281,8 @@ cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float 
   const int64_t chunk = (rows + nb - 1) / nb;
   const int kp = (k + 3) & ~3;
   const size_t smem = sizeof(float) * kGramRows * kp;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_gram_partial<<<nb, kGramThreads, smem, s>>>(X, rows, k, ldx, chunk, partials);
   k_gram_reduce<<<(k * k + 31) / 32, 256, 0, s>>>(partials, nb, k, G);
   g_launches += 2;

@@ -87,7 +87,9 @@ cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64
     case 2: k_spmm<2><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
     case 3: k_spmm<3><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
     case 4: k_spmm<4><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
-    default: k_spmm<8><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
+    case 5: case 6: case 7:
+    case 8: k_spmm<8><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
+    default: k_spmm<16><<<(unsigned)nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y); break;
   }
   g_launches += 1;
   return cudaGetLastError();

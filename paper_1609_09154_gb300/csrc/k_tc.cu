@@ -8,7 +8,7 @@
 // The library keeps a transposed copy of A for the second product (set up
 // once per run), so each product streams one copy of A exactly once.
 //
-// Kernel: persistent, one CTA per SM, 6 warps.
+// Kernel: persistent, one CTA per SM, 10 warps.
 //   warp 0     TMA producer: 256 x 128 B of X and BN x 128 B of Y per stage,
 //              128-byte swizzle, into an N-stage shared-memory ring
 //   warp 1     owns the TMEM allocation; one thread issues tcgen05.mma
@@ -30,6 +30,12 @@
 // BN <= 128 so that draining one chunk overlaps the next chunk's MMAs; eight
 // epilogue warps (two per TMEM lane quarter, one per 128-row half) keep a
 // drain shorter than a chunk.
+// Without the hi/lo split (k > 64) each output has one TMEM column; the
+// first 64 sums of a row stay in registers and the rest go to shared memory
+// or, when they do not fit beside two pipeline stages (BN > ~160), to a
+// per-CTA column-major accumulator in global memory that stays in L2.  MMA N
+// is at most 256: a wider product (k <= 512) runs as two column blocks in
+// one launch.
 // Work unit = (256-row tile, K split); splits are summed afterwards in a
 // fixed order, so results do not depend on scheduling.
 //
@@ -39,6 +45,8 @@
 #include <cuda_bf16.h>
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "tc.cuh"
 
@@ -47,6 +55,7 @@ namespace tc {
 namespace {
 
 constexpr int kTileM = 256;          // rows of X per work unit (2 x M=128 MMAs)
+constexpr int kMaxBN = 256;          // MMA N limit; wider products are split by columns
 constexpr int kStageBytesK = 128;    // K extent of one stage in bytes (one 128B swizzle row)
 constexpr int kThreads = 320;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -217,8 +226,9 @@ struct GemmProblem {
   int64_t unit0;       // first work unit of this problem in the launch
   int64_t total_kb;    // K blocks of 128 bytes
   int64_t per_split;   // K blocks per split
-  float *P;            // partials: S x M x k, row-major (S == 1: C itself)
+  float *P;            // partials: S x M x ldc, row-major (S == 1: C itself)
   int k;               // columns of C
+  int ldc;             // row stride of C and of each partial (floats)
   int BN;              // MMA N (rows of Y rounded up to 16), <= BNmax
   int S;               // K splits
   int pair;            // 1: Y rows (2i, 2i+1) hold hi/lo of F's row i; C_i = acc_2i + acc_2i+1
@@ -236,20 +246,35 @@ struct GemmLaunch {
   int chunk_kb;        // K blocks per TMEM accumulation chain
   int acc_ld;          // row stride (floats, odd, >= BN/2 for pair problems and BN
                        // otherwise) of the shared-memory accumulator, 256 rows;
-                       // 0: chunks are added into P itself
+                       // 0: chunks are added into `scratch` (or P without one)
+  int interleave;      // 1: two problems (`one`, `two`) with equal unit counts;
+                       // unit u is unit u / 2 of problem u % 2
+  float *scratch;      // without a shared accumulator: per-CTA column-major
+  int scr_cols;        // accumulators, scr_cols x 256 floats per CTA (L2-resident)
   int *err;
 };
 
+// The problem that work unit u belongs to, and the unit's index v within it.
 __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &one,
-                                                          const GemmProblem *group, int nprob,
-                                                          int64_t u) {
-  if (!group) return &one;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (group[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+                                                          const GemmProblem &two,
+                                                          const GemmProblem *group,
+                                                          const GemmLaunch &L, int64_t u,
+                                                          int64_t *v) {
+  if (L.interleave) {
+    *v = u >> 1;
+    return (u & 1) ? &two : &one;
   }
-  return group + lo;
+  const GemmProblem *p = &one;
+  if (group) {
+    int lo = 0, hi = L.nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (group[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    p = group + lo;
+  }
+  *v = u - p->unit0;
+  return p;
 }
 
 // REGACC: every problem of the launch is a pair problem with BN <= 128
@@ -258,8 +283,8 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &on
 // registers and the rest live in shared memory (or in P).
 template <bool BF16, bool REGACC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ GemmProblem one, const GemmProblem *__restrict__ group,
-              const GemmLaunch L) {
+    k_gemm_tc(const __grid_constant__ GemmProblem one, const __grid_constant__ GemmProblem two,
+              const GemmProblem *__restrict__ group, const GemmLaunch L) {
   constexpr int ESZ = BF16 ? 2 : 4;
   constexpr int BKE = kStageBytesK / ESZ;  // K elements per stage
   constexpr int KPM = BF16 ? 16 : 8;       // K elements per MMA (32 bytes)
@@ -294,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(&one.mapX) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&one.mapY) : "memory");
     }
+    if (L.interleave) asm volatile("prefetch.tensormap [%0];" ::"l"(&two.mapY) : "memory");
   }
   if (warp == 1) tmem_alloc(tslot, L.tmem_cols);
   __syncthreads();
@@ -308,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
-        const GemmProblem *p = find_problem(one, group, L.nprob, u);
-        const int64_t v = u - p->unit0;
+        int64_t v;
+        const GemmProblem *p = find_problem(one, two, group, L, u, &v);
         const int64_t tile = v / p->S, sp = v % p->S;
         const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
         const int row0 = (int)(tile * kTileM);
@@ -331,8 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0, tph = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
-        const GemmProblem *p = find_problem(one, group, L.nprob, u);
-        const int64_t v = u - p->unit0;
+        int64_t v;
+        const GemmProblem *p = find_problem(one, two, group, L, u, &v);
         const int64_t sp = v % p->S;
         const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
         const uint32_t id = idesc(BF16, 128, p->BN);
@@ -378,14 +404,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t tph = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
-      const GemmProblem *p = find_problem(one, group, L.nprob, u);
-      const int64_t v = u - p->unit0;
+      int64_t v;
+      const GemmProblem *p = find_problem(one, two, group, L, u, &v);
       const int64_t tile = v / p->S, sp = v % p->S;
       const int64_t kb0 = sp * p->per_split, kb1 = min(p->total_kb, kb0 + p->per_split);
       const int64_t M = p->M;
       const int k = p->k, BN = p->BN;
+      const int64_t ldc = p->ldc;
       const int64_t row = tile * kTileM + rl;
-      float *Pp = p->P + sp * M * k;
+      float *Pp = p->P + sp * M * ldc;
       const bool live = row < M;
       if constexpr (REGACC) {
         // pair problem, BN <= 128: C_i = acc_2i + acc_2i+1 for i < BN / 2
@@ -414,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         if (live) {
-          float *dg = Pp + row * k;
+          float *dg = Pp + row * ldc;
 #pragma unroll
           for (int o = 0; o < 64; ++o)
             if (o < k) dg[o] = acc[o];
@@ -423,8 +450,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // one TMEM column per output (no split): columns 0..63 summed in
       // registers, the rest in the shared accumulator (row stride acc_ld,
-      // column c at c - 64) or, without one, in P itself
+      // column c at c - 64), else in the CTA's column-major scratch (column c
+      // at (c - 64) * 256: the 32 rows of a warp are 128 contiguous bytes),
+      // else in P itself
       const int W32 = (BN + 31) & ~31;
+      float *scol = (!arow && L.scratch)
+                        ? L.scratch + (size_t)blockIdx.x * L.scr_cols * kTileM + rl
+                        : nullptr;
       float racc[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) racc[j] = 0.f;
@@ -462,8 +494,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) d[jj] = x[jj];
+          } else if (scol) {
+            float *d = scol + (size_t)(g0 - 64) * kTileM;
+            float x[32];
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) x[jj] = __uint_as_float(r[jj]);
+            if (!first) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj) x[jj] += d[jj * kTileM];
+            }
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) d[jj * kTileM] = x[jj];
           } else if (live) {
-            float *dst = Pp + row * k;
+            float *dst = Pp + row * ldc;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj)
               if (g0 + jj < k) {
@@ -479,12 +522,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       if (live) {
-        float *dg = Pp + row * k;
+        float *dg = Pp + row * ldc;
 #pragma unroll
         for (int o = 0; o < 64; ++o)
           if (o < k) dg[o] = racc[o];
-        if (arow || first)
-          for (int o = 64; o < k; ++o) dg[o] = first ? 0.f : arow[o - 64];
+        if (first)
+          for (int o = 64; o < k; ++o) dg[o] = 0.f;
+        else if (arow)
+          for (int o = 64; o < k; ++o) dg[o] = arow[o - 64];
+        else if (scol)
+          for (int o = 64; o < k; ++o) dg[o] = scol[(size_t)(o - 64) * kTileM];
       }
     }
   }
@@ -894,6 +941,7 @@ bool fill_problem(GemmProblem *p, const void *X, int64_t M, int64_t K, int64_t l
   p->per_split = (p->total_kb + S - 1) / S;
   p->P = parts;
   p->k = k;
+  p->ldc = k;
   p->BN = BN;
   p->S = S;
   p->pair = split ? 1 : 0;
@@ -952,12 +1000,15 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units,
     L->chunk_kb = kChunkKBGlobal;
   }
   if (L->nstages > 8) L->nstages = 8;
+  L->interleave = 0;
+  L->scratch = nullptr;
+  L->scr_cols = 0;
   L->err = err;
   return L->nstages >= 2;
 }
 
-cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, const GemmLaunch &L,
-                          bool bf16, cudaStream_t s) {
+cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem &two, const GemmProblem *group,
+                          const GemmLaunch &L, bool bf16, cudaStream_t s) {
   const size_t sbytes = (size_t)(kTileM + L.BNmax) * kStageBytesK;
   const size_t smem = 1024 + (size_t)L.nstages * sbytes +
                       (size_t)kTileM * L.acc_ld * sizeof(float) + 256;
@@ -965,7 +1016,7 @@ cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, cons
   if (grid < 1) return cudaSuccess;
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, kThreads, smem, s>>>(one, group, L);
+    kern<<<grid, kThreads, smem, s>>>(one, two, group, L);
   };
   if (bf16) {
     if (L.regacc) go(k_gemm_tc<true, true>); else go(k_gemm_tc<true, false>);
@@ -976,16 +1027,39 @@ cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem *group, cons
   return cudaGetLastError();
 }
 
+size_t scratch_elems() { return (size_t)num_sms() * kTileM * (kMaxBN - 64); }
+
+// Above kMaxBN columns (unsplit factor, k <= 2 kMaxBN) the product runs as two
+// problems over column blocks of C, [0, kMaxBN) and [kMaxBN, k), in one
+// launch.  Their units alternate, so the two CTAs that need the same tile of
+// X ask for it at about the same time and the second read comes from L2.
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
-                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
-                        cudaStream_t s) {
-  GemmProblem p;
-  if (!fill_problem(&p, X, M, K, ldx, Y, k, ldy, split, bf16, parts, S))
+                        int64_t ldy, bool split, bool bf16, float *parts, int S, float *scratch,
+                        int *err, cudaStream_t s) {
+  GemmProblem p[2];
+  const int k0 = (!split && k > kMaxBN) ? kMaxBN : k;
+  if (k0 < k && k - k0 > kMaxBN) return cudaErrorInvalidValue;
+  if (!fill_problem(&p[0], X, M, K, ldx, Y, k0, ldy, split, bf16, parts, S))
     return cudaErrorInvalidValue;
+  p[0].ldc = k;
+  const int np = k0 < k ? 2 : 1;
+  if (np == 2) {
+    const char *Y1 = static_cast<const char *>(Y) + (size_t)k0 * ldy * (bf16 ? 2 : 4);
+    if (!fill_problem(&p[1], X, M, K, ldx, Y1, k - k0, ldy, false, bf16, parts + k0, S))
+      return cudaErrorInvalidValue;
+    p[1].ldc = k;
+  }
+  const int BNmax = std::max(p[0].BN, p[np - 1].BN);
+  const int accw = std::max(acc_width(p[0]), acc_width(p[np - 1]));
   GemmLaunch L;
-  if (!launch_shape(&L, p.BN, acc_width(p), all_pair(p), problem_units(p), 0, err))
+  if (!launch_shape(&L, BNmax, accw, all_pair(p[0]), problem_units(p[0]) * np, 0, err))
     return cudaErrorInvalidValue;
-  return launch_kernel(p, nullptr, L, bf16, s);
+  L.interleave = np == 2 ? 1 : 0;
+  if (L.acc_ld == 0 && accw > 0 && scratch) {
+    L.scratch = scratch;
+    L.scr_cols = accw;
+  }
+  return launch_kernel(p[0], p[np - 1], nullptr, L, bf16, s);
 }
 
 size_t problem_bytes() { return sizeof(GemmProblem); }
@@ -1013,8 +1087,8 @@ cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, 
   }
   GemmLaunch L;
   if (!launch_shape(&L, BNmax, accw, pairs, units, nprob, err)) return cudaErrorInvalidValue;
-  return launch_kernel(*reinterpret_cast<const GemmProblem *>(host_first),
-                       reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
+  const GemmProblem &h0 = *reinterpret_cast<const GemmProblem *>(host_first);
+  return launch_kernel(h0, h0, reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
 }
 
 cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s) {

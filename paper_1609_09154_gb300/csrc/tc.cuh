@@ -39,10 +39,12 @@ cudaError_t launch_round_copy(const float *A, int64_t m, int64_t n, int64_t lda,
 // X, Y FP32 (TF32 MMA) or BF16.  split == false: Y = F (k x K, ldy);
 // split == true: Y holds 2k rows, hi/lo of F's row i at rows 2i, 2i+1
 // (launch_split_transpose), and the kernel adds each pair.  S == 1 writes the
-// product itself.
+// product itself.  scratch: scratch_elems() floats for the partial sums of
+// wide products (k > ~160), or null (they are then added into parts).
+size_t scratch_elems();
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
-                        int64_t ldy, bool split, bool bf16, float *parts, int S, int *err,
-                        cudaStream_t s);
+                        int64_t ldy, bool split, bool bf16, float *parts, int S, float *scratch,
+                        int *err, cudaStream_t s);
 // Y (2k x rows, ld ldo) = [hi; lo] rows of in (rows x k, ld ldi)^T, rounded to
 // nearest TF32 (FP32 containers) or BF16: hi = round(x), lo = round(x - hi).
 cudaError_t launch_split_transpose(const float *in, int64_t rows, int k, int64_t ldi, void *out,

@@ -54,9 +54,13 @@ def check(got, ref, absprod, K, prec):
 
 
 # ragged M and K, k across the MMA N steps (16 .. 256), single and double
-# TMEM buffering (N <= 128 vs > 128), one and several units per CTA and K splits
+# TMEM buffering (N <= 128 vs > 128), one and several units per CTA and K
+# splits; partial sums in shared memory (k <= ~160) or in the per-CTA global
+# accumulator (k = 256, 300, 384, 512, over several K chunks), and products
+# wider than one MMA (k > 256: two column blocks in one launch)
 SHAPES = [(300, 200, 10), (517, 389, 50), (1031, 129, 33), (64, 48, 1), (700, 260, 100),
-          (257, 1000, 129), (600, 520, 256), (40000, 3000, 50), (2100, 70000, 16)]
+          (257, 1000, 129), (600, 520, 256), (40000, 3000, 50), (2100, 70000, 16),
+          (600, 520, 300), (1500, 1300, 512), (700, 9000, 384)]
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
@@ -68,6 +72,24 @@ def test_products_tensor_cores(ax, m, n, k, prec):
     PH = host(ax.wta(Ad, dev(W), prec=prec))
     check(PW, A @ H.T, np.abs(A) @ np.abs(H).T, n, prec)
     check(PH, W.T @ A, np.abs(W).T @ np.abs(A), m, prec)
+
+
+@pytest.mark.parametrize("algo,prec", [("hals", "tf32"), ("mu", "bf16"), ("hals", "fp32")])
+def test_wide_rank_run_matches_oracle(ax, algo, prec):
+    """k = 300, above one MMA's N: the tensor-core products run as two column
+    blocks of C, the updates hold 12 entries of a row per lane.  Relative
+    residual against the oracle's run from the same start at every one of
+    10 iterations: 1e-3 for the mixed forms, 1e-6 for FP32."""
+    m, n, k, iters = 1200, 900, 300, 10
+    A, _, _ = synth.dense_lowrank(m, n, 40, seed=77)
+    W0, H0 = synth.init_factors(m, n, k, seed=77)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    A, W0, H0 = r32(A), r32(W0), r32(H0)
+    W, H, rel, _ = ax.run(dev(A), k, algo, iters, dev(W0), dev(H0), prec=prec)
+    ref = orc.nmf_run(A, k, algo, iters, W0, H0)["relres"]
+    bar = 1e-6 if prec == "fp32" else 1e-3
+    assert np.abs(rel - ref).max() <= bar, (rel, ref)
+    assert (host(W) >= 0).all() and (host(H) >= 0).all()
 
 
 def test_products_tensor_cores_padded_lda(ax):
