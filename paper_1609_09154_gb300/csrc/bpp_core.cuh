@@ -43,7 +43,7 @@ struct BppLayout {
   size_t g_dbl;    // doubles for G and for Q (each)
   size_t gf_dbl;   // doubles holding |G| in FP32 (tolerance scales)
   size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k),
-                   // r in FP32 (k)
+                   // r in FP32 (k), v split into two FP32 halves (2k)
 };
 
 __host__ __device__ inline BppLayout bpp_layout(int k) {
@@ -52,7 +52,7 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
   l.ldl = l.kh | 1;
   l.g_dbl = (size_t)k * k;
   l.gf_dbl = ((size_t)k * k + 1) / 2;
-  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + 2 * (((size_t)k + 1) / 2);
+  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + 4 * (((size_t)k + 1) / 2);
   return l;
 }
 
@@ -242,6 +242,37 @@ __device__ __forceinline__ void inv_check(const double *__restrict__ G,
   }
 }
 
+// v[0..n) (FP64, shared) into FP32 halves vh + vl = v to ~2^-48 relative, so
+// that sums of products with the FP32 pair of Q need no FP64 arithmetic.
+__device__ __forceinline__ void split_pair(const double *v, int n, float *vh, float *vl,
+                                           int lane) {
+  for (int b = lane; b < n; b += 32) {
+    const double x = v[b];
+    const float h = (float)x;
+    vh[b] = h;
+    vl[b] = (float)(x - (double)h);
+  }
+}
+
+// sum_b Q(I[b], j) v_b with Q = Qh + Ql and v = vh + vl: each Qh vh product
+// exact, the cross terms at FP32 precision (they are ~2^-24 of it), summed in
+// an FP32 pair.  ~10 FP32 operations per term against one FP64 FMA and the
+// two conversions that a product with Q in FP64 would take (the FP64 pipe runs
+// ~1/60 of the FP32 rate on this part).
+__device__ __forceinline__ double q_dot_pair(const float *Qh, const float *Ql, int k,
+                                             const int *I, int n, int j, const float *vh,
+                                             const float *vl) {
+  float hi = 0.f, lo = 0.f;
+  for (int b = 0; b < n; ++b) {
+    const int e = I[b] * k + j;
+    const float qh = Qh[e], ph = vh[b];
+    two_fma_acc(qh, ph, hi, lo);
+    lo = fmaf(qh, vl[b], lo);
+    lo = fmaf(Ql[e], ph, lo);
+  }
+  return (double)hi + (double)lo;
+}
+
 // Shared-memory view of one warp's BPP state (fast kernel).
 struct BppWarp {
   const double *G;
@@ -254,6 +285,7 @@ struct BppWarp {
   int *Fl, *Bl;
   float *xa;
   float *rsf;  // r in FP32, by index
+  float *vh, *vl;  // v = vh + vl (to ~2^-48), for products with the FP32 pair of Q
   int ldl, kh;
 };
 
@@ -289,6 +321,8 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   w.Bl = w.Fl + k;                           // active indices, ascending
   w.xa = reinterpret_cast<float *>(w.Bl + k);  // |x_F| in FP32, F order
   w.rsf = w.xa + 2 * ((k + 1) / 2);
+  w.vh = w.rsf + 2 * ((k + 1) / 2);
+  w.vl = w.vh + 2 * ((k + 1) / 2);
   w.ldl = lay.ldl;
   w.kh = lay.kh;
   return w;
@@ -405,12 +439,13 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
           __syncwarp();
           if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
           warp_chol_solve(L, ldl, nb, v, lane);  // v = Q_BB^{-1} z_B = -y_B
+          split_pair(v, nb, w.vh, w.vl, lane);
+          __syncwarp();
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
             double s = z[t];
-            if (j < k && pas[t])
-              for (int b = 0; b < nb; ++b) s = fma(-Qat(Bl[b], j), v[b], s);
+            if (j < k && pas[t]) s -= q_dot_pair(Qh, Ql, k, Bl, nb, j, w.vh, w.vl);
             x[t] = (j < k && pas[t]) ? s : 0.0;
             if (j < k && !pas[t]) y[t] = -v[posb[t]];
           }
@@ -457,14 +492,12 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             }
             __syncwarp();
             warp_chol_solve(L, ldl, nb, v, lane);
+            split_pair(v, nb, w.vh, w.vl, lane);
+            __syncwarp();
 #pragma unroll
             for (int t = 0; t < KT; ++t) {
               const int j = lane + 32 * t;
-              if (j < k && pas[t]) {
-                double s = zr[t];
-                for (int b = 0; b < nb; ++b) s = fma(-Qat(Bl[b], j), v[b], s);
-                x[t] += s;
-              }
+              if (j < k && pas[t]) x[t] += zr[t] - q_dot_pair(Qh, Ql, k, Bl, nb, j, w.vh, w.vl);
             }
             __syncwarp();
 #pragma unroll

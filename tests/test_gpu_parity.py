@@ -109,8 +109,13 @@ def test_mu_updates(ax, m, n, k):
     np.testing.assert_allclose(host(Hg), orc.mu_update_h(H, PH, GW), rtol=1e-5, atol=0)
 
 
-def assert_sweep(got, ref):
-    tol = 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+def assert_sweep(got, ref, k):
+    """HALS sweep (Eq. halsupdate, k coordinates in order) in FP32 against
+    FP64: each coordinate step is a k-term dot product whose rounding (~k u
+    of its terms) carries into every later coordinate, so the bar grows
+    with k above 64."""
+    scale = max(1.0, k / 64.0)
+    tol = scale * (1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max())
     err = np.abs(got - ref)
     assert (err <= tol).all(), f"max err/tol {np.max(err / tol):.3g}"
 
@@ -123,15 +128,15 @@ def test_hals_updates(ax, m, n, k):
     Wg, Hg = dev(W), dev(H)
     ax.update_w("hals", Wg, dev(PW), dev(GH), Hg)
     Wr, Hr = orc.hals_update_w(W, PW, GH, H)
-    assert_sweep(host(Wg), Wr)
-    assert_sweep(host(Hg), Hr)
+    assert_sweep(host(Wg), Wr, k)
+    assert_sweep(host(Hg), Hr, k)
     W1 = host(Wg)
     PH = (W1.T @ A).astype(np.float32).astype(np.float64)
     GW = (W1.T @ W1).astype(np.float32).astype(np.float64)
     H1 = host(Hg)
     Hg2 = dev(H1)
     ax.update_h("hals", Hg2, dev(PH), dev(GW))
-    assert_sweep(host(Hg2), orc.hals_update_h(H1, PH, GW))
+    assert_sweep(host(Hg2), orc.hals_update_h(H1, PH, GW), k)
 
 
 def assert_bpp(got, ref):

@@ -52,7 +52,8 @@ def host(t):
 
 
 @pytest.mark.parametrize("m,n,density,k", [(3000, 2000, 0.01, 50), (500, 700, 0.05, 1),
-                                            (257, 33, 0.3, 100), (64, 4000, 0.002, 17)])
+                                            (257, 33, 0.3, 100), (64, 4000, 0.002, 17),
+                                            (900, 600, 0.02, 300)])
 def test_sparse_products(ax, m, n, density, k):
     csr, W, H = sparse_problem(m, n, density, k, seed=m + k)
     M, keep = dev_csr(csr, (m, n))
