@@ -76,6 +76,10 @@ constexpr int kChunkKB = AUNMF_TC_CHUNK_KB;
 #endif
 constexpr int kChunkKBReg = AUNMF_TC_CHUNK_KB_REG;  // sums in registers
 constexpr int kChunkKBGlobal = 4 * AUNMF_TC_CHUNK_KB;
+// Above BN = 128 TMEM holds a single chunk buffer and the MMAs wait while it
+// drains: 16 K blocks per chain there (relative bias of the products ~-2e-6
+// TF32, ~-1e-6 BF16, extrapolated from the 4-block figures).
+constexpr int kChunkKBScratch = 8 * AUNMF_TC_CHUNK_KB;
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -129,6 +133,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint64_t policy_evict_last() {
@@ -247,8 +256,8 @@ struct GemmLaunch {
   int acc_ld;          // row stride (floats, odd, >= BN/2 for pair problems and BN
                        // otherwise) of the shared-memory accumulator, 256 rows;
                        // 0: chunks are added into `scratch` (or P without one)
-  int interleave;      // 1: two problems (`one`, `two`) with equal unit counts;
-                       // unit u is unit u / 2 of problem u % 2
+  int interleave;      // 1: two problems (`one`, `two`) with equal unit counts; unit u
+                       // is unit u / 2 of problem (u + w) % 2, w the wave of unit u & ~1
   float *scratch;      // without a shared accumulator: per-CTA column-major
   int scr_cols;        // accumulators, scr_cols x 256 floats per CTA (L2-resident)
   int *err;
@@ -261,8 +270,11 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &on
                                                           const GemmLaunch &L, int64_t u,
                                                           int64_t *v) {
   if (L.interleave) {
-    *v = u >> 1;
-    return (u & 1) ? &two : &one;
+    // the pair of units of one tile swaps blocks from one wave to the next,
+    // so that a CTA does not get the same (maybe narrower) block every wave
+    const int64_t g = u >> 1;
+    *v = g;
+    return (((u & 1) + (2 * g) / gridDim.x) & 1) ? &two : &one;
   }
   const GemmProblem *p = &one;
   if (group) {
@@ -281,7 +293,8 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem &on
 // (k <= 64); each epilogue thread keeps its row's <= 64 sums in registers.
 // Otherwise (one TMEM column per output) the first 64 sums of a row stay in
 // registers and the rest live in shared memory (or in P).
-template <bool BF16, bool REGACC>
+// SCRATCH: the sums past the first 64 columns live in L.scratch.
+template <bool BF16, bool REGACC, bool SCRATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmProblem one, const __grid_constant__ GemmProblem two,
               const GemmProblem *__restrict__ group, const GemmLaunch L) {
@@ -329,7 +342,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
-      const uint64_t pol_x = policy_evict_first(), pol_y = policy_evict_last();
+      // X streams through once (evict first), unless two column blocks share it
+      const uint64_t pol_x = L.interleave ? policy_evict_normal() : policy_evict_first();
+      const uint64_t pol_y = policy_evict_last();
       int st = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -454,14 +469,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       // at (c - 64) * 256: the 32 rows of a warp are 128 contiguous bytes),
       // else in P itself
       const int W32 = (BN + 31) & ~31;
-      float *scol = (!arow && L.scratch)
-                        ? L.scratch + (size_t)blockIdx.x * L.scr_cols * kTileM + rl
-                        : nullptr;
+      float *scol =
+          SCRATCH ? L.scratch + (size_t)blockIdx.x * L.scr_cols * kTileM + rl : nullptr;
       float racc[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) racc[j] = 0.f;
       bool first = true;
       for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
+        // scratch sums of the first group, loaded while the chunk's MMAs run
+        float nx[SCRATCH ? 32 : 1];
+        if constexpr (SCRATCH) {
+          if (!first) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) nx[jj] = scol[(size_t)jj * kTileM];
+          }
+        }
         if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr =
@@ -494,17 +516,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) d[jj] = x[jj];
-          } else if (scol) {
+          } else if constexpr (SCRATCH) {
+            // this group's sums are in nx; the next group's are loaded before
+            // this group is stored (one L2 round trip per group, overlapped)
             float *d = scol + (size_t)(g0 - 64) * kTileM;
-            float x[32];
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) x[jj] = __uint_as_float(r[jj]);
             if (!first) {
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj) x[jj] += d[jj * kTileM];
+              for (int jj = 0; jj < 32; ++jj)
+                r[jj] = __float_as_uint(__uint_as_float(r[jj]) + nx[jj]);
+              if (g0 + 32 < W32) {
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) nx[jj] = d[(size_t)(32 + jj) * kTileM];
+              }
             }
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) d[jj * kTileM] = x[jj];
+            for (int jj = 0; jj < 32; ++jj) d[(size_t)jj * kTileM] = __uint_as_float(r[jj]);
           } else if (live) {
             float *dst = Pp + row * ldc;
 #pragma unroll
@@ -530,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int o = 64; o < k; ++o) dg[o] = 0.f;
         else if (arow)
           for (int o = 64; o < k; ++o) dg[o] = arow[o - 64];
-        else if (scol)
+        else if (SCRATCH)
           for (int o = 64; o < k; ++o) dg[o] = scol[(size_t)(o - 64) * kTileM];
       }
     }
@@ -1000,6 +1026,8 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units,
     L->chunk_kb = kChunkKBGlobal;
   }
   if (L->nstages > 8) L->nstages = 8;
+  // a single TMEM buffer stalls the MMAs for every drain: long chains
+  if (L->nbuf == 1 && L->chunk_kb < kChunkKBScratch) L->chunk_kb = kChunkKBScratch;
   L->interleave = 0;
   L->scratch = nullptr;
   L->scr_cols = 0;
@@ -1019,9 +1047,13 @@ cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem &two, const 
     kern<<<grid, kThreads, smem, s>>>(one, two, group, L);
   };
   if (bf16) {
-    if (L.regacc) go(k_gemm_tc<true, true>); else go(k_gemm_tc<true, false>);
+    if (L.regacc) go(k_gemm_tc<true, true, false>);
+    else if (L.scratch) go(k_gemm_tc<true, false, true>);
+    else go(k_gemm_tc<true, false, false>);
   } else {
-    if (L.regacc) go(k_gemm_tc<false, true>); else go(k_gemm_tc<false, false>);
+    if (L.regacc) go(k_gemm_tc<false, true, false>);
+    else if (L.scratch) go(k_gemm_tc<false, false, true>);
+    else go(k_gemm_tc<false, false, false>);
   }
   g_launches += 1;
   return cudaGetLastError();
@@ -1030,15 +1062,17 @@ cudaError_t launch_kernel(const GemmProblem &one, const GemmProblem &two, const 
 size_t scratch_elems() { return (size_t)num_sms() * kTileM * (kMaxBN - 64); }
 
 // Above kMaxBN columns (unsplit factor, k <= 2 kMaxBN) the product runs as two
-// problems over column blocks of C, [0, kMaxBN) and [kMaxBN, k), in one
-// launch.  Their units alternate, so the two CTAs that need the same tile of
+// problems over column blocks of C, [0, k0) and [k0, k), in one launch.
+// Their units alternate, so the two CTAs that need the same tile of
 // X ask for it at about the same time and the second read comes from L2.
 cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const void *Y, int k,
                         int64_t ldy, bool split, bool bf16, float *parts, int S, float *scratch,
                         int *err, cudaStream_t s) {
+  // two blocks of (about) equal width, which stream X at the same speed and
+  // so stay close enough for the second read of each X tile to hit L2
   GemmProblem p[2];
-  const int k0 = (!split && k > kMaxBN) ? kMaxBN : k;
-  if (k0 < k && k - k0 > kMaxBN) return cudaErrorInvalidValue;
+  const int k0 = (!split && k > kMaxBN) ? pad_to((k + 1) / 2, 16) : k;
+  if (k0 > kMaxBN || k - k0 > kMaxBN) return cudaErrorInvalidValue;
   if (!fill_problem(&p[0], X, M, K, ldx, Y, k0, ldy, split, bf16, parts, S))
     return cudaErrorInvalidValue;
   p[0].ldc = k;
