@@ -44,6 +44,17 @@
  *      passive: its x is 0, as the normal equations leave it undetermined.
  *   R5 (Sec. 6.2) the relative error is measured after both updates of an
  *      iteration, directly as ||A - WH||_F / ||A||_F.
+ *   R6 (Eq. halsupdate, taken as printed: hals_variant 1) the correction is
+ *      not divided by the Gram diagonal, and w^i is normalised inside the
+ *      sweep, before column i+1 is updated, without any rescaling of h_i.
+ *   R7 (Sec. 6.2, the projected gradient as a stopping measure; the paper
+ *      gives no formula) for f = 0.5 ||A - WH||_F^2 the gradient is
+ *      (W H H^T - A H^T, W^T W H - W^T A); its projection keeps an entry
+ *      where the factor's entry is > 0 and min(0, g) where it is 0.  The
+ *      norm of the state an iteration starts from is taken with that
+ *      iteration's H H^T, A H^T and the previous iteration's W^T W, W^T A;
+ *      when it is <= stop_tol times the norm at the start (W0, H0), the run
+ *      stops after that iteration.
  */
 #include <math.h>
 #include <stdint.h>
@@ -240,6 +251,72 @@ void or_hals_update_h(double *H, const double *PH, const double *GW, int k, int6
       H[i * n + c] = v > 0.0 ? v : 0.0;
     }
   }
+}
+
+/* HALS as printed (Eq. halsupdate; reading R6).  W: columns i = 0..k-1 in
+   order,
+     w^i <- [ w^i + (A H^T)^i - W (H H^T)^i ]_+,   w^i <- w^i / ||w^i||,
+   the normalisation taking effect before column i+1 is updated (a zero column
+   stays zero); H is not touched. */
+void or_hals_update_w_printed(double *W, const double *PW, const double *GH, int64_t m,
+                              int k) {
+  for (int i = 0; i < k; ++i) {
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m; ++r) {
+      double wg = 0.0; /* (W (HH^T)^i)_r with the current W */
+      for (int l = 0; l < k; ++l) wg += W[r * k + l] * GH[l * k + i];
+      const double v = W[r * k + i] + PW[r * k + i] - wg;
+      W[r * k + i] = v > 0.0 ? v : 0.0;
+    }
+    double ss = 0.0;
+    for (int64_t r = 0; r < m; ++r) ss += W[r * k + i] * W[r * k + i];
+    const double s = sqrt(ss);
+    if (s > 0.0)
+      for (int64_t r = 0; r < m; ++r) W[r * k + i] /= s;
+  }
+}
+
+/* Rows i = 0..k-1 of H in order:  h_i <- [ h_i + (W^T A)_i - (W^T W)_i H ]_+ */
+void or_hals_update_h_printed(double *H, const double *PH, const double *GW, int k, int64_t n) {
+  for (int i = 0; i < k; ++i) {
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n; ++c) {
+      double gh = 0.0;
+      for (int l = 0; l < k; ++l) gh += GW[i * k + l] * H[l * n + c];
+      const double v = H[i * n + c] + PH[i * n + c] - gh;
+      H[i * n + c] = v > 0.0 ? v : 0.0;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projected gradient (Sec. 6.2; reading R7)                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Squared Frobenius norm of the projected gradient of 0.5 ||A - WH||^2 at
+   (W, H), from GH = H H^T, PW = A H^T, GW = W^T W, PH = W^T A:
+     g = W GH - PW  (m x k),   g' = GW H - PH  (k x n),
+   each entry kept where the factor's entry is > 0, else min(0, entry). */
+double or_pgrad2(const double *W, const double *H, const double *GH, const double *PW,
+                 const double *GW, const double *PH, int64_t m, int64_t n, int k) {
+  double sw = 0.0, sh = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sw)
+  for (int64_t r = 0; r < m; ++r)
+    for (int j = 0; j < k; ++j) {
+      double g = -PW[r * k + j];
+      for (int l = 0; l < k; ++l) g += W[r * k + l] * GH[l * k + j];
+      const double p = W[r * k + j] > 0.0 ? g : (g < 0.0 ? g : 0.0);
+      sw += p * p;
+    }
+#pragma omp parallel for schedule(static) reduction(+ : sh)
+  for (int64_t c = 0; c < n; ++c)
+    for (int i = 0; i < k; ++i) {
+      double g = -PH[i * n + c];
+      for (int l = 0; l < k; ++l) g += GW[i * k + l] * H[l * n + c];
+      const double p = H[i * n + c] > 0.0 ? g : (g < 0.0 ? g : 0.0);
+      sh += p * p;
+    }
+  return sw + sh;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -517,15 +594,23 @@ void or_grad_h_col(const or_matrix *A, const double *W, const double *H, int k, 
 /* AU-NMF driver (Alg. 1)                                                     */
 /* ------------------------------------------------------------------------ */
 
-/* Runs `iters` iterations of Alg. 1 from (W0, H0); W0 is ignored by ABPP
+/* Runs up to `iters` iterations of Alg. 1 from (W0, H0); W0 is ignored by ABPP
    (the paper initialises only H).  relres[t] is ||A - WH|| / ||A|| after
-   iteration t's two updates.  Returns OR_OK, or the first error; *pivots
-   (may be NULL) receives the total number of BPP exchanges. */
-int or_nmf_run(const or_matrix *A, int k, int algo, int iters, const double *W0,
-               const double *H0, double *W, double *H, double *relres, double mu_eps,
-               int bpp_max_iter, int64_t *pivots) {
+   iteration t's two updates.  hals_variant 1 takes Eq. halsupdate as printed
+   (reading R6).  pgrad (may be NULL) receives, per iteration, the norm of the
+   projected gradient of the state the iteration starts from (reading R7);
+   with stop_tol > 0 the run ends after the first iteration whose entry is
+   <= stop_tol times pgrad[0].  *iters_done (may be NULL) is the number of
+   iterations run.  Returns OR_OK, or the first error; *pivots (may be NULL)
+   receives the total number of BPP exchanges. */
+int or_nmf_run_ex(const or_matrix *A, int k, int algo, int iters, const double *W0,
+                  const double *H0, double *W, double *H, double *relres, double mu_eps,
+                  int bpp_max_iter, int64_t *pivots, int hals_variant, double stop_tol,
+                  double *pgrad, int *iters_done) {
   const int64_t m = A->m, n = A->n;
   if (k < 1 || k > 1024 || iters < 0 || algo < 0 || algo > 2) return OR_E_INVAL;
+  if (hals_variant < 0 || hals_variant > 1 || !(stop_tol >= 0.0)) return OR_E_INVAL;
+  const int track = pgrad != NULL || stop_tol > 0.0;
   double *GH = (double *)malloc(sizeof(double) * (size_t)k * k);
   double *GW = (double *)malloc(sizeof(double) * (size_t)k * k);
   double *PW = (double *)malloc(sizeof(double) * (size_t)m * k);
@@ -536,16 +621,29 @@ int or_nmf_run(const or_matrix *A, int k, int algo, int iters, const double *W0,
     else memcpy(W, W0, sizeof(double) * (size_t)m * k);
   }
   if (H != H0) memcpy(H, H0, sizeof(double) * (size_t)k * n);
+  if (track) {
+    /* W^T W and W^T A of the starting W, for the first iteration's measure */
+    or_gram_w(W, m, k, GW);
+    or_wta(A, W, k, PH);
+  }
   int64_t piv = 0;
-  int rc = OR_OK;
+  int rc = OR_OK, done = 0;
+  double pg0 = 0.0;
   for (int t = 0; t < iters && rc == OR_OK; ++t) {
     /* Alg. 1 line 3: update W using H H^T and A H^T */
     or_gram_h(H, k, n, GH);
     or_aht(A, H, k, PW);
+    double pg = 0.0;
+    if (track) {
+      pg = sqrt(or_pgrad2(W, H, GH, PW, GW, PH, m, n, k));
+      if (t == 0) pg0 = pg;
+      if (pgrad) pgrad[t] = pg;
+    }
     if (algo == OR_MU) {
       or_mu_update_w(W, PW, GH, m, k, mu_eps);
     } else if (algo == OR_HALS) {
-      or_hals_update_w(W, PW, GH, m, k, H, n);
+      if (hals_variant == 1) or_hals_update_w_printed(W, PW, GH, m, k);
+      else or_hals_update_w(W, PW, GH, m, k, H, n);
     } else {
       const int64_t p = or_bpp_update_w(W, PW, GH, m, k, bpp_max_iter);
       if (p < 0) rc = (int)p; else piv += p;
@@ -556,14 +654,26 @@ int or_nmf_run(const or_matrix *A, int k, int algo, int iters, const double *W0,
     if (algo == OR_MU) {
       or_mu_update_h(H, PH, GW, k, n, mu_eps);
     } else if (algo == OR_HALS) {
-      or_hals_update_h(H, PH, GW, k, n);
+      if (hals_variant == 1) or_hals_update_h_printed(H, PH, GW, k, n);
+      else or_hals_update_h(H, PH, GW, k, n);
     } else {
       const int64_t p = or_bpp_update_h(H, PH, GW, k, n, bpp_max_iter);
       if (p < 0 && rc == OR_OK) rc = (int)p; else if (p >= 0) piv += p;
     }
     if (relres) relres[t] = or_relres_direct(A, W, H, k);
+    done = t + 1;
+    if (stop_tol > 0.0 && pg <= stop_tol * pg0) break;
   }
   if (pivots) *pivots = piv;
+  if (iters_done) *iters_done = done;
   free(GH); free(GW); free(PW); free(PH);
   return rc;
+}
+
+/* Alg. 1 for exactly `iters` iterations with the default readings. */
+int or_nmf_run(const or_matrix *A, int k, int algo, int iters, const double *W0,
+               const double *H0, double *W, double *H, double *relres, double mu_eps,
+               int bpp_max_iter, int64_t *pivots) {
+  return or_nmf_run_ex(A, k, algo, iters, W0, H0, W, H, relres, mu_eps, bpp_max_iter, pivots, 0,
+                       0.0, NULL, NULL);
 }

@@ -10,10 +10,12 @@ Function map (paper sections / equations):
   aht, wta                    Alg. 1 lines 3-4 (products A H^T, W^T A; dense or CSR)
   mu_update_w, mu_update_h    Sec. 4.1, Eq. (muupdate)
   hals_update_w, hals_update_h  Sec. 4.2, Eq. (halsupdate), readings R2/R3
+  hals_update_w_printed, hals_update_h_printed  Eq. (halsupdate) as printed, R6
+  pgrad                       Sec. 6.2, projected gradient norm, reading R7
   bpp_solve, bpp_update_w/h   Sec. 4.3, Eqs. (single NLS), (KKT); SolveBPP
   relres_direct, relres_trace Sec. 6.2 (relative error ||A-WH||/||A||)
   loss_grad                   0.5||A-WH||^2 and its gradient from R = WH - A
-  nmf_run                     Alg. 1 driver
+  nmf_run                     Alg. 1 driver (HALS variant, projected-gradient stop)
 """
 from __future__ import annotations
 
@@ -75,6 +77,9 @@ def lib():
                 "or_mu_update_h": (None, [P, P, P, I, I64, D]),
                 "or_hals_update_w": (None, [P, P, P, I64, I, P, I64]),
                 "or_hals_update_h": (None, [P, P, P, I, I64]),
+                "or_hals_update_w_printed": (None, [P, P, P, I64, I]),
+                "or_hals_update_h_printed": (None, [P, P, P, I, I64]),
+                "or_pgrad2": (D, [P, P, P, P, P, P, I64, I64, I]),
                 "or_bpp_solve": (I, [P, P, I, P, I]),
                 "or_bpp_update_w": (I64, [P, P, P, I64, I, I]),
                 "or_bpp_update_h": (I64, [P, P, P, I, I64, I]),
@@ -86,6 +91,7 @@ def lib():
                 "or_grad_w_row": (None, [P, P, P, I, I64, P]),
                 "or_grad_h_col": (None, [P, P, P, I, I64, P]),
                 "or_nmf_run": (I, [P, I, I, I, P, P, P, P, P, D, I, P]),
+                "or_nmf_run_ex": (I, [P, I, I, I, P, P, P, P, P, D, I, P, I, D, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -212,6 +218,32 @@ def hals_update_h(H, PH, GW):
     return H
 
 
+def hals_update_w_printed(W, PW, GH):
+    """Eq. (halsupdate) as printed (reading R6): no division by (H H^T)_ii,
+    each column normalised before the next is updated, H untouched."""
+    W = _d(W).copy()
+    m, k = W.shape
+    lib().or_hals_update_w_printed(_p(W), _p(_d(PW)), _p(_d(GH)), m, k)
+    return W
+
+
+def hals_update_h_printed(H, PH, GW):
+    H = _d(H).copy()
+    k, n = H.shape
+    lib().or_hals_update_h_printed(_p(H), _p(_d(PH)), _p(_d(GW)), k, n)
+    return H
+
+
+def pgrad(W, H, GH, PW, GW, PH):
+    """Norm of the projected gradient of 0.5 ||A - WH||^2 at (W, H) from its
+    four products (reading R7)."""
+    W, H = _d(W), _d(H)
+    m, k = W.shape
+    n = H.shape[1]
+    return float(np.sqrt(lib().or_pgrad2(_p(W), _p(H), _p(_d(GH)), _p(_d(PW)), _p(_d(GW)),
+                                         _p(_d(PH)), m, n, k)))
+
+
 def bpp_solve(G, r, max_iter=None):
     """x = argmin_{x>=0} ||Cx - b|| from G = C^T C, r = C^T b.  Returns (x, rc)
     where rc >= 0 is the number of exchanges, < 0 an error code."""
@@ -296,8 +328,11 @@ def resid2(A, W, H):
     return float(lib().or_resid2_direct(as_matrix(A).ptr, _p(W), _p(H), W.shape[1]))
 
 
-def nmf_run(A, k, algo, iters, W0, H0, mu_eps=1e-16, bpp_max_iter=None):
-    """Alg. 1 from (W0, H0).  Returns dict(W, H, relres, rc, pivots)."""
+def nmf_run(A, k, algo, iters, W0, H0, mu_eps=1e-16, bpp_max_iter=None, hals_variant=0,
+            stop_tol=0.0, track_pgrad=False):
+    """Alg. 1 from (W0, H0).  Returns dict(W, H, relres, rc, pivots, iters_done,
+    pgrad); relres and pgrad hold iters_done entries (pgrad None unless
+    tracked: track_pgrad or stop_tol > 0)."""
     A = as_matrix(A)
     algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     W0 = _d(W0) if W0 is not None else np.zeros((A.m, k))
@@ -305,9 +340,14 @@ def nmf_run(A, k, algo, iters, W0, H0, mu_eps=1e-16, bpp_max_iter=None):
     W = np.empty((A.m, k))
     H = np.empty((k, A.n))
     rel = np.zeros(iters)
+    pg = np.zeros(iters) if (track_pgrad or stop_tol > 0) else None
     piv = ctypes.c_int64(0)
-    rc = lib().or_nmf_run(
+    done = ctypes.c_int(0)
+    rc = lib().or_nmf_run_ex(
         A.ptr, k, algo, iters, _p(W0), _p(H0), _p(W), _p(H), _p(rel), mu_eps,
-        10 * k if bpp_max_iter is None else bpp_max_iter, ctypes.byref(piv),
+        10 * k if bpp_max_iter is None else bpp_max_iter, ctypes.byref(piv), int(hals_variant),
+        float(stop_tol), _p(pg) if pg is not None else None, ctypes.byref(done),
     )
-    return {"W": W, "H": H, "relres": rel, "rc": int(rc), "pivots": int(piv.value)}
+    d = int(done.value)
+    return {"W": W, "H": H, "relres": rel[:d], "rc": int(rc), "pivots": int(piv.value),
+            "iters_done": d, "pgrad": pg[:d] if pg is not None else None}

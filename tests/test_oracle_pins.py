@@ -401,3 +401,133 @@ def test_sampled_gradient_rows_and_columns_match_full_gradient():
     np.testing.assert_allclose(dW, R @ H.T, rtol=1e-12)
     np.testing.assert_allclose(dH, W.T @ R, rtol=1e-12)
     assert orc.resid2(A, W, H) == pytest.approx(np.sum(R * R), rel=1e-13)
+
+
+# ------------------------------------------------------------------ HALS as printed (R6)
+def _orthogonal_rows(k, n, norms, seed):
+    """k x n with mutually orthogonal rows of the given norms (H H^T diagonal)."""
+    q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((n, k)))
+    return np.asarray(norms)[:, None] * q.T
+
+
+def test_hals_printed_w_closed_form_with_diagonal_gram():
+    """With H H^T = D diagonal the columns decouple, and the printed rule
+    (no division by D_ii, then normalisation) gives column i = the unit
+    vector along [(1 - D_ii) w^i + (A H^T)^i]_+ in closed form; the exact
+    coordinate step (reading R2) would give [(A H^T)^i / D_ii]_+ instead."""
+    A, _, _ = synth.dense_lowrank(30, 24, 4, seed=21)
+    W0, _ = synth.init_factors(30, 24, 4, seed=21)
+    d = np.array([0.5, 2.0, 1.0, 3.5])
+    H = _orthogonal_rows(4, 24, np.sqrt(d), seed=21)
+    GH = H @ H.T
+    assert np.abs(GH - np.diag(d)).max() < 1e-12
+    PW = A @ H.T
+    W1 = orc.hals_update_w_printed(W0, PW, GH)
+    zero = 0
+    for i in range(4):
+        v = np.maximum(0.0, (1.0 - d[i]) * W0[:, i] + PW[:, i])
+        s = np.linalg.norm(v)
+        if s == 0.0:  # the step empties the column, which then stays zero
+            zero += 1
+            np.testing.assert_array_equal(W1[:, i], 0.0)
+        else:
+            np.testing.assert_allclose(W1[:, i], v / s, rtol=1e-11, atol=1e-13)
+    assert zero == 1  # D_33 = 3.5 overshoots: (1 - 3.5) w + p < 0 here
+
+
+def test_hals_printed_w_satisfies_its_recurrence():
+    """The printed sweep normalises each column before the next is updated:
+    column i of the result is the unit vector along
+    [w0^i + p^i - sum_{l < i} W1^l G_li - sum_{l >= i} W0^l G_li]_+, i.e. the
+    later columns see the earlier ones already normalised (checked on the
+    output, with a Gram matrix that couples every pair of columns)."""
+    A, _, _ = synth.dense_lowrank(25, 20, 3, seed=22)
+    W0, H = synth.init_factors(25, 20, 5, seed=22)
+    GH, PW = H @ H.T, A @ H.T
+    W1 = orc.hals_update_w_printed(W0, PW, GH)
+    np.testing.assert_allclose(np.linalg.norm(W1, axis=0), 1.0, rtol=1e-13)
+    for i in range(5):
+        v = W0[:, i] + PW[:, i] - W1[:, :i] @ GH[:i, i] - W0[:, i:] @ GH[i:, i]
+        v = np.maximum(0.0, v)
+        np.testing.assert_allclose(W1[:, i], v / np.linalg.norm(v), rtol=1e-10, atol=1e-13)
+    # and it differs from normalising after the sweep
+    Wa = W0.copy()
+    for i in range(5):
+        Wa[:, i] = np.maximum(0.0, Wa[:, i] + PW[:, i] - Wa @ GH[:, i])
+    Wa /= np.linalg.norm(Wa, axis=0)
+    assert np.abs(Wa - W1).max() > 1e-3
+
+
+def test_hals_printed_h_equals_exact_step_for_unit_columns():
+    """With unit-norm columns of W, (W^T W)_ii = 1 and the printed H rule is
+    the exact coordinate minimiser (reading R2's rule, pinned above)."""
+    A, _, _ = synth.dense_lowrank(30, 26, 4, seed=23)
+    W, H = synth.init_factors(30, 26, 4, seed=23)
+    W = W / np.linalg.norm(W, axis=0)
+    PH, GW = W.T @ A, W.T @ W
+    np.testing.assert_allclose(orc.hals_update_h_printed(H, PH, GW),
+                               orc.hals_update_h(H, PH, GW), rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ projected gradient (R7)
+def _products(A, W, H):
+    return H @ H.T, A @ H.T, W.T @ W, W.T @ A
+
+
+def test_pgrad_interior_equals_gradient_norm():
+    """For W, H > 0 the projection keeps every entry: the measure is the norm
+    of the gradient of 0.5 ||A - WH||^2 (pinned by finite differences)."""
+    A, _, _ = synth.dense_lowrank(20, 16, 3, seed=24)
+    W, H = synth.init_factors(20, 16, 4, seed=24)
+    W, H = W + 0.1, H + 0.1
+    _, dW, dH = orc.loss_grad(A, W, H)
+    want = np.sqrt(np.sum(dW ** 2) + np.sum(dH ** 2))
+    assert orc.pgrad(W, H, *_products(A, W, H)) == pytest.approx(want, rel=1e-12)
+
+
+def test_pgrad_vanishes_at_an_nnls_solution():
+    """W from an exact NLS solve for fixed H meets the KKT conditions: the
+    W block of the projected gradient is zero (the zero entries' positive
+    gradient is projected away, the positive entries' gradient is zero)."""
+    A, _, _ = synth.dense_lowrank(30, 25, 4, seed=25)
+    _, H = synth.init_factors(30, 25, 4, seed=25)
+    W, rc = orc.bpp_update_w(A @ H.T, H @ H.T)
+    assert rc >= 0
+    assert (W == 0).any() and (W > 0).any()
+    GH, PW = H @ H.T, A @ H.T
+    Hz = np.zeros_like(H)  # no H block
+    assert orc.pgrad(W, Hz, GH, PW, W.T @ W, np.zeros_like(H)) < 1e-10 * np.abs(PW).max()
+    # the raw gradient is not zero there: the projection is doing the work
+    g = W @ GH - PW
+    assert np.abs(g[W == 0]).max() > 1e-3
+
+
+def test_stop_rule_stops_at_the_first_iteration_below_tolerance():
+    """stop_tol: the run ends after the first iteration whose starting state
+    has a projected gradient <= stop_tol times the initial one (reading R7);
+    stop_tol >= 1 ends after one iteration, and the tracked sequence of a
+    full run gives the stopping iteration."""
+    A, _, _ = synth.dense_lowrank(40, 30, 4, seed=26)
+    W0, H0 = synth.init_factors(40, 30, 4, seed=26)
+    assert orc.nmf_run(A, 4, "hals", 10, W0, H0, stop_tol=1.0)["iters_done"] == 1
+    full = orc.nmf_run(A, 4, "hals", 40, W0, H0, track_pgrad=True)
+    pg = full["pgrad"]
+    assert full["iters_done"] == 40 and pg[-1] < 0.05 * pg[0]
+    tol = 0.5 * (pg[5] + pg[6]) / pg[0] if pg[6] < pg[5] else None
+    assert tol is not None
+    first = int(np.argmax(pg <= tol * pg[0]))
+    run = orc.nmf_run(A, 4, "hals", 40, W0, H0, stop_tol=tol)
+    assert run["iters_done"] == first + 1
+    # the same iterates (to the rounding of the threaded residual sums)
+    np.testing.assert_allclose(run["relres"], full["relres"][: first + 1], rtol=1e-13)
+
+
+def test_hals_printed_run_keeps_unit_columns_and_finite_iterates():
+    """The printed rule (a step of 1 instead of 1 / (H H^T)_ii) still keeps
+    W's columns at unit norm and the iterates finite over a run."""
+    A, _, _ = synth.dense_lowrank(40, 30, 4, seed=27)
+    W0, H0 = synth.init_factors(40, 30, 4, seed=27)
+    r = orc.nmf_run(A, 4, "hals", 30, W0, H0, hals_variant=1)
+    assert r["rc"] == 0 and np.isfinite(r["relres"]).all() and np.isfinite(r["H"]).all()
+    norms = np.linalg.norm(r["W"], axis=0)
+    np.testing.assert_allclose(norms[norms > 0], 1.0, rtol=1e-12)
