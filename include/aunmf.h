@@ -80,6 +80,9 @@ typedef struct {
   int bpp_max_pivots; /* ABPP: exchange cap per right-hand side; 0 -> 10*k */
   int use_graph;      /* 1: capture one iteration as a CUDA graph and replay it */
   int profile;        /* 1: time product / update / Gram phases with CUDA events */
+  int hals_variant;   /* HALS: 0 = exact coordinate steps, normalisation compensated in H;
+                         1 = Eq. halsupdate as printed (see aunmf_run) */
+  double stop_tol;    /* > 0: stop on the projected gradient (see aunmf_run); 0 = off */
 } aunmf_options;
 
 /* Per-call report, filled when the pointer is non-NULL. */
@@ -97,6 +100,8 @@ typedef struct {
   int tuned_bpp_rows;       /*   rows per warp per item)                                    */
   int64_t bpp_redone;       /* right-hand sides the fast BPP solver handed to the direct    */
                             /*   (cold-start, full-size Cholesky) fallback                  */
+  double pgrad_first;       /* stop_tol > 0: projected-gradient norm of (W0, H0) ...        */
+  double pgrad_last;        /*   ... and of the state the last iteration started from       */
 } aunmf_info;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -128,7 +133,19 @@ const char *aunmf_last_cuda_error(aunmf_handle *h);
  * HALS takes each column step as the exact coordinate minimiser (the
  * correction divided by the Gram diagonal) and normalises W's columns after
  * the sweep while scaling H's rows by the same norms, which leaves W H
- * unchanged (Eq. halsupdate).  Synchronises the stream. */
+ * unchanged (Eq. halsupdate).  With opt->hals_variant = 1 it takes Eq.
+ * halsupdate as printed instead: no division by the diagonal, and each
+ * column of W normalised before the next is updated, H not rescaled (the W
+ * sweep is then one cooperative launch with a grid-wide norm per column;
+ * no CUDA graph).
+ * Stopping (Sec. 6.2 names the projected gradient as a stopping measure):
+ * with opt->stop_tol > 0 each iteration also forms ||P(grad f)||_F for the
+ * state it starts from, f = 0.5 ||A - WH||_F^2, grad f = (W HH^T - AH^T,
+ * W^T W H - W^T A), P keeping an entry where the factor's entry is > 0 and
+ * min(0, entry) where it is 0 (FP32 entries, FP64 sum); the run ends after
+ * the first iteration whose value is <= stop_tol times that of (W0, H0).
+ * info->iters_done is then the iterations run, and relres holds that many
+ * entries.  Synchronises the stream. */
 int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
               const float *W0, const float *H0, float *W, float *H, double *relres,
               const aunmf_options *opt, aunmf_info *info);

@@ -44,10 +44,10 @@
  *      passive: its x is 0, as the normal equations leave it undetermined.
  *   R5 (Sec. 6.2) the relative error is measured after both updates of an
  *      iteration, directly as ||A - WH||_F / ||A||_F.
- *   R6 (Eq. halsupdate, taken as printed: hals_variant 1) the correction is
+ *   R9 (Eq. halsupdate, taken as printed: hals_variant 1) the correction is
  *      not divided by the Gram diagonal, and w^i is normalised inside the
  *      sweep, before column i+1 is updated, without any rescaling of h_i.
- *   R7 (Sec. 6.2, the projected gradient as a stopping measure; the paper
+ *   R10 (Sec. 6.2, the projected gradient as a stopping measure; the paper
  *      gives no formula) for f = 0.5 ||A - WH||_F^2 the gradient is
  *      (W H H^T - A H^T, W^T W H - W^T A); its projection keeps an entry
  *      where the factor's entry is > 0 and min(0, g) where it is 0.  The
@@ -253,7 +253,7 @@ void or_hals_update_h(double *H, const double *PH, const double *GW, int k, int6
   }
 }
 
-/* HALS as printed (Eq. halsupdate; reading R6).  W: columns i = 0..k-1 in
+/* HALS as printed (Eq. halsupdate; reading R9).  W: columns i = 0..k-1 in
    order,
      w^i <- [ w^i + (A H^T)^i - W (H H^T)^i ]_+,   w^i <- w^i / ||w^i||,
    the normalisation taking effect before column i+1 is updated (a zero column
@@ -290,7 +290,7 @@ void or_hals_update_h_printed(double *H, const double *PH, const double *GW, int
 }
 
 /* ------------------------------------------------------------------------ */
-/* Projected gradient (Sec. 6.2; reading R7)                                  */
+/* Projected gradient (Sec. 6.2; reading R10)                                  */
 /* ------------------------------------------------------------------------ */
 
 /* Squared Frobenius norm of the projected gradient of 0.5 ||A - WH||^2 at
@@ -597,8 +597,8 @@ void or_grad_h_col(const or_matrix *A, const double *W, const double *H, int k, 
 /* Runs up to `iters` iterations of Alg. 1 from (W0, H0); W0 is ignored by ABPP
    (the paper initialises only H).  relres[t] is ||A - WH|| / ||A|| after
    iteration t's two updates.  hals_variant 1 takes Eq. halsupdate as printed
-   (reading R6).  pgrad (may be NULL) receives, per iteration, the norm of the
-   projected gradient of the state the iteration starts from (reading R7);
+   (reading R9).  pgrad (may be NULL) receives, per iteration, the norm of the
+   projected gradient of the state the iteration starts from (reading R10);
    with stop_tol > 0 the run ends after the first iteration whose entry is
    <= stop_tol times pgrad[0].  *iters_done (may be NULL) is the number of
    iterations run.  Returns OR_OK, or the first error; *pivots (may be NULL)

@@ -10,8 +10,8 @@ Function map (paper sections / equations):
   aht, wta                    Alg. 1 lines 3-4 (products A H^T, W^T A; dense or CSR)
   mu_update_w, mu_update_h    Sec. 4.1, Eq. (muupdate)
   hals_update_w, hals_update_h  Sec. 4.2, Eq. (halsupdate), readings R2/R3
-  hals_update_w_printed, hals_update_h_printed  Eq. (halsupdate) as printed, R6
-  pgrad                       Sec. 6.2, projected gradient norm, reading R7
+  hals_update_w_printed, hals_update_h_printed  Eq. (halsupdate) as printed, R9
+  pgrad                       Sec. 6.2, projected gradient norm, reading R10
   bpp_solve, bpp_update_w/h   Sec. 4.3, Eqs. (single NLS), (KKT); SolveBPP
   relres_direct, relres_trace Sec. 6.2 (relative error ||A-WH||/||A||)
   loss_grad                   0.5||A-WH||^2 and its gradient from R = WH - A
@@ -219,7 +219,7 @@ def hals_update_h(H, PH, GW):
 
 
 def hals_update_w_printed(W, PW, GH):
-    """Eq. (halsupdate) as printed (reading R6): no division by (H H^T)_ii,
+    """Eq. (halsupdate) as printed (reading R9): no division by (H H^T)_ii,
     each column normalised before the next is updated, H untouched."""
     W = _d(W).copy()
     m, k = W.shape
@@ -236,7 +236,7 @@ def hals_update_h_printed(H, PH, GW):
 
 def pgrad(W, H, GH, PW, GW, PH):
     """Norm of the projected gradient of 0.5 ||A - WH||^2 at (W, H) from its
-    four products (reading R7)."""
+    four products (reading R10)."""
     W, H = _d(W), _d(H)
     m, k = W.shape
     n = H.shape[1]

@@ -49,6 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [
         ("prec", ctypes.c_int), ("mu_eps", ctypes.c_double), ("bpp_max_pivots", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
+        ("hals_variant", ctypes.c_int), ("stop_tol", ctypes.c_double),
     ]
 
 
@@ -62,6 +63,7 @@ class Info(ctypes.Structure):
         ("n_aht", ctypes.c_int), ("n_wta", ctypes.c_int), ("launches", ctypes.c_int64),
         ("tuned_bpp_warps", ctypes.c_int), ("tuned_bpp_rows", ctypes.c_int),
         ("bpp_redone", ctypes.c_int64),
+        ("pgrad_first", ctypes.c_double), ("pgrad_last", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -195,9 +197,12 @@ class Handle:
 
     # ---------------------------------------------------------- whole runs
     def run(self, A, k, algo, iters, W0, H0, *, prec="fp32", mu_eps=0.0, bpp_max_pivots=0,
-            use_graph=True, profile=False, out=None, allow_noconverge=False):
+            use_graph=True, profile=False, out=None, allow_noconverge=False, hals_variant=0,
+            stop_tol=0.0):
         """Alg. 1 on device tensors.  A: dense (m x n) tensor or a Matrix
-        (e.g. from csr_matrix).  Returns (W, H, relres ndarray, info dict)."""
+        (e.g. from csr_matrix).  hals_variant 1: Eq. halsupdate as printed;
+        stop_tol > 0: stop on the projected gradient.  Returns (W, H, relres
+        ndarray of info["iters_done"] entries, info dict)."""
         torch = _torch()
         M = A if isinstance(A, Matrix) else dense_matrix(A)
         algo = ALGOS[algo] if isinstance(algo, str) else algo
@@ -210,12 +215,14 @@ class Handle:
         else:
             W, H = out
         rel = np.zeros(max(iters, 1), dtype=np.float64)
-        opt = Options(prec, mu_eps, bpp_max_pivots, int(use_graph), int(profile))
+        opt = Options(prec, mu_eps, bpp_max_pivots, int(use_graph), int(profile),
+                      int(hals_variant), float(stop_tol))
         info = Info()
         rc = self._lib.aunmf_run(self._h, ctypes.byref(M), k, algo, iters, _ptr(W0), _ptr(H0),
                                  _ptr(W), _ptr(H), rel.ctypes.data_as(ctypes.c_void_p),
                                  ctypes.byref(opt), ctypes.byref(info))
-        result = (W, H, rel[:iters], info.as_dict())
+        done = info.iters_done if rc in (OK, E_NOCONVERGE) else iters
+        result = (W, H, rel[:done], info.as_dict())
         self._check(rc, allow=(E_NOCONVERGE,) if allow_noconverge else (), result=result)
         return result
 

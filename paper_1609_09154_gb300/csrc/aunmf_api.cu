@@ -49,6 +49,7 @@ struct aunmf_handle {
   // autotuned BPP work tile per batch signature: (warps per block, rows per warp)
   std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> bpp_tuned;
   Buf hA, hW, hH;  // device copies for aunmf_run_host
+  Buf aux;         // printed HALS sweep / projected gradient: partials, barrier, values
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
 };
@@ -136,6 +137,12 @@ struct RunCtx {
   const int32_t *rowidx;
   const float *cval;
   bool profile;
+  int hals_variant;     // 1: Eq. halsupdate as printed
+  bool track_pg;        // form the projected gradient each iteration
+  double *sweep_part;   // printed W sweep: 2 x printed_sweep_blocks() partials
+  unsigned *bar;        // its grid-barrier counter
+  double *pg_part;      // projected gradient: 2 x pgrad_blocks() partials
+  double *pg_dev;       // projected-gradient norm per iteration (slot ctr->iter)
   std::vector<cudaEvent_t> *ev;          // profile events (pairs)
   std::vector<int> *ev_phase;            // phase index per pair
 };
@@ -264,23 +271,49 @@ cudaError_t gram(aunmf_handle *h, RunCtx &c, const float *X, int64_t rows, float
   return launch_gram(X, rows, c.k, c.k, G32, c.gpart, h->max_gram_blocks, s);
 }
 
+// Projected-gradient norm of the current (W, H) into pg_dev[ctr->iter], from
+// G_H, A H^T of H and G_W, W^T A of W (the last two held from the update of
+// H that produced it).
+cudaError_t projected_gradient(RunCtx &c, cudaStream_t s) {
+  const int nb = pgrad_blocks();
+  cudaError_t e = launch_pgrad_partial(c.W, c.PW, c.GH, c.A->m, c.k, c.pg_part, s);
+  if (e == cudaSuccess) e = launch_pgrad_partial(c.Ht, c.PHt, c.GW, c.A->n, c.k, c.pg_part + nb, s);
+  if (e == cudaSuccess) e = launch_pgrad_final(c.pg_part, 2 * nb, c.ctr, c.pg_dev, s);
+  return e;
+}
+
 // One AU-NMF iteration (see the file header).
 cudaError_t iterate(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   const int64_t m = c.A->m, n = c.A->n;
   const int k = c.k;
+  const bool printed = c.algo == AUNMF_HALS && c.hals_variant == 1;
   cudaError_t e;
   if ((e = product_aht(h, c, s)) != cudaSuccess) return e;
-  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.W, c.PW, c.GH, c.GH64, m, s)) != cudaSuccess) return e; }
+  if (c.track_pg) {
+    PhaseTimer t(c, s, kPhOther);
+    if ((e = projected_gradient(c, s)) != cudaSuccess) return e;
+  }
+  {
+    PhaseTimer t(c, s, kPhUpdate);
+    e = printed ? launch_hals_w_printed(c.W, c.PW, c.GH, m, k, c.sweep_part, c.bar, c.err, s)
+                : update(c, c.W, c.PW, c.GH, c.GH64, m, s);
+    if (e != cudaSuccess) return e;
+  }
   {
     PhaseTimer t(c, s, kPhGram);
     if ((e = gram(h, c, c.W, m, c.GW, c.GW64, s)) != cudaSuccess) return e;
   }
-  if (c.algo == AUNMF_HALS) {
+  if (c.algo == AUNMF_HALS && !printed) {
     PhaseTimer t(c, s, kPhUpdate);
     if ((e = launch_hals_normalise(c.W, m, c.Ht, n, c.GW, k, s)) != cudaSuccess) return e;
   }
   if ((e = product_wta(h, c, s)) != cudaSuccess) return e;
-  { PhaseTimer t(c, s, kPhUpdate); if ((e = update(c, c.Ht, c.PHt, c.GW, c.GW64, n, s)) != cudaSuccess) return e; }
+  {
+    PhaseTimer t(c, s, kPhUpdate);
+    e = printed ? launch_hals(c.Ht, c.PHt, c.GW, n, k, s, true)
+                : update(c, c.Ht, c.PHt, c.GW, c.GW64, n, s);
+    if (e != cudaSuccess) return e;
+  }
   {
     PhaseTimer t(c, s, kPhGram);
     if ((e = gram(h, c, c.Ht, n, c.GH, c.GH64, s)) != cudaSuccess) return e;
@@ -303,6 +336,8 @@ int check_run_args(const aunmf_matrix *A, int k, int algo, int iters, const floa
   if (!H0 || !W || !H || (algo != AUNMF_ABPP && !W0)) return AUNMF_E_INVAL;
   const int prec = o ? o->prec : AUNMF_FP32;
   if (prec < AUNMF_FP32 || prec > AUNMF_BF16) return AUNMF_E_INVAL;
+  if (o && (o->hals_variant < 0 || o->hals_variant > 1)) return AUNMF_E_INVAL;
+  if (o && !(o->stop_tol >= 0.0 && o->stop_tol < 1e300)) return AUNMF_E_INVAL;
   if (prec != AUNMF_FP32) {
     if (!A->dense) return AUNMF_E_UNSUPPORTED;
     int rc = tc::check(A->m, A->n, A->lda, k, prec, A->dense);
@@ -422,7 +457,7 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->G64, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->tcacc, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
+                 &h->err, &h->tcacc, &h->aux, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
                  &h->batch, &h->batch_meta, &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
@@ -486,6 +521,20 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   c.ev = &ev;
   c.ev_phase = &ev_phase;
   c.profile = o.profile != 0;
+  c.hals_variant = algo == AUNMF_HALS ? o.hals_variant : 0;
+  c.track_pg = o.stop_tol > 0.0;
+  if (c.hals_variant == 1 || c.track_pg) {
+    const size_t dbl = 2 * (size_t)printed_sweep_blocks() + 2 * (size_t)pgrad_blocks() +
+                       (size_t)(iters > 0 ? iters : 1);
+    ENS(h, h->aux, sizeof(double) * dbl + 256);
+    c.sweep_part = P<double>(h->aux);
+    c.pg_part = c.sweep_part + 2 * (size_t)printed_sweep_blocks();
+    c.pg_dev = c.pg_part + 2 * (size_t)pgrad_blocks();
+    c.bar = reinterpret_cast<unsigned *>(c.pg_dev + (iters > 0 ? iters : 1));
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), s));
+  }
   const long long launches0 = g_launches;
   long long graph_launches = 0;
   cudaEvent_t t0, t1;
@@ -519,10 +568,16 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     if (prc != AUNMF_OK) return prc;
   }
   CK(h, gram(h, c, c.Ht, n, c.GH, c.GH64, s));
+  if (c.track_pg) {
+    // W^T W and W^T A of the starting W, for the first iteration's measure
+    CK(h, gram(h, c, c.W, m, c.GW, c.GW64, s));
+    CK(h, product_wta(h, c, s));
+  }
 
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
-  const bool use_graph = o.use_graph && !o.profile && iters > 1;
+  // the printed HALS sweep is a cooperative launch: not captured
+  const bool use_graph = o.use_graph && !o.profile && iters > 1 && c.hals_variant == 0;
   if (use_graph) {
     // capture one iteration on the private stream, replay on the caller's
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -530,26 +585,39 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     cudaError_t ce = iterate(h, c, h->cap_stream);
     const long long per_iter = g_launches - lc0;
     g_launches = lc0;  // captured, not launched: counted per replay below
-    graph_launches = per_iter * iters;
+    graph_launches = per_iter;
     cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
     if (ce != cudaSuccess) return fail_cuda(h, ce, "iterate (capture)");
     if (ee != cudaSuccess) return fail_cuda(h, ee, "cudaStreamEndCapture");
     CK(h, cudaGraphInstantiate(&gexec, graph, 0));
-    for (int t = 0; t < iters; ++t) CK(h, cudaGraphLaunch(gexec, s));
-  } else {
-    for (int t = 0; t < iters; ++t) {
+  }
+  // with a stop rule the host reads each iteration's measure before the next
+  int done = 0;
+  double pg0 = 0.0, pg_last = 0.0;
+  for (int t = 0; t < iters; ++t) {
+    if (gexec) {
+      CK(h, cudaGraphLaunch(gexec, s));
+    } else {
       cudaError_t e = iterate(h, c, s);
       if (e != cudaSuccess) return fail_cuda(h, e, "iterate");
     }
+    done = t + 1;
+    if (c.track_pg) {
+      CK(h, cudaMemcpyAsync(&pg_last, c.pg_dev + t, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaStreamSynchronize(s));
+      if (t == 0) pg0 = pg_last;
+      if (!(pg_last > o.stop_tol * pg0)) break;
+    }
   }
+  graph_launches *= done;
   CK(h, launch_transpose(c.Ht, n, k, H, s));
   CK(h, cudaEventRecord(t1, s));
   DevCounters hc{};
   int herr = 0;
   CK(h, cudaMemcpyAsync(&hc, c.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
   if (c.err) CK(h, cudaMemcpyAsync(&herr, c.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  if (relres && iters > 0)
-    CK(h, cudaMemcpyAsync(relres, c.relres_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+  if (relres && done > 0)
+    CK(h, cudaMemcpyAsync(relres, c.relres_dev, sizeof(double) * done, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
@@ -559,7 +627,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     info->bpp_nonconverged = hc.bpp_nonconv;
     info->bpp_numeric = hc.bpp_numeric;
     info->bpp_redone = hc.bpp_redo;
-    info->iters_done = iters;
+    info->iters_done = done;
+    info->pgrad_first = pg0;
+    info->pgrad_last = pg_last;
     info->launches = g_launches - launches0 + graph_launches;
     cudaEventElapsedTime(&info->ms_total, t0, t1);
     for (size_t p = 0; p < ev_phase.size(); ++p) {

@@ -87,8 +87,24 @@ cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, float 
 // Local updates on row-major X (rows x k) given P (rows x k) and G (k x k).
 cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
                       cudaStream_t s);
+// unit: Eq. halsupdate as printed (no division by G_ii).
 cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, int k,
-                        cudaStream_t s);
+                        cudaStream_t s, bool unit = false);
+// The W sweep of Eq. halsupdate as printed (no division by (HH^T)_ii, each
+// column normalised before the next is updated), one cooperative launch.
+// part: 2 * printed_sweep_blocks() doubles; bar: one counter (zeroed here);
+// err: set when a grid barrier waits too long.
+int printed_sweep_blocks();
+cudaError_t launch_hals_w_printed(float *W, const float *P, const float *G, int64_t rows, int k,
+                                  double *part, unsigned *bar, int *err, cudaStream_t s);
+// Projected gradient of 0.5 ||A - WH||^2: pgrad_blocks() FP64 partials of
+// sum p^2 over rows of X, p = (X G - P)_rj where X_rj > 0, else min(0, .);
+// then out[ctr->iter] = sqrt(sum of n partials).
+int pgrad_blocks();
+cudaError_t launch_pgrad_partial(const float *X, const float *P, const float *G, int64_t rows,
+                                 int k, double *part, cudaStream_t s);
+cudaError_t launch_pgrad_final(const double *part, int n, const DevCounters *ctr, double *out,
+                               cudaStream_t s);
 // HALS normalisation: s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i (Y = Ht,
 // may be null, rows_y rows); GW_ij /= s_i s_j.  Zero norms leave column i as is.
 cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t rows_y, float *GW,

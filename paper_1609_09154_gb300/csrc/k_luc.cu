@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kLucThreads)
 template <int KT, bool SMEM>
 __global__ void __launch_bounds__(kLucThreads)
     k_hals(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ Gg,
-           int64_t rows, int k) {
+           int64_t rows, int k, int unit) {
   extern __shared__ float sG[];
   const float *G = stage_gram<SMEM>(Gg, k, sG);
   const int lane = threadIdx.x & 31;
@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(kLucThreads)
         }
         const float dot = warp_sum(part);
         const float gii = Gi[i];
-        if (lane == ii && gii > 0.f) {
-          const float v = x[ti] + (p[ti] - dot) / gii;
+        if (lane == ii && (unit || gii > 0.f)) {
+          // unit: Eq. halsupdate as printed, no division by G_ii
+          const float v = x[ti] + (unit ? p[ti] - dot : (p[ti] - dot) / gii);
           x[ti] = v > 0.f ? v : 0.f;
         }
       }
@@ -214,7 +215,7 @@ __global__ void k_hals_scale_gram(float *__restrict__ GW, int k) {
 // staged transposed and zero-padded to KP, so (x G)_i = sum_j x_j G_ji reads
 // row i of the staged copy with 16-byte broadcast loads; padded coordinates
 // have G_ii = 0 and stay 0.
-enum LucOp { kOpMu = 0, kOpHals = 1, kOpGrad = 2 };
+enum LucOp { kOpMu = 0, kOpHals = 1, kOpGrad = 2, kOpHalsUnit = 3 };
 constexpr int kTprThreads = 256;
 constexpr int kTprWarps = kTprThreads / kWarp;
 
@@ -301,13 +302,19 @@ __global__ void __launch_bounds__(kTprThreads)
     for (int j = 0; j < KP; ++j) x[j] = t[j];
     __syncwarp();
     tile_in<KP>(P + r0 * k, nr, k, tile, lane);
-    if constexpr (OP == kOpHals) {
+    if constexpr (OP == kOpHals || OP == kOpHalsUnit) {
       // x_i <- max(0, x_i + (p_i - (x G)_i) / G_ii), i ascending, with the
-      // entries before i already updated; G_ii <= 0 leaves x_i as it is
+      // entries before i already updated; G_ii <= 0 leaves x_i as it is.
+      // kOpHalsUnit: Eq. halsupdate as printed, without the division.
 #pragma unroll
       for (int i = 0; i < KP; ++i) {
         const float gii = sGt[i * KP + i];
-        if (gii > 0.f) {
+        if (OP == kOpHalsUnit) {
+          if (i < k) {
+            const float v = x[i] + (t[i] - xg<KP>(x, sGt, i));
+            x[i] = v > 0.f ? v : 0.f;
+          }
+        } else if (gii > 0.f) {
           const float v = x[i] + (t[i] - xg<KP>(x, sGt, i)) / gii;
           x[i] = v > 0.f ? v : 0.f;
         }
@@ -374,7 +381,211 @@ int luc_blocks(int64_t rows) {
     default: CALL(16); break;         \
   }
 
+// ---------------------------------------------------------------- HALS as printed
+// The W sweep of Eq. halsupdate as printed: w^i <- [w^i + P^i - W G^i]_+ with
+// no division by G_ii, and w^i normalised before column i + 1 is updated (H
+// is not rescaled).  Every column waits for a norm over all rows, so the
+// sweep is one cooperative launch: threads own rows (grid-strided); after
+// column i the blocks' FP64 sums of squares meet behind a bounded grid
+// barrier, each block adds them in block order (the same norm everywhere),
+// and each thread rescales its rows' column i when it next reads them.
+constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kPrintedThreads = 256;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// true once every block of the grid has arrived for the gen-th time (the
+// counter starts at 0); false, with *err set, after ~2 s or once another
+// block has given up.
+__device__ bool grid_barrier(unsigned *count, unsigned gen, int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const unsigned target = gen * gridDim.x;
+    const long long t0 = clock64();
+    ok = 1;
+    while (ld_acquire_u32(count) < target) {
+      if (clock64() - t0 > kBarrierCycles || *(volatile int *)err) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double block_sum_d256(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kPrintedThreads / 32; ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kPrintedThreads)
+    k_hals_w_printed(float *__restrict__ W, const float *__restrict__ P,
+                     const float *__restrict__ Gg, int64_t rows, int k, int gsm,
+                     double *__restrict__ part, unsigned *bar, int *err) {
+  extern __shared__ float sG[];
+  __shared__ double red[kPrintedThreads / 32];
+  __shared__ float s_inv;
+  const float *G = Gg;
+  if (gsm) {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) sG[e] = Gg[e];
+    __syncthreads();
+    G = sG;
+  }
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  float inv = 1.f;  // 1 / ||w^{i-1}||, or 1 for a zero column
+  for (int i = 0; i < k; ++i) {
+    double ss = 0.0;
+    for (int64_t r = tid; r < rows; r += nt) {
+      float *x = W + r * k;
+      if (i > 0) x[i - 1] *= inv;
+      float d = 0.f;
+      for (int l = 0; l < k; ++l) d = fmaf(x[l], G[l * k + i], d);
+      const float v = x[i] + P[r * k + i] - d;
+      const float y = v > 0.f ? v : 0.f;
+      x[i] = y;
+      ss = fma((double)y, (double)y, ss);
+    }
+    const double bsum = block_sum_d256(ss, red);
+    double *pi = part + (size_t)(i & 1) * gridDim.x;
+    if (threadIdx.x == 0) pi[blockIdx.x] = bsum;
+    if (!grid_barrier(bar, (unsigned)(i + 1), err)) return;
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(pi + b);
+      s_inv = t > 0.0 ? (float)(1.0 / sqrt(t)) : 1.f;
+    }
+    __syncthreads();
+    inv = s_inv;
+  }
+  for (int64_t r = tid; r < rows; r += nt) W[r * k + k - 1] *= inv;
+}
+
+// ---------------------------------------------------------------- projected gradient
+// Per block: sum over rows of X (rows x k) of p^2, p the projected entry of
+// g = (X G - P)_rj: g where X_rj > 0, else min(0, g).  A warp per row; lane
+// l holds x_j and g_j for j = l, l + 32, ...; x_l is broadcast by shuffle.
+template <int KT>
+__global__ void __launch_bounds__(kLucThreads)
+    k_pgrad_partial(const float *__restrict__ X, const float *__restrict__ P,
+                    const float *__restrict__ G, int64_t rows, int k, double *__restrict__ part) {
+  __shared__ double red[kLucWarps];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
+  const int64_t ws = (int64_t)gridDim.x * kLucWarps;
+  double acc = 0.0;
+  for (int64_t r = w0; r < rows; r += ws) {
+    float x[KT], g[KT];
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      x[t] = j < k ? X[r * k + j] : 0.f;
+      g[t] = 0.f;
+    }
+#pragma unroll
+    for (int tl = 0; tl < KT; ++tl)
+      for (int ll = 0; ll < 32; ++ll) {
+        const int l = 32 * tl + ll;
+        if (l >= k) break;
+        const float xl = __shfl_sync(0xffffffffu, x[tl], ll);
+#pragma unroll
+        for (int t = 0; t < KT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < k) g[t] = fmaf(xl, G[l * k + j], g[t]);
+        }
+      }
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) {
+        const float gg = g[t] - P[r * k + j];
+        const float pr = x[t] > 0.f ? gg : fminf(gg, 0.f);
+        acc = fma((double)pr, (double)pr, acc);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLucWarps; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out[ctr->iter] = sqrt(sum of the partials), in partial order.
+__global__ void k_pgrad_final(const double *__restrict__ part, int n, const DevCounters *ctr,
+                              double *__restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int b = 0; b < n; ++b) t += part[b];
+  out[ctr->iter] = sqrt(t);
+}
+
 }  // namespace
+
+int printed_sweep_blocks() { return 2 * 152; }
+
+cudaError_t launch_hals_w_printed(float *W, const float *P, const float *G, int64_t rows, int k,
+                                  double *part, unsigned *bar, int *err, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  int gsm = k <= kSmemGramMaxK ? 1 : 0;
+  const size_t smem = gsm ? sizeof(float) * k * k : 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hals_w_printed, kPrintedThreads, smem);
+  int64_t grid = (int64_t)per_sm * sms;
+  const int64_t need = (rows + kPrintedThreads - 1) / kPrintedThreads;
+  if (grid > need) grid = need;
+  if (grid > printed_sweep_blocks()) grid = printed_sweep_blocks();
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  void *args[] = {&W, &P, &G, &rows, &k, &gsm, &part, &bar, &err};
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_hals_w_printed), (int)grid,
+                                  kPrintedThreads, args, smem, s);
+  g_launches += 1;
+  return e;
+}
+
+int pgrad_blocks() { return 152 * 2; }
+
+cudaError_t launch_pgrad_partial(const float *X, const float *P, const float *G, int64_t rows,
+                                 int k, double *part, cudaStream_t s) {
+  const int kt = (k + 31) / 32, nb = pgrad_blocks();
+  if (rows == 0) return cudaMemsetAsync(part, 0, sizeof(double) * nb, s);
+#define AUNMF_CALL_PG(KT) k_pgrad_partial<KT><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k, part);
+  AUNMF_KT_SWITCH(kt, AUNMF_CALL_PG)
+#undef AUNMF_CALL_PG
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pgrad_final(const double *part, int n, const DevCounters *ctr, double *out,
+                               cudaStream_t s) {
+  k_pgrad_final<<<1, 32, 0, s>>>(part, n, ctr, out);
+  g_launches += 1;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
                       cudaStream_t s) {
@@ -393,15 +604,18 @@ cudaError_t launch_mu(float *X, const float *P, const float *G, int64_t rows, in
 }
 
 cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, int k,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool unit) {
   if (rows == 0) return cudaSuccess;
-  if (k <= kTprMaxK) return launch_tpr_k<kOpHals>(X, P, G, rows, k, 0.f, nullptr, nullptr, s);
+  if (k <= kTprMaxK)
+    return unit ? launch_tpr_k<kOpHalsUnit>(X, P, G, rows, k, 0.f, nullptr, nullptr, s)
+                : launch_tpr_k<kOpHals>(X, P, G, rows, k, 0.f, nullptr, nullptr, s);
   const int kt = (k + 31) / 32, nb = luc_blocks(rows);
   const bool sm = k <= kSmemGramMaxK;
   const size_t smem = sm ? sizeof(float) * k * k : 0;
-#define AUNMF_CALL_HALS(KT)                                                    \
-  if (sm) k_hals<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k);    \
-  else k_hals<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k);
+  const int u = unit ? 1 : 0;
+#define AUNMF_CALL_HALS(KT)                                                       \
+  if (sm) k_hals<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k, u);    \
+  else k_hals<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k, u);
   AUNMF_KT_SWITCH(kt, AUNMF_CALL_HALS)
 #undef AUNMF_CALL_HALS
   g_launches += 1;

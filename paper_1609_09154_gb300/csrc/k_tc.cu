@@ -78,8 +78,11 @@ constexpr int kChunkKBReg = AUNMF_TC_CHUNK_KB_REG;  // sums in registers
 constexpr int kChunkKBGlobal = 4 * AUNMF_TC_CHUNK_KB;
 // Above BN = 128 TMEM holds a single chunk buffer and the MMAs wait while it
 // drains: 16 K blocks per chain there (relative bias of the products ~-2e-6
-// TF32, ~-1e-6 BF16, extrapolated from the 4-block figures).
-constexpr int kChunkKBScratch = 8 * AUNMF_TC_CHUNK_KB;
+// TF32, ~-1e-6 BF16, extrapolated from the 4-block figures), and 32 when the
+// sums live in the L2-resident scratch (~-5e-6 / ~-2e-6), whose round trips
+// make each drain the longest.
+constexpr int kChunkKBLong = 8 * AUNMF_TC_CHUNK_KB;
+constexpr int kChunkKBScratch = 16 * AUNMF_TC_CHUNK_KB;
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -139,6 +142,15 @@ __device__ __forceinline__ uint64_t policy_evict_normal() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
   return p;
+}
+// Scratch sums: kept in L2 (evict last) against the stream of X tiles.
+__device__ __forceinline__ float ld_keep(const float *p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
@@ -471,6 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int W32 = (BN + 31) & ~31;
       float *scol =
           SCRATCH ? L.scratch + (size_t)blockIdx.x * L.scr_cols * kTileM + rl : nullptr;
+      const uint64_t pol_s = SCRATCH ? policy_evict_last() : 0;
       float racc[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) racc[j] = 0.f;
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (SCRATCH) {
           if (!first) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) nx[jj] = scol[(size_t)jj * kTileM];
+            for (int jj = 0; jj < 32; ++jj) nx[jj] = ld_keep(scol + (size_t)jj * kTileM, pol_s);
           }
         }
         if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
@@ -526,11 +539,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 r[jj] = __float_as_uint(__uint_as_float(r[jj]) + nx[jj]);
               if (g0 + 32 < W32) {
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) nx[jj] = d[(size_t)(32 + jj) * kTileM];
+                for (int jj = 0; jj < 32; ++jj)
+                  nx[jj] = ld_keep(d + (size_t)(32 + jj) * kTileM, pol_s);
               }
             }
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) d[(size_t)jj * kTileM] = __uint_as_float(r[jj]);
+            for (int jj = 0; jj < 32; ++jj)
+              st_keep(d + (size_t)jj * kTileM, __uint_as_float(r[jj]), pol_s);
           } else if (live) {
             float *dst = Pp + row * ldc;
 #pragma unroll
@@ -1027,7 +1042,7 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units,
   }
   if (L->nstages > 8) L->nstages = 8;
   // a single TMEM buffer stalls the MMAs for every drain: long chains
-  if (L->nbuf == 1 && L->chunk_kb < kChunkKBScratch) L->chunk_kb = kChunkKBScratch;
+  if (L->nbuf == 1 && L->chunk_kb < kChunkKBLong) L->chunk_kb = kChunkKBLong;
   L->interleave = 0;
   L->scratch = nullptr;
   L->scr_cols = 0;
@@ -1092,6 +1107,7 @@ cudaError_t launch_gemm(const void *X, int64_t M, int64_t K, int64_t ldx, const 
   if (L.acc_ld == 0 && accw > 0 && scratch) {
     L.scratch = scratch;
     L.scr_cols = accw;
+    L.chunk_kb = kChunkKBScratch;
   }
   return launch_kernel(p[0], p[np - 1], nullptr, L, bf16, s);
 }

@@ -1,0 +1,138 @@
+"""HALS as printed (Eq. halsupdate taken literally: no division by the Gram
+diagonal, each column of W normalised before the next is updated, H not
+rescaled) and the projected-gradient stop rule, against the FP64 oracle.
+
+The printed rule overshoots (its step is 1 instead of 1 / (HH^T)_ii), so its
+relative residual jumps between iterations and the trajectory amplifies
+rounding: input noise of FP32 size (6e-8 relative) moves the oracle's relres
+by <= 7e-8 over 8 iterations on the small configuration, and by ~2e-5 over
+20.  Whole runs are therefore compared over 6 iterations: 1e-6 for FP32,
+1e-3 for the mixed forms.  The projected gradient is formed from FP32 entries
+(g = X G - P, cancellation near a stationary point) and summed in FP64: its
+values are compared at 1e-4 relative for the first iterations."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1609_09154_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ax():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1609_09154_gb300 import aunmf
+
+    return aunmf.Handle()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def problem(m, n, k, rank, seed):
+    A, _, _ = synth.dense_lowrank(m, n, rank, seed=seed)
+    W0, H0 = synth.init_factors(m, n, k, seed=seed)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    return r32(A), r32(W0), r32(H0)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return problem(2000, 1500, 10, 10, 2024)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_printed_run_matches_oracle(ax, small, prec):
+    A, W0, H0 = small
+    iters = 6
+    W, H, rel, info = ax.run(dev(A), 10, "hals", iters, dev(W0), dev(H0), prec=prec,
+                             hals_variant=1)
+    ref = orc.nmf_run(A, 10, "hals", iters, W0, H0, hals_variant=1)
+    bar = 1e-6 if prec == "fp32" else 1e-3
+    assert info["iters_done"] == iters
+    assert np.abs(rel - ref["relres"]).max() <= bar, (rel, ref["relres"])
+    Wh = host(W)
+    norms = np.linalg.norm(Wh, axis=0)
+    np.testing.assert_allclose(norms[norms > 0], 1.0, rtol=1e-5)
+    assert (Wh >= 0).all() and (host(H) >= 0).all()
+
+
+@pytest.mark.parametrize("m,n,k", [(2000, 1500, 10), (3000, 700, 150), (40000, 3000, 16),
+                                   (257, 300, 64)])
+def test_printed_sweep_one_iteration_elementwise(ax, m, n, k):
+    """One iteration (printed W sweep, then the printed H rows), factors entry
+    by entry: k = 150 reads G from global memory in the sweep and takes the
+    warp-per-row H step; m = 40000 spreads the sweep over many blocks, each
+    column's norm crossing the grid barrier."""
+    A, W0, H0 = problem(m, n, k, min(k, 12), seed=m + k)
+    W, H, _, _ = ax.run(dev(A), k, "hals", 1, dev(W0), dev(H0), hals_variant=1)
+    ref = orc.nmf_run(A, k, "hals", 1, W0, H0, hals_variant=1)
+    for got, want in ((host(W), ref["W"]), (host(H), ref["H"])):
+        tol = 1e-4 * np.abs(want) + 1e-5 * np.abs(want).max()
+        err = np.abs(got - want)
+        assert (err <= tol).all(), f"max err/tol {np.max(err / tol):.3g}"
+
+
+def _stop_tol_for(pg, lo=2, hi=25):
+    """A tolerance whose first crossing is at an index j in [lo, hi) with a
+    >= 1.5 % margin on both sides (FP32 rounding moves the GPU's values by
+    ~1e-5 relative, so it cannot move the crossing)."""
+    for j in range(lo, min(hi, len(pg))):
+        before = pg[:j].min()
+        if pg[j] < 0.97 * before:
+            return 0.5 * (pg[j] + before) / pg[0], j
+    return None, None
+
+
+# (the printed HALS rule's measure stays above its starting value on this
+# problem, so it has no crossing to test; its runs are compared above)
+@pytest.mark.parametrize("algo,variant", [("hals", 0), ("mu", 0), ("abpp", 0)])
+def test_stop_rule_matches_oracle(ax, small, algo, variant):
+    A, W0, H0 = small
+    full = orc.nmf_run(A, 10, algo, 30, W0, H0, hals_variant=variant, track_pgrad=True)
+    tol, j = _stop_tol_for(full["pgrad"])
+    assert tol is not None, full["pgrad"] / full["pgrad"][0]
+    ref = orc.nmf_run(A, 10, algo, 30, W0, H0, hals_variant=variant, stop_tol=tol)
+    assert ref["iters_done"] == j + 1
+    W, H, rel, info = ax.run(dev(A), 10, algo, 30, dev(W0), dev(H0), hals_variant=variant,
+                             stop_tol=tol)
+    assert info["iters_done"] == j + 1
+    assert len(rel) == j + 1
+    np.testing.assert_allclose(rel, ref["relres"], rtol=0, atol=1e-6)
+    assert info["pgrad_first"] == pytest.approx(full["pgrad"][0], rel=1e-4)
+    assert info["pgrad_last"] == pytest.approx(full["pgrad"][j], rel=1e-3)
+
+
+def test_stop_rule_graph_and_eager_agree(ax, small):
+    A, W0, H0 = small
+    full = orc.nmf_run(A, 10, "hals", 30, W0, H0, track_pgrad=True)
+    tol, j = _stop_tol_for(full["pgrad"])
+    Ad = dev(A)
+    out = []
+    for g in (True, False):
+        W, H, rel, info = ax.run(Ad, 10, "hals", 30, dev(W0), dev(H0), use_graph=g,
+                                 stop_tol=tol)
+        out.append((host(W), host(H), rel, info["iters_done"]))
+    assert out[0][3] == out[1][3] == j + 1
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+
+
+def test_stop_tol_one_runs_one_iteration_and_bad_options(ax, small):
+    from paper_1609_09154_gb300 import aunmf
+
+    A, W0, H0 = small
+    W, H, rel, info = ax.run(dev(A), 10, "mu", 10, dev(W0), dev(H0), stop_tol=1.0)
+    assert info["iters_done"] == 1 and len(rel) == 1
+    for kw in ({"hals_variant": 2}, {"stop_tol": -1.0}, {"stop_tol": float("nan")}):
+        with pytest.raises(aunmf.AunmfError) as e:
+            ax.run(dev(A), 10, "hals", 2, dev(W0), dev(H0), **kw)
+        assert e.value.code == aunmf.E_INVAL

@@ -403,7 +403,7 @@ def test_sampled_gradient_rows_and_columns_match_full_gradient():
     assert orc.resid2(A, W, H) == pytest.approx(np.sum(R * R), rel=1e-13)
 
 
-# ------------------------------------------------------------------ HALS as printed (R6)
+# ------------------------------------------------------------------ HALS as printed (R9)
 def _orthogonal_rows(k, n, norms, seed):
     """k x n with mutually orthogonal rows of the given norms (H H^T diagonal)."""
     q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((n, k)))
@@ -469,7 +469,7 @@ def test_hals_printed_h_equals_exact_step_for_unit_columns():
                                orc.hals_update_h(H, PH, GW), rtol=1e-12, atol=1e-14)
 
 
-# ------------------------------------------------------------------ projected gradient (R7)
+# ------------------------------------------------------------------ projected gradient (R10)
 def _products(A, W, H):
     return H @ H.T, A @ H.T, W.T @ W, W.T @ A
 
@@ -504,7 +504,7 @@ def test_pgrad_vanishes_at_an_nnls_solution():
 
 def test_stop_rule_stops_at_the_first_iteration_below_tolerance():
     """stop_tol: the run ends after the first iteration whose starting state
-    has a projected gradient <= stop_tol times the initial one (reading R7);
+    has a projected gradient <= stop_tol times the initial one (reading R10);
     stop_tol >= 1 ends after one iteration, and the tracked sequence of a
     full run gives the stopping iteration."""
     A, _, _ = synth.dense_lowrank(40, 30, 4, seed=26)
