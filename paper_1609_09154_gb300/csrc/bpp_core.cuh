@@ -41,7 +41,7 @@ struct BppLayout {
   int kh;          // largest factorisation: floor(k / 2)
   int ldl;         // leading dimension of L (odd)
   size_t g_dbl;    // doubles for G and for Q (each)
-  size_t gf_dbl;   // doubles holding |G| in FP32 (tolerance scales)
+  size_t gf_dbl;   // doubles holding G as an FP32 pair (hi k^2, lo k^2)
   size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k),
                    // r in FP32 (k), v split into two FP32 halves (2k)
 };
@@ -51,7 +51,7 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
   l.kh = k / 2 > 0 ? k / 2 : 1;
   l.ldl = l.kh | 1;
   l.g_dbl = (size_t)k * k;
-  l.gf_dbl = ((size_t)k * k + 1) / 2;
+  l.gf_dbl = (size_t)k * k;
   l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + 4 * (((size_t)k + 1) / 2);
   return l;
 }
@@ -277,7 +277,7 @@ __device__ __forceinline__ double q_dot_pair(const float *Qh, const float *Ql, i
 struct BppWarp {
   const double *G;
   const float *Qh, *Ql;  // G^{-1} = Qh + Ql (FP32 pair)
-  const float *Gabs;
+  const float *Gh, *Gl;  // G = Gh + Gl (to ~2^-48); |Gh| scales the tolerances
   double dead_below;  // kDead * max diagonal of G
   bool have_q;
   bool refine;  // solves through G^{-1} take a refinement step
@@ -289,26 +289,31 @@ struct BppWarp {
   int ldl, kh;
 };
 
-// Stage G (FP64), Q and |G| (FP32) of one problem into shared memory (block-
-// wide; the caller synchronises) and return warp wib's view.
+// Stage G (FP64 and as an FP32 pair) and Q (FP32 pair) of one problem into
+// shared memory (block-wide; the caller synchronises) and return warp wib's
+// view.
 __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
                                              const float *__restrict__ Qsg, const int *q_ok, int k,
                                              double *sm, int wib) {
   const BppLayout lay = bpp_layout(k);
   double *G = sm;
   float *Qs = reinterpret_cast<float *>(sm + lay.g_dbl);  // hi (k^2), lo (k^2)
-  float *Gabs = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);
+  float *Gp = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);  // hi (k^2), lo (k^2)
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    G[e] = Gd[e];
+    const double g = Gd[e];
+    G[e] = g;
     Qs[e] = Qsg[e];
     Qs[k * k + e] = Qsg[k * k + e];
-    Gabs[e] = (float)fabs(Gd[e]);
+    const float gh = (float)g;
+    Gp[e] = gh;
+    Gp[k * k + e] = (float)(g - (double)gh);
   }
   BppWarp w;
   w.G = G;
   w.Qh = Qs;
   w.Ql = Qs + k * k;
-  w.Gabs = Gabs;
+  w.Gh = Gp;
+  w.Gl = Gp + k * k;
   double gmax = 0.0;
   for (int i = 0; i < k; ++i) gmax = fmax(gmax, Gd[i * k + i]);
   w.dead_below = kDead * gmax;
@@ -341,7 +346,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
   const float *Qh = w.Qh, *Ql = w.Ql;
   auto Gat = [G, k](int a, int b) { return G[a * k + b]; };
   auto Qat = [Qh, Ql, k](int a, int b) { return (double)Qh[a * k + b] + (double)Ql[a * k + b]; };
-  const float *Gabs = w.Gabs;
+  const float *Gh = w.Gh, *Gl = w.Gl;
   const bool have_q = w.have_q;
   double *L = w.L, *v = w.v, *rs = w.rs;
   int *Fl = w.Fl, *Bl = w.Bl;
@@ -455,20 +460,21 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the tolerance scales
           if (w.refine) {
             // one step of iterative refinement: the passive system's residual
-            // rho_F = r_F - G_FF x_F in FP64, its correction through the same
-            // Q route (z' = Q [rho_F; 0] from the FP32 pair of Q, rho rounded to
-            // FP32: a correction needs no more), and y_B = G_BF x_F - r_B
-            // formed directly; the error of the route drops from ~cond u to
-            // ~(cond u)^2.  r in FP32 is no longer needed (z is formed).
+            // rho_F = r_F - G_FF x_F, its correction through the same Q route
+            // (z' = Q [rho_F; 0] from the FP32 pair of Q, rho rounded to FP32:
+            // a correction needs no more), and y_B = G_BF x_F - r_B formed
+            // directly; the error of the route drops from ~cond u to
+            // ~(cond u)^2.  The sums with G take its FP32 pair and x_F split
+            // in two: ~2^-44 of the terms, on a par with the ~1e-14 to which
+            // G itself is formed.  r in FP32 is no longer needed (z is formed).
+            __syncwarp();
+            split_pair(v, nf, w.vh, w.vl, lane);
             __syncwarp();
 #pragma unroll
             for (int t = 0; t < KT; ++t) {
               const int j = lane + 32 * t;
               double rho = 0.0;
-              if (j < k && pas[t]) {
-                rho = rr[t];
-                for (int a = 0; a < nf; ++a) rho = fma(-G[Fl[a] * k + j], v[a], rho);
-              }
+              if (j < k && pas[t]) rho = rr[t] - q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl);
               if (j < k) rsf[j] = (float)rho;
             }
             __syncwarp();
@@ -504,14 +510,12 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             for (int t = 0; t < KT; ++t)
               if (pas[t]) v[posf[t]] = x[t];
             __syncwarp();
+            split_pair(v, nf, w.vh, w.vl, lane);
+            __syncwarp();
 #pragma unroll
             for (int t = 0; t < KT; ++t) {
               const int j = lane + 32 * t;
-              if (j < k && !pas[t]) {
-                double s = -rr[t];
-                for (int a = 0; a < nf; ++a) s = fma(G[Fl[a] * k + j], v[a], s);
-                y[t] = s;
-              }
+              if (j < k && !pas[t]) y[t] = q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl) - rr[t];
             }
           }
         }
@@ -519,9 +523,14 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
         for (int a = lane; a < nf; a += 32) xa[a] = fabsf((float)v[a]);
         __syncwarp();
         // ---- active set: y = G_BF x_F - r_B (direct route; the Q route has
-        // it already) and the tolerance scale |r_j| + sum |G_jF x_F|, summed
-        // in FP32 from |G| and |x_F|
+        // it already), from the FP32 pairs of G and x_F like z (its error,
+        // ~2^-44 of the scale below, is far under the 1e-11 tolerance), and
+        // the tolerance scale |r_j| + sum |G_jF x_F| in FP32
         const bool direct = nf <= nb || !have_q;
+        if (direct) {
+          split_pair(v, nf, w.vh, w.vl, lane);
+          __syncwarp();
+        }
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int j = lane + 32 * t;
@@ -531,13 +540,9 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             tau[t] = 0.0;
           } else {
             float mag = fabsf((float)rr[t]);
-            for (int a = 0; a < nf; ++a) mag = fmaf(Gabs[Fl[a] * k + j], xa[a], mag);
+            for (int a = 0; a < nf; ++a) mag = fmaf(fabsf(Gh[Fl[a] * k + j]), xa[a], mag);
             tau[t] = kBppYTol * (double)mag;
-            if (direct) {
-              double s = -rr[t];
-              for (int a = 0; a < nf; ++a) s = fma(G[Fl[a] * k + j], v[a], s);
-              y[t] = s;
-            }
+            if (direct) y[t] = q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl) - rr[t];
           }
         }
         __syncwarp();
