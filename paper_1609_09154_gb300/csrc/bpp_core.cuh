@@ -17,6 +17,7 @@ namespace bpp {
 // conflicts at k = 64).
 
 constexpr double kBppYTol = 1e-11;
+constexpr float kBppYTolF = 1e-11f;
 // An index whose Gram diagonal is <= kDead of the largest (a zero column of
 // the fixed factor, which ABPP can produce) never becomes passive: the normal
 // equations leave its value undetermined and it stays 0.
@@ -66,8 +67,11 @@ __host__ __device__ inline BppLayout bpp_layout(int k) {
 // instructions plus ~10 per column, where one lane per row would cost
 // ~n^2 / 2 (each lane running the longest dot product of its column).
 // Returns false (warp-uniform) on a non-positive pivot.
-template <class Acc>
-__device__ __forceinline__ bool warp_cholesky(Acc M, const int *I, int n, double *L, int ldl,
+__device__ __forceinline__ double rsq(double d) { return rsqrt(d); }
+__device__ __forceinline__ float rsq(float d) { return rsqrtf(d); }
+
+template <class T, class Acc>
+__device__ __forceinline__ bool warp_cholesky(Acc M, const int *I, int n, T *L, int ldl,
                                               int lane) {
   // lower triangle of M_FF into L; entry e of the triangle is (a, b) with
   // a (a + 1) / 2 <= e < (a + 1) (a + 2) / 2
@@ -81,9 +85,9 @@ __device__ __forceinline__ bool warp_cholesky(Acc M, const int *I, int n, double
   }
   __syncwarp();
   for (int c = 0; c < n; ++c) {
-    const double d = L[c * ldl + c];
-    if (!(d > 0.0)) return false;
-    const double r = rsqrt(d);
+    const T d = L[c * ldl + c];
+    if (!(d > T(0))) return false;
+    const T r = rsq(d);
     for (int a = c + 1 + lane; a < n; a += 32) L[a * ldl + c] *= r;
     __syncwarp();
     if (lane == 0) L[c * ldl + c] = r;
@@ -103,17 +107,17 @@ __device__ __forceinline__ bool warp_cholesky(Acc M, const int *I, int n, double
 
 // v <- (L L^T)^{-1} v for v[0..n) in shared memory (L from warp_cholesky,
 // reciprocal diagonal).
-__device__ __forceinline__ void warp_chol_solve(const double *L, int ldl, int n, double *v,
-                                                int lane) {
+template <class T>
+__device__ __forceinline__ void warp_chol_solve(const T *L, int ldl, int n, T *v, int lane) {
   for (int c = 0; c < n; ++c) {
-    const double vc = v[c] * L[c * ldl + c];
+    const T vc = v[c] * L[c * ldl + c];
     __syncwarp();
     for (int a = c + 1 + lane; a < n; a += 32) v[a] = fma(-L[a * ldl + c], vc, v[a]);
     if (lane == 0) v[c] = vc;
     __syncwarp();
   }
   for (int c = n - 1; c >= 0; --c) {
-    const double vc = v[c] * L[c * ldl + c];
+    const T vc = v[c] * L[c * ldl + c];
     __syncwarp();
     for (int a = lane; a < c; a += 32) v[a] = fma(-L[c * ldl + a], vc, v[a]);
     if (lane == 0) v[c] = vc;
@@ -279,6 +283,7 @@ struct BppWarp {
   const float *Qh, *Ql;  // G^{-1} = Qh + Ql (FP32 pair)
   const float *Gh, *Gl;  // G = Gh + Gl (to ~2^-48); |Gh| scales the tolerances
   double dead_below;  // kDead * max diagonal of G
+  unsigned live[2];    // bit j % 32 of live[j / 32]: G_jj > dead_below (k <= 64)
   bool have_q;
   bool refine;  // solves through G^{-1} take a refinement step
   double *L, *v, *rs;
@@ -317,6 +322,13 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   double gmax = 0.0;
   for (int i = 0; i < k; ++i) gmax = fmax(gmax, Gd[i * k + i]);
   w.dead_below = kDead * gmax;
+  {
+    // the warp's own copy of the live-index mask (its lanes are converged here)
+    const int lane = threadIdx.x & 31;
+    const int j0 = lane, j1 = lane + 32;
+    w.live[0] = __ballot_sync(0xffffffffu, j0 < k && Gd[j0 * k + j0] > w.dead_below);
+    w.live[1] = __ballot_sync(0xffffffffu, j1 < k && Gd[j1 * k + j1] > w.dead_below);
+  }
   w.have_q = *q_ok != 0;
   w.refine = *q_ok == 2;
   w.L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
@@ -333,8 +345,99 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   return w;
 }
 
+// ---- FP32-pair arithmetic (no FP64 instruction): a value is hi + lo with
+// |lo| <= ulp(hi) / 2, ~48 bits.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (h, l) += (bh, bl)
+__device__ __forceinline__ void pair_add(float &h, float &l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+// (h, l) = sum_b M(I[b], j) x_b, M = Mh + Ml and x = xh + xl (pairs): each
+// Mh xh product exact, the cross terms at FP32 precision, summed in a pair.
+__device__ __forceinline__ void pair_dot(const float *Mh, const float *Ml, int k, const int *I,
+                                         int n, int j, const float *xh, const float *xl,
+                                         float &h, float &l) {
+  float hi = 0.f, lo = 0.f;
+  for (int b = 0; b < n; ++b) {
+    const int e = I[b] * k + j;
+    const float mh = Mh[e], ph = xh[b];
+    two_fma_acc(mh, ph, hi, lo);
+    lo = fmaf(mh, xl[b], lo);
+    lo = fmaf(Ml[e], ph, lo);
+  }
+  h = __fadd_rn(hi, lo);
+  l = __fsub_rn(lo, __fsub_rn(h, hi));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+constexpr int kRefineSteps = 6;
+constexpr float kRefineTol = 9.31322575e-10f;  // 2^-30
+
+// M x = b for the n x n SPD matrix M = Mh + Ml (an FP32 pair; rows and
+// columns I of a k x k matrix) and b = bh + bl (a pair, in I order): an FP32
+// Cholesky of Mh, then iterative refinement with the residual b - M x summed
+// in pairs, until a correction is below 2^-30 of x (x goes out in FP32).  No
+// FP64 instruction: this part runs ~60x more FP32 than FP64 operations per
+// clock, and its FP64 solves cost ~16 SM clocks per warp instruction, most of
+// them serial (one per column).  x = xh + xl, in I order.  Returns false
+// (warp-uniform) on a pivot <= 0 of Mh or when the corrections stall (an
+// ill-conditioned M); the caller then takes the FP64 solve.
+__device__ __forceinline__ bool solve_mixed(const float *Mh, const float *Ml, int k, const int *I,
+                                            int n, const float *bh, const float *bl, float *Lf,
+                                            int ldl, float *d, float *xh, float *xl, int lane) {
+  auto Mf = [Mh, k](int a, int b) { return Mh[a * k + b]; };
+  if (!warp_cholesky(Mf, I, n, Lf, ldl, lane)) return false;
+  for (int a = lane; a < n; a += 32) {
+    xh[a] = 0.f;
+    xl[a] = 0.f;
+    d[a] = bh[a];
+  }
+  __syncwarp();
+  for (int step = 0; step < kRefineSteps; ++step) {
+    warp_chol_solve(Lf, ldl, n, d, lane);
+    float dm = 0.f, xm = 0.f;
+    for (int a = lane; a < n; a += 32) {
+      pair_add(xh[a], xl[a], d[a], 0.f);
+      dm = fmaxf(dm, fabsf(d[a]));
+      xm = fmaxf(xm, fabsf(xh[a]));
+    }
+    dm = warp_max(dm);
+    xm = warp_max(xm);
+    if (dm <= kRefineTol * xm) return true;
+    if (!(dm < 3.0e38f)) return false;
+    __syncwarp();
+    for (int a = lane; a < n; a += 32) {
+      float h, l;
+      pair_dot(Mh, Ml, k, I, n, I[a], xh, xl, h, l);  // (M x)_a
+      float rh = bh[a], rl = bl[a];
+      pair_add(rh, rl, -h, -l);
+      d[a] = __fadd_rn(rh, rl);
+    }
+    __syncwarp();
+  }
+  return false;
+}
+
 // Solves row `row` of R (rows x k) into X (warm: start from the support of
-// X's row); returns the exchanges, *failed_numeric / *failed_cap.
+// X's row); returns the exchanges, *failed_numeric / *failed_cap.  Each
+// lane keeps its entries of r (FP32), x and y (FP32 pairs) and the
+// tolerances (FP32): the exchange rule needs only their signs and
+// magnitudes, and FP64 instructions -- conversions and compares included --
+// run at ~1/60 of the FP32 rate.  The passive-set systems are solved by
+// solve_mixed, with the FP64 Cholesky as the fallback.
 template <int KT>
 __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__restrict__ R,
                                             int64_t row, int k, float *__restrict__ X, int warm,
@@ -348,247 +451,308 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
   auto Qat = [Qh, Ql, k](int a, int b) { return (double)Qh[a * k + b] + (double)Ql[a * k + b]; };
   const float *Gh = w.Gh, *Gl = w.Gl;
   const bool have_q = w.have_q;
-  double *L = w.L, *v = w.v, *rs = w.rs;
+  double *L = w.L, *v = w.v;
+  float *Lf = reinterpret_cast<float *>(w.L);
+  float *bh = reinterpret_cast<float *>(w.v), *bl = bh + k;  // right-hand side pair
+  float *dv = reinterpret_cast<float *>(w.rs);               // corrections
+  float *vh = w.vh, *vl = w.vl;  // solution pairs: F order (x_F) or B order (Q_BB^-1 z_B)
   int *Fl = w.Fl, *Bl = w.Bl;
   float *xa = w.xa, *rsf = w.rsf;
-  const int ldl = w.ldl;
-  struct {
-    int kh;
-  } lay{w.kh};
-    double rr[KT], x[KT], y[KT], tau[KT];
-    bool pas[KT], dead[KT];
-    bool any = false;
+  const int ldl = w.ldl, kh = w.kh;
+  float rf[KT], xh[KT], xl[KT], yh[KT], yl[KT], tauf[KT];
+  bool pas[KT], dead[KT];
+  bool any = false;
 #pragma unroll
-    for (int t = 0; t < KT; ++t) {
-      const int j = lane + 32 * t;
-      const float rf = j < k ? R[row * k + j] : 0.f;
-      rr[t] = (double)rf;
-      if (j < k) {
-        rs[j] = rr[t];
-        rsf[j] = rf;
+  for (int t = 0; t < KT; ++t) {
+    const int j = lane + 32 * t;
+    rf[t] = j < k ? R[row * k + j] : 0.f;
+    if (j < k) rsf[j] = rf[t];
+    dead[t] = !(j < k && ((w.live[j >> 5] >> (j & 31)) & 1u));
+    pas[t] = warm && !dead[t] && X[row * k + j] > 0.f;
+    any |= pas[t];
+    xh[t] = xl[t] = 0.f;
+    yh[t] = -rf[t];
+    yl[t] = 0.f;
+    tauf[t] = kBppYTolF * fabsf(rf[t]);
+  }
+  __syncwarp();
+  // z = G^{-1} r (a pair), shared by every exchange of this right-hand side
+  // that takes the Q route; formed on the first such exchange
+  float zh[KT], zl[KT];
+  bool have_z = false;
+  int alpha = 3, beta = k + 1, it = 0;
+  bool failed_numeric = false, failed_cap = false;
+  bool need_solve = __any_sync(0xffffffffu, any);
+  for (;;) {
+    if (need_solve) {
+      // ---- passive / active lists and each lane's positions in them
+      int nf = 0, nb = 0, posf[KT], posb[KT];
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        const unsigned pf = __ballot_sync(0xffffffffu, pas[t] && j < k);
+        const unsigned pb = __ballot_sync(0xffffffffu, !pas[t] && j < k);
+        posf[t] = nf + __popc(pf & lt_mask);
+        posb[t] = nb + __popc(pb & lt_mask);
+        nf += __popc(pf);
+        nb += __popc(pb);
       }
-      dead[t] = !(j < k && G[j * k + j] > w.dead_below);
-      pas[t] = warm && !dead[t] && X[row * k + j] > 0.f;
-      any |= pas[t];
-      x[t] = 0.0;
-      y[t] = -rr[t];
-      tau[t] = kBppYTol * fabs(rr[t]);
-    }
-    __syncwarp();
-    // z = G^{-1} r, shared by every exchange of this right-hand side that
-    // takes the Q route; formed on the first such exchange (k^2 FP64 FMAs,
-    // as many as a k/2-sized factorisation)
-    double z[KT];
-    bool have_z = false;
-    int alpha = 3, beta = k + 1, it = 0;
-    bool failed_numeric = false, failed_cap = false;
-    bool need_solve = __any_sync(0xffffffffu, any);
-    for (;;) {
-      if (need_solve) {
-        // ---- passive / active lists and each lane's positions in them
-        int nf = 0, nb = 0, posf[KT], posb[KT];
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int j = lane + 32 * t;
+        if (j < k) {
+          if (pas[t]) Fl[posf[t]] = j; else Bl[posb[t]] = j;
+        }
+      }
+      __syncwarp();
+      const bool direct = nf <= nb || !have_q;
+      if (direct) {
+        // ---- direct: G_FF x_F = r_F; (vh, vl)[0..nf) end as x_F in F order
+        if (nf > kh) { failed_numeric = true; break; }
+#pragma unroll
+        for (int t = 0; t < KT; ++t)
+          if (pas[t]) {
+            bh[posf[t]] = rf[t];
+            bl[posf[t]] = 0.f;
+          }
+        __syncwarp();
+        if (!solve_mixed(Gh, Gl, k, Fl, nf, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
+          __syncwarp();
+          if (!warp_cholesky(Gat, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
+#pragma unroll
+          for (int t = 0; t < KT; ++t)
+            if (pas[t]) v[posf[t]] = (double)rf[t];
+          __syncwarp();
+          warp_chol_solve(L, ldl, nf, v, lane);
+          split_pair(v, nf, vh, vl, lane);
+        }
+        __syncwarp();
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
-          const int j = lane + 32 * t;
-          const unsigned pf = __ballot_sync(0xffffffffu, pas[t] && j < k);
-          const unsigned pb = __ballot_sync(0xffffffffu, !pas[t] && j < k);
-          posf[t] = nf + __popc(pf & lt_mask);
-          posb[t] = nb + __popc(pb & lt_mask);
-          nf += __popc(pf);
-          nb += __popc(pb);
+          xh[t] = pas[t] ? vh[posf[t]] : 0.f;
+          xl[t] = pas[t] ? vl[posf[t]] : 0.f;
+        }
+      } else {
+        // ---- through Q = G^{-1} and z = Q r: the constrained solution has
+        // Q_BB y_B = -z_B and x_F = z_F + Q_FB y_B (y_F = 0, x_B = 0)
+        if (!have_z) {
+#pragma unroll
+          for (int t = 0; t < KT; ++t) {
+            // z_j = sum_l (Qh + Ql)_lj r_l, r_l an FP32 value
+            const int j = lane + 32 * t;
+            float hi = 0.f, lo = 0.f;
+            if (j < k)
+              for (int l = 0; l < k; ++l) {
+                const float rl = rsf[l];
+                two_fma_acc(Qh[l * k + j], rl, hi, lo);
+                lo = fmaf(Ql[l * k + j], rl, lo);
+              }
+            zh[t] = __fadd_rn(hi, lo);
+            zl[t] = __fsub_rn(lo, __fsub_rn(zh[t], hi));
+          }
+          have_z = true;
         }
 #pragma unroll
+        for (int t = 0; t < KT; ++t)
+          if (!pas[t] && lane + 32 * t < k) {
+            bh[posb[t]] = zh[t];
+            bl[posb[t]] = zl[t];
+          }
+        __syncwarp();
+        // (vh, vl)[0..nb) = Q_BB^{-1} z_B = -y_B
+        if (!solve_mixed(Qh, Ql, k, Bl, nb, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
+          __syncwarp();
+          if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
+#pragma unroll
+          for (int t = 0; t < KT; ++t)
+            if (!pas[t] && lane + 32 * t < k) v[posb[t]] = (double)zh[t] + (double)zl[t];
+          __syncwarp();
+          warp_chol_solve(L, ldl, nb, v, lane);
+          split_pair(v, nb, vh, vl, lane);
+        }
+        __syncwarp();
+#pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int j = lane + 32 * t;
-          if (j < k) {
-            if (pas[t]) Fl[posf[t]] = j; else Bl[posb[t]] = j;
+          xh[t] = xl[t] = 0.f;
+          if (j < k && pas[t]) {
+            float h, l;
+            pair_dot(Qh, Ql, k, Bl, nb, j, vh, vl, h, l);
+            xh[t] = zh[t];
+            xl[t] = zl[t];
+            pair_add(xh[t], xl[t], -h, -l);
+          }
+          if (j < k && !pas[t]) {
+            yh[t] = -vh[posb[t]];
+            yl[t] = -vl[posb[t]];
           }
         }
         __syncwarp();
-        if (nf <= nb || !have_q) {
-          // ---- direct: G_FF x_F = r_F; v[0..nf) ends as x_F in F order
-          if (nf > lay.kh) { failed_numeric = true; break; }
-          if (!warp_cholesky(Gat, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
-          for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
-          __syncwarp();
-          warp_chol_solve(L, ldl, nf, v, lane);
+        // x_F in F order for the tolerance scales (and the refinement)
 #pragma unroll
-          for (int t = 0; t < KT; ++t) x[t] = pas[t] ? v[posf[t]] : 0.0;
-        } else {
-          // ---- through Q = G^{-1} and z = Q r: the constrained solution has
-          // Q_BB y_B = -z_B and x_F = z_F + Q_FB y_B (y_F = 0, x_B = 0)
-          if (!have_z) {
+        for (int t = 0; t < KT; ++t)
+          if (pas[t]) {
+            vh[posf[t]] = xh[t];
+            vl[posf[t]] = xl[t];
+          }
+        __syncwarp();
+        if (w.refine) {
+          // one step of iterative refinement of the route through Q: the
+          // passive system's residual rho_F = r_F - G_FF x_F, its correction
+          // through the same route (z' = Q [rho_F; 0], rho rounded to FP32:
+          // a correction needs no more), and y_B = G_BF x_F - r_B formed
+          // directly; the error of the route drops from ~cond u to ~(cond
+          // u)^2.  The sums with G take its FP32 pair: ~2^-44 of the terms,
+          // on a par with the ~1e-14 to which G itself is formed.  r in FP32
+          // (rsf) is no longer needed: z is formed, and a direct solve takes
+          // r from the lanes' registers.
 #pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              // z_j = sum_l (Qh + Ql)_lj r_l: each Qh r product exact (two
-              // FP32 numbers), summed in an FP32 pair with the rounding errors
-              // kept; r_l is an FP32 value.  ~10 FP32 operations per term,
-              // where one FP64 FMA costs the FP64 pipe ~60x as much.
-              const int j = lane + 32 * t;
-              float hi = 0.f, lo = 0.f;
-              if (j < k)
-                for (int l = 0; l < k; ++l) {
-                  const float rl = rsf[l];
-                  two_fma_acc(Qh[l * k + j], rl, hi, lo);
-                  lo = fmaf(Ql[l * k + j], rl, lo);
-                }
-              z[t] = (double)hi + (double)lo;
+          for (int t = 0; t < KT; ++t) {
+            const int j = lane + 32 * t;
+            float rho = 0.f;
+            if (j < k && pas[t]) {
+              float h, l, rh = rf[t], rl = 0.f;
+              pair_dot(Gh, Gl, k, Fl, nf, j, vh, vl, h, l);
+              pair_add(rh, rl, -h, -l);
+              rho = __fadd_rn(rh, rl);
             }
-            have_z = true;
+            if (j < k) rsf[j] = rho;
           }
+          __syncwarp();
+          float zrh[KT], zrl[KT];
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
-            if (j < k && !pas[t]) v[posb[t]] = z[t];
+            float hi = 0.f, lo = 0.f;
+            if (j < k)
+              for (int l = 0; l < k; ++l) {
+                const float rl = rsf[l];
+                two_fma_acc(Qh[l * k + j], rl, hi, lo);
+                lo = fmaf(Ql[l * k + j], rl, lo);
+              }
+            zrh[t] = __fadd_rn(hi, lo);
+            zrl[t] = __fsub_rn(lo, __fsub_rn(zrh[t], hi));
           }
+#pragma unroll
+          for (int t = 0; t < KT; ++t)
+            if (!pas[t] && lane + 32 * t < k) {
+              bh[posb[t]] = zrh[t];
+              bl[posb[t]] = zrl[t];
+            }
           __syncwarp();
-          if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
-          warp_chol_solve(L, ldl, nb, v, lane);  // v = Q_BB^{-1} z_B = -y_B
-          split_pair(v, nb, w.vh, w.vl, lane);
+          if (!solve_mixed(Qh, Ql, k, Bl, nb, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
+            __syncwarp();
+            if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
+#pragma unroll
+            for (int t = 0; t < KT; ++t)
+              if (!pas[t] && lane + 32 * t < k) v[posb[t]] = (double)zrh[t] + (double)zrl[t];
+            __syncwarp();
+            warp_chol_solve(L, ldl, nb, v, lane);
+            split_pair(v, nb, vh, vl, lane);
+          }
           __syncwarp();
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
-            double s = z[t];
-            if (j < k && pas[t]) s -= q_dot_pair(Qh, Ql, k, Bl, nb, j, w.vh, w.vl);
-            x[t] = (j < k && pas[t]) ? s : 0.0;
-            if (j < k && !pas[t]) y[t] = -v[posb[t]];
+            if (j < k && pas[t]) {
+              float h, l, ch = zrh[t], cl = zrl[t];
+              pair_dot(Qh, Ql, k, Bl, nb, j, vh, vl, h, l);
+              pair_add(ch, cl, -h, -l);
+              pair_add(xh[t], xl[t], ch, cl);
+            }
           }
           __syncwarp();
 #pragma unroll
           for (int t = 0; t < KT; ++t)
-            if (pas[t]) v[posf[t]] = x[t];  // x_F in F order for the tolerance scales
-          if (w.refine) {
-            // one step of iterative refinement: the passive system's residual
-            // rho_F = r_F - G_FF x_F, its correction through the same Q route
-            // (z' = Q [rho_F; 0] from the FP32 pair of Q, rho rounded to FP32:
-            // a correction needs no more), and y_B = G_BF x_F - r_B formed
-            // directly; the error of the route drops from ~cond u to
-            // ~(cond u)^2.  The sums with G take its FP32 pair and x_F split
-            // in two: ~2^-44 of the terms, on a par with the ~1e-14 to which
-            // G itself is formed.  r in FP32 is no longer needed (z is formed).
-            __syncwarp();
-            split_pair(v, nf, w.vh, w.vl, lane);
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              const int j = lane + 32 * t;
-              double rho = 0.0;
-              if (j < k && pas[t]) rho = rr[t] - q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl);
-              if (j < k) rsf[j] = (float)rho;
+            if (pas[t]) {
+              vh[posf[t]] = xh[t];
+              vl[posf[t]] = xl[t];
             }
-            __syncwarp();
-            double zr[KT];
-#pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              const int j = lane + 32 * t;
-              float hi = 0.f, lo = 0.f;
-              if (j < k)
-                for (int l = 0; l < k; ++l) {
-                  const float rl = rsf[l];
-                  two_fma_acc(Qh[l * k + j], rl, hi, lo);
-                  lo = fmaf(Ql[l * k + j], rl, lo);
-                }
-              zr[t] = (double)hi + (double)lo;
-            }
-#pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              const int j = lane + 32 * t;
-              if (j < k && !pas[t]) v[posb[t]] = zr[t];
-            }
-            __syncwarp();
-            warp_chol_solve(L, ldl, nb, v, lane);
-            split_pair(v, nb, w.vh, w.vl, lane);
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              const int j = lane + 32 * t;
-              if (j < k && pas[t]) x[t] += zr[t] - q_dot_pair(Qh, Ql, k, Bl, nb, j, w.vh, w.vl);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < KT; ++t)
-              if (pas[t]) v[posf[t]] = x[t];
-            __syncwarp();
-            split_pair(v, nf, w.vh, w.vl, lane);
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < KT; ++t) {
-              const int j = lane + 32 * t;
-              if (j < k && !pas[t]) y[t] = q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl) - rr[t];
-            }
-          }
-        }
-        __syncwarp();
-        for (int a = lane; a < nf; a += 32) xa[a] = fabsf((float)v[a]);
-        __syncwarp();
-        // ---- active set: y = G_BF x_F - r_B (direct route; the Q route has
-        // it already), from the FP32 pairs of G and x_F like z (its error,
-        // ~2^-44 of the scale below, is far under the 1e-11 tolerance), and
-        // the tolerance scale |r_j| + sum |G_jF x_F| in FP32
-        const bool direct = nf <= nb || !have_q;
-        if (direct) {
-          split_pair(v, nf, w.vh, w.vl, lane);
           __syncwarp();
-        }
 #pragma unroll
-        for (int t = 0; t < KT; ++t) {
-          const int j = lane + 32 * t;
-          if (j >= k) continue;
-          if (pas[t]) {
-            y[t] = 0.0;
-            tau[t] = 0.0;
-          } else {
-            float mag = fabsf((float)rr[t]);
-            for (int a = 0; a < nf; ++a) mag = fmaf(fabsf(Gh[Fl[a] * k + j]), xa[a], mag);
-            tau[t] = kBppYTol * (double)mag;
-            if (direct) y[t] = q_dot_pair(Gh, Gl, k, Fl, nf, j, w.vh, w.vl) - rr[t];
+          for (int t = 0; t < KT; ++t) {
+            const int j = lane + 32 * t;
+            if (j < k && !pas[t]) {
+              float h, l;
+              pair_dot(Gh, Gl, k, Fl, nf, j, vh, vl, h, l);
+              yh[t] = h;
+              yl[t] = l;
+              pair_add(yh[t], yl[t], -rf[t], 0.f);
+            }
           }
         }
-        __syncwarp();
       }
-      // ---- infeasible set and exchange
-      bool inf[KT];
-      unsigned bal[KT];
-      int nv = 0;
+      // ---- active set: y = G_BF x_F - r_B (direct route; the Q route has
+      // it already) and the tolerance scale |r_j| + sum |G_jF x_F|, in FP32
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (pas[t]) xa[posf[t]] = fabsf(__fadd_rn(xh[t], xl[t]));
+      __syncwarp();
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
         const int j = lane + 32 * t;
-        inf[t] = j < k && (pas[t] ? (x[t] < 0.0) : (!dead[t] && y[t] < -tau[t]));
-        bal[t] = __ballot_sync(0xffffffffu, inf[t]);
-        nv += __popc(bal[t]);
+        if (j >= k) continue;
+        if (pas[t]) {
+          yh[t] = yl[t] = 0.f;
+          tauf[t] = 0.f;
+        } else {
+          float mag = fabsf(rf[t]);
+          for (int a = 0; a < nf; ++a) mag = fmaf(fabsf(Gh[Fl[a] * k + j]), xa[a], mag);
+          tauf[t] = kBppYTolF * mag;
+          if (direct) {
+            float h, l;
+            pair_dot(Gh, Gl, k, Fl, nf, j, vh, vl, h, l);
+            yh[t] = h;
+            yl[t] = l;
+            pair_add(yh[t], yl[t], -rf[t], 0.f);
+          }
+        }
       }
-      if (nv == 0) break;
-      if (it >= max_piv) { failed_cap = true; break; }
-      ++it;
-      if (nv < beta || alpha >= 1) {
-        if (nv < beta) { beta = nv; alpha = 3; } else { alpha -= 1; }
-#pragma unroll
-        for (int t = 0; t < KT; ++t)
-          if (inf[t]) pas[t] = !pas[t];
-      } else {
-        int vmax = -1;
-#pragma unroll
-        for (int t = KT - 1; t >= 0; --t)
-          if (vmax < 0 && bal[t]) vmax = 32 * t + 31 - __clz(bal[t]);
-#pragma unroll
-        for (int t = 0; t < KT; ++t)
-          if (lane + 32 * t == vmax) pas[t] = !pas[t];
-      }
-      need_solve = true;
+      __syncwarp();
     }
-    // a row handed to the fallback keeps its previous iterate, whose support
-    // the fallback starts from
-    if (!failed_numeric) {
+    // ---- infeasible set and exchange
+    bool inf[KT];
+    unsigned bal[KT];
+    int nv = 0;
 #pragma unroll
-      for (int t = 0; t < KT; ++t) {
-        const int j = lane + 32 * t;
-        if (j < k) X[row * k + j] = (float)x[t];
-      }
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      const bool xneg = xh[t] < 0.f || (xh[t] == 0.f && xl[t] < 0.f);
+      inf[t] = j < k && (pas[t] ? xneg : (!dead[t] && __fadd_rn(yh[t], yl[t]) < -tauf[t]));
+      bal[t] = __ballot_sync(0xffffffffu, inf[t]);
+      nv += __popc(bal[t]);
     }
-    *failed_numeric_out = failed_numeric;
-    *failed_cap_out = failed_cap;
-    return it;
+    if (nv == 0) break;
+    if (it >= max_piv) { failed_cap = true; break; }
+    ++it;
+    if (nv < beta || alpha >= 1) {
+      if (nv < beta) { beta = nv; alpha = 3; } else { alpha -= 1; }
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (inf[t]) pas[t] = !pas[t];
+    } else {
+      int vmax = -1;
+#pragma unroll
+      for (int t = KT - 1; t >= 0; --t)
+        if (vmax < 0 && bal[t]) vmax = 32 * t + 31 - __clz(bal[t]);
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+        if (lane + 32 * t == vmax) pas[t] = !pas[t];
+    }
+    need_solve = true;
+  }
+  // a row handed to the fallback keeps its previous iterate, whose support
+  // the fallback starts from
+  if (!failed_numeric) {
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) X[row * k + j] = __fadd_rn(xh[t], xl[t]);
+    }
+  }
+  *failed_numeric_out = failed_numeric;
+  *failed_cap_out = failed_cap;
+  return it;
 }
 
 // Fallback for the rows the fast kernel flagged (a non-positive pivot in a
