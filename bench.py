@@ -34,6 +34,9 @@ WORKLOADS = {
     "batched": {"m": 8000, "n": 8000, "k": 64, "count": 256},
     # the dense matrix factorised at ranks from 10 to 512 (Sec. 6.3's sweep of k,
     # carried past the rank where the products leave the HBM roof)
+    # power-law sparse matrix at the size of webbase-2001 (Sec. 6, the paper's
+    # largest sparse input), which is not available: synthetic stand-in
+    "webbase": {"m": 118_142_155, "n": 118_142_155, "k": 50, "nnz": 1_019_903_190},
     "ksweep": {"m": M_FULL, "n": N_FULL, "k": 512, "rank": RANK_FULL,
                "ks": [10, 20, 30, 40, 50, 64, 100, 128, 192, 256, 320, 384, 448, 512]},
 }
@@ -262,7 +265,12 @@ def run_reference(args):
 def config_dict(args):
     m, n = getattr(args, "m", M_FULL), getattr(args, "n", N_FULL)
     wl = getattr(args, "workload", "dense")
-    if wl == "sparse":
+    if wl == "webbase":
+        desc = (f"sparse CSR {m}x{n}, {args.nnz:,} nonzeros drawn with power-law row and column "
+                f"degrees (stand-in for webbase-2001), values U(0,1], k={args.k}, "
+                f"{args.algo.upper()}, FP32 SpMM")
+        size = f"{8 * args.nnz / 1e9:.1f} GB of CSR values and indices"
+    elif wl == "sparse":
         desc = (f"sparse CSR {m}x{n}, density {args.density:g} at uniform positions, values "
                 f"U(0,1], k={args.k}, {args.algo.upper()}, FP32 SpMM")
         size = f"{8 * m * n * args.density / 1e9:.2f} GB of CSR values and indices"
@@ -449,9 +457,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     m, n, k = args.m, args.n, args.k
-    sparse = args.workload == "sparse"
+    sparse = args.workload in ("sparse", "webbase")
+    if args.workload == "webbase":
+        csr = synth.sparse_powerlaw_torch(m, n, args.nnz, seed=SEED + rank, device=dev)
+        torch.cuda.empty_cache()
     if sparse:
-        csr = synth.sparse_uniform_torch(m, n, args.density, seed=SEED + rank, device=dev)
+        if args.workload == "sparse":
+            csr = synth.sparse_uniform_torch(m, n, args.density, seed=SEED + rank, device=dev)
         A = aunmf.csr_matrix(*csr, (m, n))
         nnz = int(csr[2].numel())
     else:
@@ -610,6 +622,7 @@ def main():
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--m", type=int, default=None, help="rows of A (profiling cases)")
     ap.add_argument("--n", type=int, default=None, help="columns of A (profiling cases)")
+    ap.add_argument("--nnz", type=int, default=None, help="nonzeros of the power-law case")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
@@ -623,7 +636,8 @@ def main():
     args.k = args.k or wl["k"]
     args.rank = wl.get("rank", RANK_FULL)
     args.density = wl.get("density", 0.0)
-    if args.workload == "sparse":
+    args.nnz = args.nnz or wl.get("nnz", 0)
+    if args.workload in ("sparse", "webbase"):
         args.prec = "fp32"
     if args.impl == "reference":
         return run_reference(args)

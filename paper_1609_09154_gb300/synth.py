@@ -121,3 +121,58 @@ def sparse_uniform_torch(m: int, n: int, density: float, seed: int, device):
     torch.cumsum(counts, 0, out=rowptr[1:])
     val = 1.0 - torch.rand(key.shape[0], generator=g, device=device, dtype=torch.float32)
     return rowptr, cols.contiguous(), val
+
+
+def _powerlaw_ranks(count: int, size: int, a: float, g, device):
+    """`count` ranks in [0, size) with P(rank = i) ~ (i + 1)^-a (0 < a < 1),
+    by inverse-transform sampling of the continuous density."""
+    import torch
+
+    u = torch.rand(count, generator=g, device=device, dtype=torch.float64)
+    top = (size + 1.0) ** (1.0 - a) - 1.0
+    x = torch.pow(1.0 + u * top, 1.0 / (1.0 - a)) - 1.0
+    return torch.clamp(x.to(torch.int64), max=size - 1)
+
+
+def _spread(rank, size: int, mult: int):
+    """A bijection of [0, size) (multiplication by a number coprime to size),
+    so that the high-degree ranks land at scattered indices."""
+    return (rank * mult) % size
+
+
+def _coprime(size: int, start: int) -> int:
+    import math
+
+    c = start
+    while math.gcd(c, size) != 1:
+        c += 1
+    return c
+
+
+def sparse_powerlaw_torch(m: int, n: int, nnz: int, seed: int, device, a_rows: float = 0.5,
+                          a_cols: float = 0.7):
+    """CSR on ``device`` with power-law row and column degrees (a stand-in for
+    a web graph such as webbase-2001): `nnz` (row, column) pairs drawn with
+    independent power-law ranks (row rank i with probability ~ (i+1)^-a_rows,
+    column ranks with a_cols), the ranks spread over the indices by a fixed
+    bijection, repeated positions dropped; values uniform on (0, 1].  Returns
+    (rowptr int64, colidx int32, val float32)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rows = _spread(_powerlaw_ranks(nnz, m, a_rows, g, device), m, _coprime(m, 2654435761 % m or 1))
+    cols = _spread(_powerlaw_ranks(nnz, n, a_cols, g, device), n, _coprime(n, 40503 * 65537 % n or 1))
+    key = rows * n + cols
+    del rows, cols
+    key = torch.unique(key)  # sorted by (row, col)
+    rows = key // n
+    colidx = (key % n).to(torch.int32)
+    del key
+    counts = torch.bincount(rows, minlength=m)
+    del rows
+    rowptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=rowptr[1:])
+    val = 1.0 - torch.rand(colidx.shape[0], generator=g, device=device, dtype=torch.float32)
+    return rowptr, colidx.contiguous(), val
+

@@ -107,3 +107,47 @@ def test_sparse_run_deterministic(ax):
     W1, H1, r1, _ = ax.run(M, k, "hals", 10, dev(W0), dev(H0))
     W2, H2, r2, _ = ax.run(M, k, "hals", 10, dev(W0), dev(H0))
     assert torch.equal(W1, W2) and torch.equal(H1, H2) and np.array_equal(r1, r2)
+
+
+def powerlaw_problem(m, n, nnz, k, seed):
+    """Power-law row and column degrees (hub columns with thousands of
+    entries next to empty ones), from the same generator as the large sparse
+    benchmark, on the CPU."""
+    rp, ci, v = synth.sparse_powerlaw_torch(m, n, nnz, seed=seed, device="cpu")
+    csr = (rp.numpy().astype(np.int64), ci.numpy().astype(np.int32),
+           v.numpy().astype(np.float32).astype(np.float64))
+    W0, H0 = synth.init_factors(m, n, k, seed=seed)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    return csr, r32(W0), r32(H0)
+
+
+@pytest.mark.parametrize("m,n,nnz,k", [(20000, 15000, 200000, 50), (3000, 50000, 150000, 17)])
+def test_sparse_powerlaw_products(ax, m, n, nnz, k):
+    """Both products on skewed degrees: W^T A goes through the CSC copy, whose
+    columns (a radix sort by column of the CSR order) must list their rows in
+    ascending order for the sums to come out as the oracle's."""
+    csr, W, H = powerlaw_problem(m, n, nnz, k, seed=m + nnz)
+    assert np.bincount(csr[1], minlength=n).max() > 50 * csr[1].size / n  # a hub column
+    M, keep = dev_csr(csr, (m, n))
+    S = sp.csr_matrix((csr[2], csr[1], csr[0]), shape=(m, n))
+    Mo = orc.Matrix(csr=csr, shape=(m, n))
+    PW = host(ax.aht(M, dev(H)))
+    PH = host(ax.wta(M, dev(W)))
+    absS = abs(S)
+    nz_row = np.diff(csr[0]).max()
+    nz_col = np.bincount(csr[1], minlength=n).max()
+    tol_w = 2 * max(nz_row, 1) * U32 * (absS @ np.abs(H).T) + 1e-30
+    tol_h = 2 * max(nz_col, 1) * U32 * (np.abs(W).T @ absS) + 1e-30
+    assert (np.abs(PW - orc.aht(Mo, H)) <= tol_w).all()
+    assert (np.abs(PH - orc.wta(Mo, W)) <= tol_h).all()
+
+
+@pytest.mark.parametrize("algo", ["mu", "hals"])
+def test_sparse_powerlaw_run_matches_oracle(ax, algo):
+    m, n, k = 20000, 15000, 20
+    csr, W0, H0 = powerlaw_problem(m, n, 200000, k, seed=91)
+    M, keep = dev_csr(csr, (m, n))
+    ref = orc.nmf_run(orc.Matrix(csr=csr, shape=(m, n)), k, algo, 20, W0, H0)
+    assert ref["rc"] == 0
+    W, H, rel, info = ax.run(M, k, algo, 20, dev(W0), dev(H0))
+    assert np.all(np.abs(rel - ref["relres"]) <= 1e-6), np.abs(rel - ref["relres"]).max()
