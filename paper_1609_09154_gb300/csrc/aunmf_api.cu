@@ -50,6 +50,7 @@ struct aunmf_handle {
   std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> bpp_tuned;
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   Buf aux;         // printed HALS sweep / projected gradient: partials, barrier, values
+  Buf spl, splpart;  // sparse: long-row lists of the CSR and the CSC; their chunk partials
   int max_gram_blocks = 4 * 152;
   int n_dparts = 2 * 152;
 };
@@ -132,10 +133,11 @@ struct RunCtx {
   float *parts;
   float *tcacc;  // k > 64: the products' per-CTA partial sums (null: added into parts)
   int *err;
-  // sparse path: CSC form of A
+  // sparse path: CSC form of A; the long rows of the CSR and the CSC
   const int64_t *colptr;
   const int32_t *rowidx;
   const float *cval;
+  SpLongRows csr_long, csc_long;
   bool profile;
   int hals_variant;     // 1: Eq. halsupdate as printed
   bool track_pg;        // form the projected gradient each iteration
@@ -182,7 +184,7 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   (void)h;
   if (!A->dense) {
     PhaseTimer t(c, s, kPhAht);
-    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, s);
+    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, &c.csr_long, s);
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhAht);
@@ -216,7 +218,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   (void)h;
   if (!A->dense) {
     PhaseTimer t(c, s, kPhWta);
-    return launch_wta_csc(c.colptr, c.rowidx, c.cval, A->n, c.W, c.k, c.PHt, s);
+    return launch_wta_csc(c.colptr, c.rowidx, c.cval, A->n, c.W, c.k, c.PHt, &c.csc_long, s);
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhWta);
@@ -406,6 +408,22 @@ int prepare_sparse(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   c.colptr = P<int64_t>(h->colptr);
   c.rowidx = P<int32_t>(h->rowidx);
   c.cval = P<float>(h->cval);
+  // rows of either form long enough to be split over several warps
+  const int64_t cap = long_rows_capacity(A->nnz);
+  ENS_TC(h, h->spl, sizeof(int64_t) * (size_t)(4 * cap + 2) + 2 * sizeof(unsigned long long));
+  int64_t *L = P<int64_t>(h->spl);
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(L + 4 * cap + 2);
+  e = find_long_rows(A->rowptr, A->m, A->nnz, L, L + cap, cnt, &c.csr_long, s);
+  if (e == cudaSuccess)
+    e = find_long_rows(c.colptr, A->n, A->nnz, L + 2 * cap + 1, L + 3 * cap + 1, cnt + 1,
+                       &c.csc_long, s);
+  if (e != cudaSuccess) return fail_cuda(h, e, "find_long_rows");
+  const int64_t parts = c.csr_long.nchunks + c.csc_long.nchunks;
+  if (parts > 0) {
+    ENS_TC(h, h->splpart, sizeof(float) * (size_t)parts * c.k);
+    c.csr_long.part = P<float>(h->splpart);
+    c.csc_long.part = c.csr_long.part + (size_t)c.csr_long.nchunks * c.k;
+  }
   return AUNMF_OK;
 }
 
@@ -457,7 +475,7 @@ int aunmf_destroy(aunmf_handle *h) {
   cudaStreamSynchronize(h->stream);
   Buf *bufs[] = {&h->Ht, &h->PW, &h->PHt, &h->GH, &h->GW, &h->G64, &h->gpart, &h->dpart, &h->n2a,
                  &h->ctr, &h->relres, &h->last, &h->Ax, &h->At, &h->Hk, &h->Wt, &h->parts,
-                 &h->err, &h->tcacc, &h->aux, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
+                 &h->err, &h->tcacc, &h->aux, &h->spl, &h->splpart, &h->colptr, &h->rowidx, &h->cval, &h->cscratch, &h->bppq, &h->dHt,
                  &h->batch, &h->batch_meta, &h->hA, &h->hW, &h->hH};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
@@ -897,7 +915,7 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
     c.A = A;
     int rc = prepare_sparse(h, c, s);
     if (rc != AUNMF_OK) return rc;
-    CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, W, k, PHt, s));
+    CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, W, k, PHt, &c.csc_long, s));
   }
   CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
   CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s));

@@ -71,10 +71,30 @@ cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, c
 // Sparse products (FP32).  P_W (m x k) = A Ht from CSR; P_Ht (n x k) = A^T W
 // from the CSC form (colptr[n+1], rowidx[nnz], cval[nnz]) built by
 // launch_csr_to_csc (scratch: csc_scratch_bytes(n, nnz) bytes).
+// Rows (of the CSR, or of the CSC: columns of A) with more than kLongRowNz
+// nonzeros, which the products split into chunks over many warps: the sorted
+// row list, its chunk prefix, and chunk partial sums (nchunks x k floats);
+// nlong = 0: none (or lr == null).
+constexpr int64_t kLongRowNz = 4096;
+struct SpLongRows {
+  int64_t nlong = 0, nchunks = 0;
+  const int64_t *row = nullptr;
+  const int64_t *chunk0 = nullptr;
+  float *part = nullptr;
+};
 cudaError_t launch_aht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, const float *Ht, int k, float *P, cudaStream_t s);
+                           int64_t m, const float *Ht, int k, float *P, const SpLongRows *lr,
+                           cudaStream_t s);
 cudaError_t launch_wta_csc(const int64_t *colptr, const int32_t *rowidx, const float *cval,
-                           int64_t n, const float *W, int k, float *P, cudaStream_t s);
+                           int64_t n, const float *W, int k, float *P, const SpLongRows *lr,
+                           cudaStream_t s);
+// list: long_rows_capacity(nnz) int64; chunk0: capacity + 1 int64; count: one
+// counter.  Fills lr (its part stays null: the caller allocates nchunks x k
+// floats).  Synchronises the stream.
+int64_t long_rows_capacity(int64_t nnz);
+cudaError_t find_long_rows(const int64_t *ptr, int64_t rows, int64_t nnz, int64_t *list,
+                           int64_t *chunk0, unsigned long long *count, SpLongRows *lr,
+                           cudaStream_t s);
 size_t csc_scratch_bytes(int64_t n, int64_t nnz);
 cudaError_t launch_csr_to_csc(const int64_t *rowptr, const int32_t *colidx, const float *val,
                               int64_t m, int64_t n, int64_t nnz, int64_t *colptr, int32_t *rowidx,

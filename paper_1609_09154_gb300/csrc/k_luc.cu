@@ -354,6 +354,7 @@ cudaError_t launch_tpr_k(float *X, const float *P, const float *G, int64_t rows,
   if (k <= 16) return launch_tpr<16, OP>(X, P, G, rows, k, eps, gscale, out, s);
   if (k <= 32) return launch_tpr<32, OP>(X, P, G, rows, k, eps, gscale, out, s);
   if (k <= 48) return launch_tpr<48, OP>(X, P, G, rows, k, eps, gscale, out, s);
+  if (k <= 56) return launch_tpr<56, OP>(X, P, G, rows, k, eps, gscale, out, s);
   return launch_tpr<64, OP>(X, P, G, rows, k, eps, gscale, out, s);
 }
 

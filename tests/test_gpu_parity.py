@@ -58,7 +58,7 @@ def assert_product(got, ref, absprod, K, extra_rel=0.0):
 
 # shapes spanning several 128-row tiles with ragged tails, and k across the
 # 16 / 32 / 64-wide product tiles, the thread-per-row updates' padded widths
-# (16, 32, 48, 64 for k <= 64) and the warp-per-row updates above 64 (up to
+# (16, 32, 48, 56, 64 for k <= 64) and the warp-per-row updates above 64 (up to
 # 12 and 16 entries per lane at k = 300 and 512)
 SHAPES = [(300, 200, 10), (517, 389, 50), (129, 1031, 33), (64, 48, 1), (700, 260, 100),
           (257, 300, 24), (200, 150, 64), (600, 520, 300), (420, 380, 512)]

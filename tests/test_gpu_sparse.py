@@ -151,3 +151,34 @@ def test_sparse_powerlaw_run_matches_oracle(ax, algo):
     assert ref["rc"] == 0
     W, H, rel, info = ax.run(M, k, algo, 20, dev(W0), dev(H0))
     assert np.all(np.abs(rel - ref["relres"]) <= 1e-6), np.abs(rel - ref["relres"]).max()
+
+
+def test_sparse_long_rows_are_split(ax):
+    """A row of 7000 and a column of 9000 nonzeros, longer than the 4096 a
+    warp takes alone: both products split them into chunks over several warps
+    (partials added in chunk order).  Products entry by entry and a HALS run
+    against the oracle, and the run is repeatable bit for bit."""
+    m, n, k = 9000, 7000, 24
+    S = sp.random(m, n, density=0.002, format="lil", random_state=12, dtype=np.float64)
+    g = np.random.default_rng(12)
+    S[37, :] = g.random(n) + 0.01
+    S[:, 4242] = (g.random(m) + 0.01)[:, None]
+    S = S.tocsr()
+    S.sort_indices()
+    csr = (S.indptr.astype(np.int64), S.indices.astype(np.int32),
+           S.data.astype(np.float32).astype(np.float64))
+    W0, H0 = synth.init_factors(m, n, k, seed=12)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    W0, H0 = r32(W0), r32(H0)
+    M, keep = dev_csr(csr, (m, n))
+    Mo = orc.Matrix(csr=csr, shape=(m, n))
+    absS = abs(sp.csr_matrix((csr[2], csr[1], csr[0]), shape=(m, n)))
+    tol_w = 2 * n * U32 * (absS @ np.abs(H0).T) + 1e-30
+    tol_h = 2 * m * U32 * (np.abs(W0).T @ absS) + 1e-30
+    assert (np.abs(host(ax.aht(M, dev(H0))) - orc.aht(Mo, H0)) <= tol_w).all()
+    assert (np.abs(host(ax.wta(M, dev(W0))) - orc.wta(Mo, W0)) <= tol_h).all()
+    ref = orc.nmf_run(Mo, k, "hals", 10, W0, H0)
+    W1, H1, r1, _ = ax.run(M, k, "hals", 10, dev(W0), dev(H0))
+    W2, H2, r2, _ = ax.run(M, k, "hals", 10, dev(W0), dev(H0))
+    assert np.all(np.abs(r1 - ref["relres"]) <= 1e-6), np.abs(r1 - ref["relres"]).max()
+    assert torch.equal(W1, W2) and torch.equal(H1, H2) and np.array_equal(r1, r2)
