@@ -170,10 +170,9 @@ __global__ void __launch_bounds__(kLucThreads)
 
 // HALS normalisation (Eq. halsupdate, w^i / ||w^i||, compensated in H):
 // s_i = sqrt(GW_ii); X(:, i) /= s_i; Y(:, i) *= s_i; GW_ij /= s_i s_j.
-// The column of element e is e mod k, taken in 32-bit arithmetic when the
-// element count allows (a 64-bit remainder costs ~40 instructions and bound
-// the pass); the column scales are staged once per block.
-template <bool WIDE>
+// A warp per row, its lanes on the row's entries (no index division per
+// entry: a 64-bit remainder costs ~40 instructions and bound the pass at
+// 5.9e9 entries); the column scales are staged once per block.
 __global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
                                   const float *__restrict__ GW, bool divide) {
   __shared__ float sc[AUNMF_K_MAX];
@@ -184,11 +183,13 @@ __global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
     sc[i] = g > 0.f ? sqrtf(g) : 1.f;
   }
   __syncthreads();
-  const int64_t total = rows * k;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = WIDE ? (int)(e % k) : (int)((uint32_t)e % (uint32_t)k);
-    if (ok[i]) X[e] = divide ? X[e] / sc[i] : X[e] * sc[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += ws) {
+    float *x = X + r * k;
+    for (int i = lane; i < k; i += 32)
+      if (ok[i]) x[i] = divide ? x[i] / sc[i] : x[i] * sc[i];
   }
 }
 
@@ -340,9 +341,19 @@ cudaError_t launch_tpr(float *X, const float *P, const float *G, int64_t rows, i
                        const float *gscale, float *out, cudaStream_t s) {
   const size_t smem = sizeof(float) * ((size_t)KP * KP + (size_t)kTprWarps * 32 * (KP + 1));
   cudaFuncSetAttribute(k_luc_tpr<KP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one wave of resident blocks (a second, partial wave would leave most
+  // SMs idle for its whole length), each walking its share of row groups
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_luc_tpr<KP, OP>, kTprThreads, smem);
+    resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 152);
+  }
   const int64_t groups = (rows + 31) / 32;
   int64_t nb = (groups + kTprWarps - 1) / kTprWarps;
-  if (nb > 152 * 4) nb = 152 * 4;
+  if (nb > resident) nb = resident;
   k_luc_tpr<KP, OP><<<(unsigned)nb, kTprThreads, smem, s>>>(X, P, G, rows, k, eps, gscale, out);
   g_launches += 1;
   return cudaGetLastError();
@@ -648,10 +659,7 @@ cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t ro
     return (int)(b < 1 ? 1 : b);
   };
   auto scale = [&](float *Z, int64_t rows, bool divide) {
-    if (rows * k + 256LL * 152 * 16 < 0xFFFFFFFFLL)
-      k_hals_scale_rows<false><<<nb(rows * k), 256, 0, s>>>(Z, rows, k, GW, divide);
-    else
-      k_hals_scale_rows<true><<<nb(rows * k), 256, 0, s>>>(Z, rows, k, GW, divide);
+    k_hals_scale_rows<<<nb(rows * 32), 256, 0, s>>>(Z, rows, k, GW, divide);
   };
   if (rows_x > 0) scale(X, rows_x, true);
   if (Y && rows_y > 0) scale(Y, rows_y, false);
