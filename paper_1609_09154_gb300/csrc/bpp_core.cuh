@@ -38,22 +38,25 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Shared memory of the fast kernel: Q = G^{-1} and G as FP32 pairs (k^2
+// doubles each), then per warp: the FP32 Cholesky factor L (kh x ldl floats),
+// a right-hand-side pair (2k floats), corrections (k floats), the index lists
+// (2k ints), |x_F|, r, and a solution pair (k floats each).  Nothing is FP64:
+// a row whose FP32 solve cannot finish goes to the FP64 fallback kernel.
 struct BppLayout {
-  int kh;          // largest factorisation: floor(k / 2)
-  int ldl;         // leading dimension of L (odd)
-  size_t g_dbl;    // doubles for G and for Q (each)
-  size_t gf_dbl;   // doubles holding G as an FP32 pair (hi k^2, lo k^2)
-  size_t warp_dbl; // doubles per warp: L, v (k), r (k), index lists (2k ints), |x_F| FP32 (k),
-                   // r in FP32 (k), v split into two FP32 halves (2k)
+  int kh;            // largest factorisation: floor(k / 2)
+  int ldl;           // leading dimension of L (odd)
+  size_t shared_dbl; // doubles shared by the block (the two pairs)
+  size_t warp_dbl;   // doubles per warp
 };
 
 __host__ __device__ inline BppLayout bpp_layout(int k) {
   BppLayout l;
   l.kh = k / 2 > 0 ? k / 2 : 1;
   l.ldl = l.kh | 1;
-  l.g_dbl = (size_t)k * k;
-  l.gf_dbl = (size_t)k * k;
-  l.warp_dbl = (size_t)l.kh * l.ldl + 2 * (size_t)k + (size_t)k + 4 * (((size_t)k + 1) / 2);
+  l.shared_dbl = 2 * (size_t)k * k;
+  const size_t kf = 2 * (((size_t)k + 1) / 2);  // k floats, rounded up to whole doubles
+  l.warp_dbl = ((size_t)l.kh * l.ldl + 1) / 2 + kf + kf / 2 + (size_t)k + 4 * (kf / 2);
   return l;
 }
 
@@ -279,34 +282,32 @@ __device__ __forceinline__ double q_dot_pair(const float *Qh, const float *Ql, i
 
 // Shared-memory view of one warp's BPP state (fast kernel).
 struct BppWarp {
-  const double *G;
   const float *Qh, *Ql;  // G^{-1} = Qh + Ql (FP32 pair)
   const float *Gh, *Gl;  // G = Gh + Gl (to ~2^-48); |Gh| scales the tolerances
   double dead_below;  // kDead * max diagonal of G
   unsigned live[2];    // bit j % 32 of live[j / 32]: G_jj > dead_below (k <= 64)
   bool have_q;
   bool refine;  // solves through G^{-1} take a refinement step
-  double *L, *v, *rs;
+  float *Lf;       // FP32 Cholesky factor (kh x ldl)
+  float *bh, *bl;  // right-hand side pair (k each)
+  float *dv;       // corrections (k)
   int *Fl, *Bl;
   float *xa;
   float *rsf;  // r in FP32, by index
-  float *vh, *vl;  // v = vh + vl (to ~2^-48), for products with the FP32 pair of Q
+  float *vh, *vl;  // solution pairs: x_F in F order or Q_BB^{-1} z_B in B order
   int ldl, kh;
 };
 
-// Stage G (FP64 and as an FP32 pair) and Q (FP32 pair) of one problem into
-// shared memory (block-wide; the caller synchronises) and return warp wib's
-// view.
+// Stage Q and G (FP32 pairs) of one problem into shared memory (block-wide;
+// the caller synchronises) and return warp wib's view.
 __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
                                              const float *__restrict__ Qsg, const int *q_ok, int k,
                                              double *sm, int wib) {
   const BppLayout lay = bpp_layout(k);
-  double *G = sm;
-  float *Qs = reinterpret_cast<float *>(sm + lay.g_dbl);  // hi (k^2), lo (k^2)
-  float *Gp = reinterpret_cast<float *>(sm + 2 * lay.g_dbl);  // hi (k^2), lo (k^2)
+  float *Qs = reinterpret_cast<float *>(sm);                        // hi (k^2), lo (k^2)
+  float *Gp = reinterpret_cast<float *>(sm + (size_t)k * k);        // hi (k^2), lo (k^2)
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const double g = Gd[e];
-    G[e] = g;
     Qs[e] = Qsg[e];
     Qs[k * k + e] = Qsg[k * k + e];
     const float gh = (float)g;
@@ -314,7 +315,6 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
     Gp[k * k + e] = (float)(g - (double)gh);
   }
   BppWarp w;
-  w.G = G;
   w.Qh = Qs;
   w.Ql = Qs + k * k;
   w.Gh = Gp;
@@ -331,15 +331,18 @@ __device__ __forceinline__ BppWarp bpp_stage(const double *__restrict__ Gd,
   }
   w.have_q = *q_ok != 0;
   w.refine = *q_ok == 2;
-  w.L = sm + 2 * lay.g_dbl + lay.gf_dbl + (size_t)wib * lay.warp_dbl;
-  w.v = w.L + (size_t)lay.kh * lay.ldl;  // small system's right-hand side, then x_F
-  w.rs = w.v + k;                        // r, by index
-  w.Fl = reinterpret_cast<int *>(w.rs + k);  // passive indices, ascending
-  w.Bl = w.Fl + k;                           // active indices, ascending
+  const size_t kf = 2 * (((size_t)k + 1) / 2);
+  float *base = reinterpret_cast<float *>(sm + lay.shared_dbl + (size_t)wib * lay.warp_dbl);
+  w.Lf = base;
+  w.bh = base + 2 * (((size_t)lay.kh * lay.ldl + 1) / 2);
+  w.bl = w.bh + kf;
+  w.dv = w.bl + kf;
+  w.Fl = reinterpret_cast<int *>(w.dv + kf);  // passive indices, ascending (k)
+  w.Bl = w.Fl + k;                            // active indices, ascending (k)
   w.xa = reinterpret_cast<float *>(w.Bl + k);  // |x_F| in FP32, F order
-  w.rsf = w.xa + 2 * ((k + 1) / 2);
-  w.vh = w.rsf + 2 * ((k + 1) / 2);
-  w.vl = w.vh + 2 * ((k + 1) / 2);
+  w.rsf = w.xa + kf;
+  w.vh = w.rsf + kf;
+  w.vl = w.vh + kf;
   w.ldl = lay.ldl;
   w.kh = lay.kh;
   return w;
@@ -437,7 +440,8 @@ __device__ __forceinline__ bool solve_mixed(const float *Mh, const float *Ml, in
 // tolerances (FP32): the exchange rule needs only their signs and
 // magnitudes, and FP64 instructions -- conversions and compares included --
 // run at ~1/60 of the FP32 rate.  The passive-set systems are solved by
-// solve_mixed, with the FP64 Cholesky as the fallback.
+// solve_mixed; a system it cannot finish sends the row to the FP64 fallback
+// kernel (k_bpp_direct), so this kernel keeps no FP64 state.
 template <int KT>
 __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__restrict__ R,
                                             int64_t row, int k, float *__restrict__ X, int warm,
@@ -445,16 +449,12 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
                                             bool *failed_cap_out) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const double *G = w.G;
   const float *Qh = w.Qh, *Ql = w.Ql;
-  auto Gat = [G, k](int a, int b) { return G[a * k + b]; };
-  auto Qat = [Qh, Ql, k](int a, int b) { return (double)Qh[a * k + b] + (double)Ql[a * k + b]; };
   const float *Gh = w.Gh, *Gl = w.Gl;
   const bool have_q = w.have_q;
-  double *L = w.L, *v = w.v;
-  float *Lf = reinterpret_cast<float *>(w.L);
-  float *bh = reinterpret_cast<float *>(w.v), *bl = bh + k;  // right-hand side pair
-  float *dv = reinterpret_cast<float *>(w.rs);               // corrections
+  float *Lf = w.Lf;
+  float *bh = w.bh, *bl = w.bl;  // right-hand side pair
+  float *dv = w.dv;              // corrections
   float *vh = w.vh, *vl = w.vl;  // solution pairs: F order (x_F) or B order (Q_BB^-1 z_B)
   int *Fl = w.Fl, *Bl = w.Bl;
   float *xa = w.xa, *rsf = w.rsf;
@@ -516,15 +516,11 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             bl[posf[t]] = 0.f;
           }
         __syncwarp();
+        // a system the FP32 solve cannot finish (an ill-conditioned G_FF)
+        // sends the row to the FP64 fallback kernel
         if (!solve_mixed(Gh, Gl, k, Fl, nf, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
-          __syncwarp();
-          if (!warp_cholesky(Gat, Fl, nf, L, ldl, lane)) { failed_numeric = true; break; }
-#pragma unroll
-          for (int t = 0; t < KT; ++t)
-            if (pas[t]) v[posf[t]] = (double)rf[t];
-          __syncwarp();
-          warp_chol_solve(L, ldl, nf, v, lane);
-          split_pair(v, nf, vh, vl, lane);
+          failed_numeric = true;
+          break;
         }
         __syncwarp();
 #pragma unroll
@@ -561,14 +557,8 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
         __syncwarp();
         // (vh, vl)[0..nb) = Q_BB^{-1} z_B = -y_B
         if (!solve_mixed(Qh, Ql, k, Bl, nb, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
-          __syncwarp();
-          if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
-#pragma unroll
-          for (int t = 0; t < KT; ++t)
-            if (!pas[t] && lane + 32 * t < k) v[posb[t]] = (double)zh[t] + (double)zl[t];
-          __syncwarp();
-          warp_chol_solve(L, ldl, nb, v, lane);
-          split_pair(v, nb, vh, vl, lane);
+          failed_numeric = true;
+          break;
         }
         __syncwarp();
 #pragma unroll
@@ -641,14 +631,8 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             }
           __syncwarp();
           if (!solve_mixed(Qh, Ql, k, Bl, nb, bh, bl, Lf, ldl, dv, vh, vl, lane)) {
-            __syncwarp();
-            if (!warp_cholesky(Qat, Bl, nb, L, ldl, lane)) { failed_numeric = true; break; }
-#pragma unroll
-            for (int t = 0; t < KT; ++t)
-              if (!pas[t] && lane + 32 * t < k) v[posb[t]] = (double)zrh[t] + (double)zrl[t];
-            __syncwarp();
-            warp_chol_solve(L, ldl, nb, v, lane);
-            split_pair(v, nb, vh, vl, lane);
+            failed_numeric = true;
+            break;
           }
           __syncwarp();
 #pragma unroll

@@ -510,7 +510,7 @@ cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count,
   g_inv_cols<<<count * kmax, 32, 0, s>>>(P, kmax);
   g_inv_check<<<count, 32, 0, s>>>(P, side);
   const bpp::BppLayout lay = bpp::bpp_layout(kmax);
-  const size_t smem = sizeof(double) * (2 * lay.g_dbl + lay.gf_dbl + (size_t)wpb * lay.warp_dbl);
+  const size_t smem = sizeof(double) * (lay.shared_dbl + (size_t)wpb * lay.warp_dbl);
   const int grid = nitems < sms() * 2 ? nitems : sms() * 2;
   const size_t fb_warp = (size_t)kmax * (kmax | 1) + 3 * (size_t)kmax;
   int fbw = (int)((200 * 1024 / sizeof(double) - (size_t)kmax * kmax) / fb_warp);
@@ -533,7 +533,7 @@ cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count,
 
 int bpp_max_warps(int kmax) {
   const bpp::BppLayout lay = bpp::bpp_layout(kmax);
-  int wpb = (int)((200 * 1024 / sizeof(double) - 2 * lay.g_dbl - lay.gf_dbl) / lay.warp_dbl);
+  int wpb = (int)((200 * 1024 / sizeof(double) - lay.shared_dbl) / lay.warp_dbl);
   if (wpb > bpp::kBppWarps) wpb = bpp::kBppWarps;
   return wpb < 1 ? 1 : wpb;
 }

@@ -162,10 +162,10 @@ cudaError_t launch_bpp(const double *G, const float *R, int64_t rows, int k, flo
   k_inv_check<<<1, 32, 0, s>>>(G, colsum, k, chol_ok, q_ok);
   const BppLayout lay = bpp_layout(k);
   const size_t budget = 200 * 1024;
-  int wpb = (int)((budget / sizeof(double) - 2 * lay.g_dbl - lay.gf_dbl) / lay.warp_dbl);
+  int wpb = (int)((budget / sizeof(double) - lay.shared_dbl) / lay.warp_dbl);
   if (wpb > kBppWarps) wpb = kBppWarps;
   if (wpb < 1) wpb = 1;
-  const size_t smem = sizeof(double) * (2 * lay.g_dbl + lay.gf_dbl + (size_t)wpb * lay.warp_dbl);
+  const size_t smem = sizeof(double) * (lay.shared_dbl + (size_t)wpb * lay.warp_dbl);
   int64_t nb = (rows + wpb - 1) / wpb;
   if (nb > (int64_t)sm_count() * 2) nb = (int64_t)sm_count() * 2;
   // fallback: a full-size factor per warp, as many warps (<= 8) as fit
