@@ -249,37 +249,6 @@ __device__ __forceinline__ void inv_check(const double *__restrict__ G,
   }
 }
 
-// v[0..n) (FP64, shared) into FP32 halves vh + vl = v to ~2^-48 relative, so
-// that sums of products with the FP32 pair of Q need no FP64 arithmetic.
-__device__ __forceinline__ void split_pair(const double *v, int n, float *vh, float *vl,
-                                           int lane) {
-  for (int b = lane; b < n; b += 32) {
-    const double x = v[b];
-    const float h = (float)x;
-    vh[b] = h;
-    vl[b] = (float)(x - (double)h);
-  }
-}
-
-// sum_b Q(I[b], j) v_b with Q = Qh + Ql and v = vh + vl: each Qh vh product
-// exact, the cross terms at FP32 precision (they are ~2^-24 of it), summed in
-// an FP32 pair.  ~10 FP32 operations per term against one FP64 FMA and the
-// two conversions that a product with Q in FP64 would take (the FP64 pipe runs
-// ~1/60 of the FP32 rate on this part).
-__device__ __forceinline__ double q_dot_pair(const float *Qh, const float *Ql, int k,
-                                             const int *I, int n, int j, const float *vh,
-                                             const float *vl) {
-  float hi = 0.f, lo = 0.f;
-  for (int b = 0; b < n; ++b) {
-    const int e = I[b] * k + j;
-    const float qh = Qh[e], ph = vh[b];
-    two_fma_acc(qh, ph, hi, lo);
-    lo = fmaf(qh, vl[b], lo);
-    lo = fmaf(Ql[e], ph, lo);
-  }
-  return (double)hi + (double)lo;
-}
-
 // Shared-memory view of one warp's BPP state (fast kernel).
 struct BppWarp {
   const float *Qh, *Ql;  // G^{-1} = Qh + Ql (FP32 pair)
