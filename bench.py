@@ -358,7 +358,10 @@ def run_batched(args):
                          "peak": peaks()[0]["hbm_gbs"], "unit": "GB/s",
                          "frac": bytes_iter / (t_batch / args.steps / 1e3) / 1e9 / peaks()[0]["hbm_gbs"],
                          "traffic": None,
-                         "kernel": "whole batched iteration (A's bytes of both products over the step)"},
+                         "kernel": "whole batched iteration (A's bytes of both products over the step)",
+                         "note": "the products stream at HBM speed; the iteration is bound by the "
+                                 "BPP solves (~2.2M right-hand sides per iteration, issue- and "
+                                 "latency-bound), so this fraction is the products' share of the step"},
             "relres_median_last": float(np.median(rel[:, -1])), "bpp_pivots": info["bpp_pivots"],
             "tuned_bpp_tile": [info["tuned_bpp_warps"], info["tuned_bpp_rows"]],
             "gpu_launches": int(info["launches"]), "clocks": clk,

@@ -1,32 +1,40 @@
 // k_bpp.cu -- batched nonnegative least squares by block principal pivoting
-// (Sec. 4.3: SolveBPP(C^T C, C^T B); Eqs. single NLS and KKT), in FP64.
+// (Sec. 4.3: SolveBPP(C^T C, C^T B); Eqs. single NLS and KKT), to FP64
+// accuracy.
 //
 // One warp solves one right-hand side r (a row of A H^T for W, a column of
 // W^T A for H) against the shared Gram matrix G:
 //     x = argmin_{x >= 0} ||C x - b||,   G = C^T C,  r = C^T b.
 // Lane l owns the indices j = l and j = l + 32 (k <= 64): its passive flag,
-// x_j, y_j = (G x - r)_j and the tolerance of the active-set test.
+// x_j and y_j = (G x - r)_j (FP32 pairs, ~48 bits) and the tolerance of the
+// active-set test (FP32).
 //
 // Exchange rule (Kim-He-Park / Judice-Pires): V = {passive j: x_j < 0} U
 // {active j: y_j < -tau_j}, tau_j = 1e-11 (|r_j| + sum_a |G_jF(a) x_F(a)|)
-// (y_j in FP64, the scale tau_j in FP32 in the fast kernel);
+// (the scale tau_j summed in FP32);
 // if |V| shrank, flip all of V and reset the backup counter to 3; else if
 // the counter is positive, decrement it and flip all of V; else flip only
 // the largest index in V.
 //
-// Each exchange solves the passive-set normal equations G_FF x_F = r_F in
-// FP64 with a Cholesky factorisation of at most k/2 rows:
-//   |F| <= |B|: Cholesky of G_FF itself;
-//   |F| >  |B|: with Q = G^{-1} (FP64, computed once per update) and
-//               z = Q r (once per right-hand side): the solution with x_B = 0
-//               and y_F = 0 satisfies x = Q (r + y), so Q_BB y_B = -z_B
-//               (Cholesky of Q_BB) and x_F = z_F + Q_FB y_B -- the block
-//               inverse G_FF^{-1} = Q_FF - Q_FB Q_BB^{-1} Q_BF in other words.
+// Each exchange solves the passive-set normal equations G_FF x_F = r_F with
+// a Cholesky factorisation of at most k/2 rows:
+//   |F| <= |B|: of G_FF itself;
+//   |F| >  |B|: with Q = G^{-1} (computed once per update in FP64, kept as
+//               an FP32 pair) and z = Q r (once per right-hand side): the
+//               solution with x_B = 0 and y_F = 0 satisfies x = Q (r + y), so
+//               Q_BB y_B = -z_B (Cholesky of Q_BB) and x_F = z_F + Q_FB y_B --
+//               the block inverse G_FF^{-1} = Q_FF - Q_FB Q_BB^{-1} Q_BF in
+//               other words.
+// The factorisation is FP32, refined with residuals summed in FP32 pairs
+// until a correction is below 2^-30 of x (bpp_core.cuh: solve_mixed); this
+// part runs ~60 times more FP32 than FP64 operations per clock.
 // The solution of each NLS is unique when G is positive definite (Sec. 4),
 // so the starting passive set changes only the work: the run driver starts
 // each right-hand side from the support of its previous iterate.  Rows whose
-// fast solve is not trustworthy (see k_bpp_direct) are redone from a cold
-// start with full-size Cholesky factorisations of G_FF.
+// fast solve cannot finish (an FP32 system too ill-conditioned to refine, or
+// a passive set too large for the route) are redone by k_bpp_direct in FP64,
+// with full-size Cholesky factorisations of G_FF, warm-started from the row's
+// previous iterate (cold if that fails at once).
 #include <math.h>
 
 #include "internal.cuh"
