@@ -40,7 +40,7 @@ extern "C" {
 #define AUNMF_E_NUMERIC -4     /* non-finite value, or a non-positive Cholesky pivot in BPP */
 #define AUNMF_E_NOCONVERGE -5  /* BPP hit its pivot cap on some right-hand side (results written) */
 #define AUNMF_E_TIMEOUT -6     /* a bounded device-side wait expired */
-#define AUNMF_E_UNSUPPORTED -7 /* valid request that this build does not implement */
+#define AUNMF_E_UNSUPPORTED -7 /* valid request that the library does not implement */
 
 /* ---- algorithms and precisions ---------------------------------------- */
 #define AUNMF_MU 0   /* Sec. 4.1, Eq. muupdate */

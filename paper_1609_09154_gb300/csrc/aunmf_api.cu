@@ -441,7 +441,7 @@ const char *aunmf_strerror(int code) {
     case AUNMF_E_NUMERIC: return "numerical failure (non-finite value or non-positive pivot)";
     case AUNMF_E_NOCONVERGE: return "BPP reached its pivot cap";
     case AUNMF_E_TIMEOUT: return "device wait timed out";
-    case AUNMF_E_UNSUPPORTED: return "unsupported by this build";
+    case AUNMF_E_UNSUPPORTED: return "unsupported by the library";
     default: return "unknown status";
   }
 }
