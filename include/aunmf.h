@@ -189,7 +189,7 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
  * GH = H H^T (k x k) [device].  MU: Eq. muupdate with eps; HALS: the
  * column sweep of Eq. halsupdate, then unit-normalised columns with H's rows
  * (H k x n, may be NULL) scaled by the norms; ABPP: each row of W solves
- * SolveBPP(GH, row of PW) in FP64 from a cold start (GH widened from FP32;
+ * SolveBPP(GH, row of PW) to FP64 accuracy from a cold start (GH widened from FP32;
  * aunmf_run forms its Grams in FP64 instead), and the call synchronises and
  * returns AUNMF_E_NUMERIC / AUNMF_E_NOCONVERGE if a row failed (W still
  * written).  eps <= 0 selects 1e-16. */
@@ -203,7 +203,8 @@ int aunmf_update_h(aunmf_handle *h, int algo, float *H, const float *PH, const f
 
 /* Batched NLS (Sec. 4.3, Eqs. single NLS and KKT): for each of `nrhs` rows r
  * of R (nrhs x k, float32 [device]) solves x = argmin_{x>=0} ||C x - b|| given
- * G = C^T C (k x k float32 [device]) and r = C^T b, in FP64; writes x as row r
+ * G = C^T C (k x k float32 [device]) and r = C^T b, to FP64 accuracy (FP32
+ * solves refined with FP32-pair residuals, FP64 where they cannot finish); writes x as row r
  * of X (nrhs x k float32 [device]).  pivots/nonconv (may be NULL) [host]
  * receive the total exchanges and the number of right-hand sides that hit
  * max_pivots (0 -> 10*k).  Returns AUNMF_E_NOCONVERGE / AUNMF_E_NUMERIC if
