@@ -66,7 +66,13 @@ def recorded_traffic(workload_key, prec, launch):
     return None
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 FMA lanes per SM
+
+
+def num_sms(device=0):
+    import torch
+
+    return torch.cuda.get_device_properties(device).multi_processor_count
 
 
 def peaks():
@@ -237,6 +243,8 @@ def run_reference(args):
     from oracle import oracle as orc
 
     orc.build()
+    if args.oracle_full:
+        return run_reference_full(args)
     ms, ns = SLICE
     A = make_slice(ms, ns)
     scale = (M_FULL * N_FULL) / (ms * ns)
@@ -252,13 +260,54 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+        # the measured wall time of one step, i.e. of one sampled iteration;
+        # value = 1 / (that time x sample_scale)
+        "ms_per_step": dt * 1e3, "sample_scale": scale,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
                          "sample": f"each step: one {args.algo.upper()} iteration of the FP64 "
-                                   f"oracle on a {ms}x{ns} slice, scaled by {scale:.0f}"},
+                                   f"oracle on a {ms}x{ns} slice ({dt:.2f} s measured), "
+                                   f"iters/s of the {M_FULL}x{N_FULL} workload = 1 / ({dt:.2f} s"
+                                   f" x {scale:.0f}), the entry ratio (the products, O(m n k), "
+                                   f"dominate the oracle's iteration)"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_full(args):
+    """The oracle on the whole 96,000 x 64,000 workload (A drawn on the host in
+    FP64 by row blocks, 49 GB), `steps` iterations timed without scaling: a
+    check of the slice-and-scale figure the default arms report.  Minutes of
+    host time per iteration; not part of the default run."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_1609_09154_gb300 import synth
+
+    m, n, k = M_FULL, N_FULL, args.k
+    t0 = time.perf_counter()
+    A, _, _ = synth.dense_lowrank_blocked(m, n, RANK_FULL, seed=SEED)
+    np.copyto(A, A.astype(np.float32))  # the FP32-rounded A the GPU sees
+    W0, H0 = synth.init_factors(m, n, k, seed=SEED)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out = orc.nmf_run(A, k, args.algo, args.steps, W0, H0)
+    dt = (time.perf_counter() - t0) / args.steps
+    assert out["rc"] in (0, -5) and np.isfinite(out["relres"]).all()
+    ms, ns = SLICE
+    dt_slice, threads = oracle_sample(args.algo, make_slice(ms, ns), k, 1)
+    line = {
+        "impl": "reference", "oracle_full": True, "metric": METRIC, "value": 1.0 / dt,
+        "unit": "iters/s", "steps": args.steps, "ms_per_step": dt * 1e3, "dtype": "f64",
+        "config": config_dict(args), "cores": threads, "host_generation_s": round(t_gen, 1),
+        "relres": [float(x) for x in out["relres"]],
+        "slice_check": {"slice": f"{ms}x{ns}", "s_per_iter": dt_slice,
+                        "scaled_s_per_iter": dt_slice * (m * n) / (ms * ns),
+                        "full_over_scaled": dt / (dt_slice * (m * n) / (ms * ns))},
     }
     print(json.dumps(line))
     return 0
@@ -451,6 +500,47 @@ def run_ksweep(args):
     return 0
 
 
+# --------------------------------------------------------------------- accuracy
+def accuracy_vs_oracle(h, dev, iters=30):
+    """Every local update in every precision form against the FP64 oracle on
+    the small dense configuration (2,000 x 1,500, planted rank 10 + noise,
+    k = 10, 30 iterations from the same (W0, H0)): the largest |relres
+    difference| over the iterations, the final one, the relative difference
+    of the objective 0.5 ||A - WH||^2 (= relres^2 ||A||^2 / 2), and the
+    factors' relative Frobenius distance from the oracle's."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as orc
+    from paper_1609_09154_gb300 import synth
+
+    m, n, k = 2000, 1500, 10
+    A, _, _ = synth.dense_lowrank(m, n, k, seed=2024)
+    W0, H0 = synth.init_factors(m, n, k, seed=2024)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    A, W0, H0 = r32(A), r32(W0), r32(H0)
+    d = lambda x: torch.as_tensor(x.astype(np.float32), device=dev)  # noqa: E731
+    out = {"workload": f"dense {m}x{n}, planted rank {k} + |N(0,0.01^2)|, k={k}, "
+                       f"{iters} iterations, FP64 oracle on the same FP32-rounded inputs"}
+    for algo in ("mu", "hals", "abpp"):
+        ref = orc.nmf_run(A, k, algo, iters, W0, H0)
+        rr = ref["relres"]
+        nw, nh = np.linalg.norm(ref["W"]), np.linalg.norm(ref["H"])
+        for prec in ("fp32", "tf32", "bf16"):
+            W, H, rel, _ = h.run(d(A), k, algo, iters, d(W0), d(H0), prec=prec,
+                                 allow_noconverge=True)
+            Wh = W.cpu().numpy().astype(np.float64)
+            Hh = H.cpu().numpy().astype(np.float64)
+            out[f"{algo}_{prec}"] = {
+                "relres_max_abs_diff": float(np.abs(rel - rr).max()),
+                "relres_last_abs_diff": float(abs(rel[-1] - rr[-1])),
+                "objective_rel_diff": float(abs(rel[-1] ** 2 - rr[-1] ** 2) / rr[-1] ** 2),
+                "w_rel_err": float(np.linalg.norm(Wh - ref["W"]) / nw),
+                "h_rel_err": float(np.linalg.norm(Hh - ref["H"]) / nh),
+            }
+    return out
+
+
 # --------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -481,15 +571,16 @@ def run_ours(args):
     H = torch.empty_like(H0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed(prec, profile=False):
+    def timed(prec, profile=False, algo=None):
         """warm-up (untimed), then `steps` iterations from (W0, H0) timed with
         CUDA events around the call (the library's stream is the current
         stream's device; the call returns after its stream synchronises)."""
-        h.run(A, k, args.algo, args.warmup, W0, H0, prec=prec, out=(W, H), allow_noconverge=True)
+        algo = algo or args.algo
+        h.run(A, k, algo, args.warmup, W0, H0, prec=prec, out=(W, H), allow_noconverge=True)
         barrier(world)
         torch.cuda.synchronize()
         e0.record()
-        _, _, r, inf = h.run(A, k, args.algo, args.steps, W0, H0, prec=prec, out=(W, H),
+        _, _, r, inf = h.run(A, k, algo, args.steps, W0, H0, prec=prec, out=(W, H),
                              profile=profile, allow_noconverge=True)
         e1.record()
         torch.cuda.synchronize()
@@ -506,21 +597,57 @@ def run_ours(args):
     # the same run in profile mode (no graph; CUDA events around each phase on
     # the library's stream) for the per-kernel durations of the roofline
     _, _, info = timed(args.prec, profile=True)
-    # the three precision forms from the same start: matched residual
+    # the three precision forms from the same start: matched residual, the
+    # factors' distance from the FP32 form's, and the time each form takes to
+    # reach a residual that all of them reach
     forms = None
     if not sparse and not args.no_forms:
-        forms = {}
+        forms, fac, rels = {}, {}, {}
         for pr in ("fp32", "tf32", "bf16"):
-            if pr == args.prec:
-                t, r = ms_total, rel
-            else:
-                t, r, _ = timed(pr)
+            t, r, _ = timed(pr)
+            fac[pr] = (W.clone(), H.clone())
+            rels[pr] = r
             forms[pr] = {"iters_per_s": world * args.steps / (t / 1e3),
                          "ms_per_step": t / args.steps, "relres_last": float(r[-1])}
         base = forms["fp32"]
+        target = max(f["relres_last"] for f in forms.values())
+        Wb, Hb = fac["fp32"]
         for pr, f in forms.items():
             f["speedup_vs_fp32"] = f["iters_per_s"] / base["iters_per_s"]
             f["relres_gap_vs_fp32"] = abs(f["relres_last"] - base["relres_last"])
+            Wf, Hf = fac[pr]
+            f["w_rel_err_vs_fp32"] = float(torch.linalg.norm(Wf - Wb) / torch.linalg.norm(Wb))
+            f["h_rel_err_vs_fp32"] = float(torch.linalg.norm(Hf - Hb) / torch.linalg.norm(Hb))
+            hit = int(np.argmax(rels[pr] <= target)) + 1
+            f["iters_to_target"] = hit
+            f["ms_to_target"] = hit * f["ms_per_step"]
+        forms["target_relres"] = target
+        forms["note"] = ("each form runs the same iterations from the same (W0, H0); the target "
+                         "is the largest final relres of the three, which all of them reach; "
+                         "factor errors are ||X_form - X_fp32||_F / ||X_fp32||_F")
+        del fac
+
+    # the paper's three local updates (Secs. 4.1-4.3) on the same input and
+    # precision: iterations/s, relres, time per phase and the product roofline
+    algos = None
+    if not sparse and not args.no_algos:
+        algos = {}
+        for al in ("mu", "hals", "abpp"):
+            t, r, _ = timed(args.prec, algo=al)
+            _, _, inf = timed(args.prec, profile=True, algo=al)
+            st = max(1, args.steps)
+            ph = {p: round(inf[f"ms_{p}"] / st, 4) for p in ("aht", "wta", "update", "gram", "other")}
+            t_prod = max(inf["ms_aht"] / max(1, inf["n_aht"]), inf["ms_wta"] / max(1, inf["n_wta"]))
+            prod = {"ms_avg": round(t_prod, 4)}
+            if args.prec != "fp32":
+                gbs = product_bytes(m, n, k, args.prec) / (t_prod / 1e3) / 1e9
+                prod.update({"bound": "hbm", "achieved_gbs": round(gbs, 1),
+                             "frac": gbs / peaks()[0]["hbm_gbs"]})
+            algos[al] = {"iters_per_s": world * args.steps / (t / 1e3),
+                         "ms_per_step": t / args.steps, "relres_last": float(r[-1]),
+                         "phases_ms_per_step": ph, "slower_product": prod,
+                         "update_share": ph["update"] / max(1e-9, sum(ph.values())),
+                         "bpp_redone": inf.get("bpp_redone", 0) if al == "abpp" else None}
 
     # dominant kernel: the product launch with the larger summed time
     pk, pks = peaks()
@@ -542,11 +669,12 @@ def run_ours(args):
                              f"are served from L2)"}
     elif args.prec == "fp32":
         sm_mhz = (clk or {}).get("sm_mhz") or 1485.0
-        peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        sms = num_sms(local)
+        peak = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         ach = 2.0 * m * n * k / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "kernel": f"{dom} (FP32 FMA products)",
-                "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM "
+                "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM "
                              f"clock sampled during the timed region)"}
     else:
         by = product_bytes(m, n, k, args.prec)
@@ -589,6 +717,9 @@ def run_ours(args):
     if (rank == 0 and world == 1 and not args.no_cpu and args.workload == "dense"
             and (m, n) == (M_FULL, N_FULL)):
         cpu = cpu_baseline(args.algo, k)
+    accuracy = None
+    if rank == 0 and not args.no_accuracy and not sparse:
+        accuracy = accuracy_vs_oracle(h, dev)
 
     if rank == 0:
         f_it = flops_per_iter(m, n, k, args.algo)
@@ -602,7 +733,7 @@ def run_ours(args):
             "data": "synthetic", "config": config_dict(args),
             "tflops": f_it * value / 1e12,
             "relres_last": float(rel[-1]) if len(rel) else None,
-            "forms": forms,
+            "forms": forms, "algos": algos, "accuracy_vs_fp64": accuracy,
             "roofline": roof, "kernels": kern, "phases_ms_per_step": phases,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(info_g["launches"]), "clocks": clk,
@@ -632,6 +763,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32 / TF32 / BF16 comparison runs")
+    ap.add_argument("--no-algos", action="store_true",
+                    help="skip the MU / HALS / ABPP runs on the same input")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the comparison with the FP64 oracle on the small configuration")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="--impl reference: time the oracle on the whole workload, unscaled")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

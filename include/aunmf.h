@@ -237,6 +237,40 @@ int aunmf_loss_fwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
 int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
                    int prec, const float *WtA, const float *grad_out, float *dW, float *dH);
 
+/* ---- fault injection for tests ---------------------------------------------- */
+
+/* Every wait of a kernel on another thread, warp or block of the same launch
+ * (the tensor-core products' mbarrier waits, the printed HALS sweep's grid
+ * barrier) is bounded: after ~2 s it raises the call's device error flag,
+ * the kernel drains the copies and tensor-core operations it has in flight,
+ * frees its tensor memory and returns, and the call returns AUNMF_E_TIMEOUT
+ * with the device context still usable.  aunmf_test_inject() makes those
+ * paths run on purpose, for tests, without faulting or hanging the GPU: it
+ * withholds one signal so that a bounded wait runs out.  The setting is
+ * process-wide and applies to every launch made after the call, until it is
+ * set back to AUNMF_INJECT_NONE; it is read when a kernel is launched (a CUDA
+ * graph keeps the value seen at capture).
+ *   site     AUNMF_INJECT_NONE          back to normal operation
+ *            AUNMF_INJECT_TC_WAIT       tensor-core products (aunmf_run,
+ *              aunmf_run_batched, aunmf_aht / aunmf_wta in TF32 / BF16): the
+ *              MMA warp never signals that the first accumulator chunk is
+ *              ready, so the epilogue's wait runs out
+ *            AUNMF_INJECT_GRID_BARRIER  printed HALS sweep (hals_variant 1):
+ *              block 0 never arrives at the first grid barrier
+ *            AUNMF_INJECT_NOMEM         every workspace allocation fails with
+ *              AUNMF_E_NOMEM (cudaMalloc is not called); buffers a handle
+ *              already holds stay usable
+ *   wait_ms  limit of the bounded waits while `site` is set, in milliseconds
+ *            of the device's maximum SM clock (<= 0: the default ~2 s);
+ *            ignored for AUNMF_INJECT_NONE, which restores the default.
+ * Returns AUNMF_OK, or AUNMF_E_INVAL for an unknown site or wait_ms > 60000.
+ * The paper has no counterpart; this is test support of the library. */
+#define AUNMF_INJECT_NONE 0
+#define AUNMF_INJECT_TC_WAIT 1
+#define AUNMF_INJECT_GRID_BARRIER 2
+#define AUNMF_INJECT_NOMEM 3
+int aunmf_test_inject(int site, double wait_ms);
+
 /* ---- fixed-memory variant ------------------------------------------------ */
 
 /* G = W^T W (k x k) for W m x k [device in/out], like aunmf_gram_w, for
@@ -253,7 +287,8 @@ int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
  *     only enqueues work and does not synchronise.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  After a device reset (a new CUDA context on
+ *     the device) the next call looks the address up again.
  *   - Every call on a device shares the one array.  Nothing in it needs to
  *     start at zero (each call overwrites all it reads), but calls whose GPU
  *     work overlaps in time -- e.g. on two streams -- race on it: order them

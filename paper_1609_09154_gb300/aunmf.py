@@ -23,6 +23,7 @@ K_MAX, BPP_K_MAX = 512, 64
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_NOCONVERGE, E_TIMEOUT, E_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6, -7)
+INJECT_NONE, INJECT_TC_WAIT, INJECT_GRID_BARRIER, INJECT_NOMEM = 0, 1, 2, 3
 
 
 class AunmfError(RuntimeError):
@@ -91,6 +92,7 @@ SIGNATURES = {
     "aunmf_nls_bpp": [_P, _P, _P, _I64, _I, _P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
     "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
+    "aunmf_test_inject": [_I, _D],
     "aunmf_loss_fwd": [_P, _MP, _I, _P, _P, _I, _P, _P],
     "aunmf_run_batched": [_P, _I, _MP, _P, _I, _I, _P, _P, _P, _P, _P, _OP, _IP],
     "aunmf_loss_bwd": [_P, _MP, _I, _P, _P, _I, _P, _P, _P, _P],
@@ -125,6 +127,12 @@ def load(build_if_missing: bool = True):
 
 def strerror(code: int) -> str:
     return load().aunmf_strerror(code).decode()
+
+
+def test_inject(site: int, wait_ms: float = 0.0) -> int:
+    """aunmf_test_inject: make one kind of bounded device wait run out (test
+    support; INJECT_NONE restores normal operation).  Returns the status."""
+    return load().aunmf_test_inject(site, wait_ms)
 
 
 # ---------------------------------------------------------------- helpers

@@ -14,10 +14,14 @@ _handles = {}
 
 
 def _handle():
+    """The library handle of the current device, bound to torch's current
+    stream: the inputs were produced there and the outputs are allocated for
+    it by torch's caching allocator, so the library's kernels must run on it."""
     dev = torch.cuda.current_device()
     h = _handles.get(dev)
     if h is None:
         h = _handles[dev] = aunmf.Handle()
+    h.set_stream(torch.cuda.current_stream())
     return h
 
 

@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <tuple>
@@ -27,6 +28,14 @@
 using namespace aunmf;
 
 thread_local long long aunmf::g_launches = 0;
+
+namespace {
+std::atomic<int> g_inject_site{AUNMF_INJECT_NONE};
+std::atomic<long long> g_inject_cycles{aunmf::fault::kDefaultWaitCycles};
+}  // namespace
+
+int aunmf::fault::site() { return g_inject_site.load(std::memory_order_relaxed); }
+long long aunmf::fault::wait_cycles() { return g_inject_cycles.load(std::memory_order_relaxed); }
 
 struct Buf {
   void *p = nullptr;
@@ -79,6 +88,10 @@ size_t dpart_bytes(const aunmf_handle *h) {
 int ensure(aunmf_handle *h, Buf &b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return AUNMF_OK;
+  if (fault::site() == AUNMF_INJECT_NOMEM) {
+    h->cuda_err = "cudaMalloc: not called (allocation failure injected)";
+    return AUNMF_E_NOMEM;
+  }
   if (b.p) {
     cudaStreamSynchronize(h->stream);
     cudaFree(b.p);
@@ -147,6 +160,28 @@ struct RunCtx {
   double *pg_dev;       // projected-gradient norm per iteration (slot ctr->iter)
   std::vector<cudaEvent_t> *ev;          // profile events (pairs)
   std::vector<int> *ev_phase;            // phase index per pair
+};
+
+// Events and the graph of one call, released on every return path (a
+// failed call must not leak them).  Destroying an event or an executable
+// graph whose work is still in flight is allowed: the driver frees it once
+// that work completes.
+struct CallResources {
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<cudaEvent_t> ev;  // profile events (pairs)
+  CallResources() = default;
+  CallResources(const CallResources &) = delete;
+  CallResources &operator=(const CallResources &) = delete;
+  ~CallResources() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+  }
 };
 
 enum Phase { kPhAht = 0, kPhWta = 1, kPhUpdate = 2, kPhGram = 3, kPhOther = 4 };
@@ -486,6 +521,26 @@ int aunmf_destroy(aunmf_handle *h) {
 
 const char *aunmf_last_cuda_error(aunmf_handle *h) { return h ? h->cuda_err.c_str() : ""; }
 
+int aunmf_test_inject(int site, double wait_ms) {
+  if (site < AUNMF_INJECT_NONE || site > AUNMF_INJECT_NOMEM) return AUNMF_E_INVAL;
+  if (!(wait_ms <= 60000.0)) return AUNMF_E_INVAL;  // also rejects NaN
+  long long cycles = fault::kDefaultWaitCycles;
+  if (site != AUNMF_INJECT_NONE && wait_ms > 0.0) {
+    // the SM clock counted by clock64(); at most the device's maximum clock
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+      cudaGetLastError();
+      khz = 2100000;
+    }
+    cycles = (long long)(wait_ms * (double)khz);
+    if (cycles < 1000) cycles = 1000;
+  }
+  g_inject_cycles.store(cycles, std::memory_order_relaxed);
+  g_inject_site.store(site, std::memory_order_relaxed);
+  return AUNMF_OK;
+}
+
 int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
               const float *W0, const float *H0, float *W, float *H, double *relres,
               const aunmf_options *opt, aunmf_info *info) {
@@ -534,9 +589,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   c.relres_dev = P<double>(h->relres);
   c.last = P<double>(h->last);
   c.ctr = P<DevCounters>(h->ctr);
-  std::vector<cudaEvent_t> ev;
+  CallResources R;
   std::vector<int> ev_phase;
-  c.ev = &ev;
+  c.ev = &R.ev;
   c.ev_phase = &ev_phase;
   c.profile = o.profile != 0;
   c.hals_variant = algo == AUNMF_HALS ? o.hals_variant : 0;
@@ -555,10 +610,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   }
   const long long launches0 = g_launches;
   long long graph_launches = 0;
-  cudaEvent_t t0, t1;
-  CK(h, cudaEventCreate(&t0));
-  CK(h, cudaEventCreate(&t1));
-  CK(h, cudaEventRecord(t0, s));
+  CK(h, cudaEventCreate(&R.t0));
+  CK(h, cudaEventCreate(&R.t1));
+  CK(h, cudaEventRecord(R.t0, s));
   CK(h, cudaMemsetAsync(c.ctr, 0, sizeof(DevCounters), s));
   // setup (a0): W0 -> W, H0 -> Ht, ||A||^2, BF16 copy of A, initial G_H
   if (algo != AUNMF_ABPP) {
@@ -592,8 +646,6 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     CK(h, product_wta(h, c, s));
   }
 
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
   // the printed HALS sweep is a cooperative launch: not captured
   const bool use_graph = o.use_graph && !o.profile && iters > 1 && c.hals_variant == 0;
   if (use_graph) {
@@ -604,17 +656,17 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     const long long per_iter = g_launches - lc0;
     g_launches = lc0;  // captured, not launched: counted per replay below
     graph_launches = per_iter;
-    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+    cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &R.graph);
     if (ce != cudaSuccess) return fail_cuda(h, ce, "iterate (capture)");
     if (ee != cudaSuccess) return fail_cuda(h, ee, "cudaStreamEndCapture");
-    CK(h, cudaGraphInstantiate(&gexec, graph, 0));
+    CK(h, cudaGraphInstantiate(&R.gexec, R.graph, 0));
   }
   // with a stop rule the host reads each iteration's measure before the next
   int done = 0;
   double pg0 = 0.0, pg_last = 0.0;
   for (int t = 0; t < iters; ++t) {
-    if (gexec) {
-      CK(h, cudaGraphLaunch(gexec, s));
+    if (R.gexec) {
+      CK(h, cudaGraphLaunch(R.gexec, s));
     } else {
       cudaError_t e = iterate(h, c, s);
       if (e != cudaSuccess) return fail_cuda(h, e, "iterate");
@@ -629,7 +681,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   }
   graph_launches *= done;
   CK(h, launch_transpose(c.Ht, n, k, H, s));
-  CK(h, cudaEventRecord(t1, s));
+  CK(h, cudaEventRecord(R.t1, s));
   DevCounters hc{};
   int herr = 0;
   CK(h, cudaMemcpyAsync(&hc, c.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
@@ -637,8 +689,6 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   if (relres && done > 0)
     CK(h, cudaMemcpyAsync(relres, c.relres_dev, sizeof(double) * done, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
   if (info) {
     memset(info, 0, sizeof(*info));
     info->bpp_pivots = hc.bpp_pivots;
@@ -649,10 +699,10 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     info->pgrad_first = pg0;
     info->pgrad_last = pg_last;
     info->launches = g_launches - launches0 + graph_launches;
-    cudaEventElapsedTime(&info->ms_total, t0, t1);
+    cudaEventElapsedTime(&info->ms_total, R.t0, R.t1);
     for (size_t p = 0; p < ev_phase.size(); ++p) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[2 * p], ev[2 * p + 1]);
+      cudaEventElapsedTime(&ms, R.ev[2 * p], R.ev[2 * p + 1]);
       switch (ev_phase[p]) {
         case kPhAht: info->ms_aht += ms; info->n_aht += 1; break;
         case kPhWta: info->ms_wta += ms; info->n_wta += 1; break;
@@ -662,9 +712,6 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
       }
     }
   }
-  for (cudaEvent_t e : ev) cudaEventDestroy(e);
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
   if (herr) return AUNMF_E_TIMEOUT;
   if (hc.nonfinite) return AUNMF_E_NUMERIC;
   if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
@@ -1271,10 +1318,10 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
   const int max_piv = max_piv_opt > 0 ? max_piv_opt : 10 * pl.kmax;
   const long long launches0 = g_launches;
   long long graph_launches = 0;
-  cudaEvent_t t0, t1;
-  CK(h, cudaEventCreate(&t0));
-  CK(h, cudaEventCreate(&t1));
-  CK(h, cudaEventRecord(t0, s));
+  CallResources R;
+  CK(h, cudaEventCreate(&R.t0));
+  CK(h, cudaEventCreate(&R.t1));
+  CK(h, cudaEventRecord(R.t0, s));
   CK(h, cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s));
   CK(h, cudaMemsetAsync(err, 0, sizeof(int), s));
 
@@ -1327,9 +1374,10 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     if (cand.empty()) cand.push_back({wmax, 4});
     float best = 1e30f;
     std::pair<int, int> best_tile = cand[0];
-    cudaEvent_t a0, a1;
-    CK(h, cudaEventCreate(&a0));
-    CK(h, cudaEventCreate(&a1));
+    R.ev.assign(2, nullptr);
+    CK(h, cudaEventCreate(&R.ev[0]));
+    CK(h, cudaEventCreate(&R.ev[1]));
+    cudaEvent_t a0 = R.ev[0], a1 = R.ev[1];
     for (const auto &c : cand) {
       tile = c;
       stage_meta(meta);
@@ -1345,8 +1393,6 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
       cudaEventElapsedTime(&ms, a0, a1);
       if (ms < best) { best = ms; best_tile = c; }
     }
-    cudaEventDestroy(a0);
-    cudaEventDestroy(a1);
     tile = best_tile;
     h->bpp_tuned[sig] = tile;
     for (const auto &b : pl.inst) CK(h, cudaMemsetAsync(b.W, 0, sizeof(float) * b.m * b.k, s));
@@ -1356,8 +1402,6 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
   }
 
   // ---- iterations: one captured iteration, replayed
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
   if (iters > 0) {
     const batched::Item *rw = reinterpret_cast<const batched::Item *>(D(pl.o_rw));
     const batched::Item *rh = reinterpret_cast<const batched::Item *>(D(pl.o_rh));
@@ -1368,12 +1412,12 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
       if (ce == cudaSuccess) ce = h_half(h->cap_stream, inst_d(), rh, (int)pl.rows_h.size());
       const long long per_iter = g_launches - lc0;
       g_launches = lc0;
-      cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+      cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &R.graph);
       if (ce != cudaSuccess) return fail_cuda(h, ce, "batched iteration (capture)");
       if (ee != cudaSuccess) return fail_cuda(h, ee, "cudaStreamEndCapture");
-      CK(h, cudaGraphInstantiate(&gexec, graph, 0));
+      CK(h, cudaGraphInstantiate(&R.gexec, R.graph, 0));
       graph_launches = per_iter * iters;
-      for (int t = 0; t < iters; ++t) CK(h, cudaGraphLaunch(gexec, s));
+      for (int t = 0; t < iters; ++t) CK(h, cudaGraphLaunch(R.gexec, s));
     } else {
       for (int t = 0; t < iters; ++t) {
         CK(h, w_half(s, inst_d(), rw, (int)pl.rows_w.size()));
@@ -1384,7 +1428,7 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
   CK(h, batched::launch_finish(inst_d(), reinterpret_cast<float *const *>(D(pl.o_h)),
                                reinterpret_cast<const int64_t *>(D(pl.o_rmx)), count,
                                pl.rows_mx[count], s));
-  CK(h, cudaEventRecord(t1, s));
+  CK(h, cudaEventRecord(R.t1, s));
   DevCounters hc{};
   int herr = 0;
   CK(h, cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -1393,8 +1437,6 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     CK(h, cudaMemcpyAsync(relres, base + relres_off, sizeof(double) * (size_t)count * iters,
                           cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
   if (info) {
     memset(info, 0, sizeof(*info));
     info->bpp_pivots = hc.bpp_pivots;
@@ -1402,13 +1444,11 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     info->bpp_numeric = hc.bpp_numeric;
     info->bpp_redone = hc.bpp_redo;
     info->iters_done = iters;
-    cudaEventElapsedTime(&info->ms_total, t0, t1);
+    cudaEventElapsedTime(&info->ms_total, R.t0, R.t1);
     info->launches = g_launches - launches0 + graph_launches;
     info->tuned_bpp_warps = tile.first;
     info->tuned_bpp_rows = tile.second;
   }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
   if (herr) return AUNMF_E_TIMEOUT;
   if (hc.bpp_numeric) return AUNMF_E_NUMERIC;
   if (hc.bpp_nonconv) return AUNMF_E_NOCONVERGE;

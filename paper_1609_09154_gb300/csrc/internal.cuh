@@ -15,6 +15,16 @@ constexpr int kWarp = 32;
 // launcher adds the number of kernels it launches.
 extern thread_local long long g_launches;
 
+// Bounded device waits and the test hook that makes them run out
+// (aunmf_test_inject).  site(): the injection now set (AUNMF_INJECT_*);
+// wait_cycles(): SM clocks a bounded wait may spin before it gives up,
+// ~2 s unless the hook set a shorter limit.
+namespace fault {
+constexpr long long kDefaultWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+int site();
+long long wait_cycles();
+}  // namespace fault
+
 // Device-side error/diagnostic counters, one block of int64 in the workspace.
 struct DevCounters {
   long long bpp_pivots;

@@ -401,7 +401,6 @@ int luc_blocks(int64_t rows) {
 // column i the blocks' FP64 sums of squares meet behind a bounded grid
 // barrier, each block adds them in block order (the same norm everywhere),
 // and each thread rescales its rows' column i when it next reads them.
-constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kPrintedThreads = 256;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -411,19 +410,22 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 }
 
 // true once every block of the grid has arrived for the gen-th time (the
-// counter starts at 0); false, with *err set, after ~2 s or once another
-// block has given up.
-__device__ bool grid_barrier(unsigned *count, unsigned gen, int *err) {
+// counter starts at 0); false, with *err set, after `limit` SM clocks or once
+// another block has given up.  skip (test hook): this block does not arrive.
+__device__ bool grid_barrier(unsigned *count, unsigned gen, int *err, long long limit,
+                             bool skip) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    if (!skip) {
+      __threadfence();
+      atomicAdd(count, 1u);
+    }
     const unsigned target = gen * gridDim.x;
     const long long t0 = clock64();
     ok = 1;
     while (ld_acquire_u32(count) < target) {
-      if (clock64() - t0 > kBarrierCycles || *(volatile int *)err) {
+      if (clock64() - t0 > limit || *(volatile int *)err) {
         atomicExch(err, 1);
         ok = 0;
         break;
@@ -449,7 +451,8 @@ __device__ __forceinline__ double block_sum_d256(double v, double *red) {
 __global__ void __launch_bounds__(kPrintedThreads)
     k_hals_w_printed(float *__restrict__ W, const float *__restrict__ P,
                      const float *__restrict__ Gg, int64_t rows, int k, int gsm,
-                     double *__restrict__ part, unsigned *bar, int *err) {
+                     double *__restrict__ part, unsigned *bar, int *err, long long limit,
+                     int inject) {
   extern __shared__ float sG[];
   __shared__ double red[kPrintedThreads / 32];
   __shared__ float s_inv;
@@ -477,7 +480,9 @@ __global__ void __launch_bounds__(kPrintedThreads)
     const double bsum = block_sum_d256(ss, red);
     double *pi = part + (size_t)(i & 1) * gridDim.x;
     if (threadIdx.x == 0) pi[blockIdx.x] = bsum;
-    if (!grid_barrier(bar, (unsigned)(i + 1), err)) return;
+    // inject (test hook): block 0 never arrives at the first barrier
+    if (!grid_barrier(bar, (unsigned)(i + 1), err, limit, inject && i == 0 && blockIdx.x == 0))
+      return;
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(pi + b);
@@ -572,7 +577,9 @@ cudaError_t launch_hals_w_printed(float *W, const float *P, const float *G, int6
   if (grid < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  void *args[] = {&W, &P, &G, &rows, &k, &gsm, &part, &bar, &err};
+  long long limit = fault::wait_cycles();
+  int inject = fault::site() == AUNMF_INJECT_GRID_BARRIER ? 1 : 0;
+  void *args[] = {&W, &P, &G, &rows, &k, &gsm, &part, &bar, &err, &limit, &inject};
   e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_hals_w_printed), (int)grid,
                                   kPrintedThreads, args, smem, s);
   g_launches += 1;

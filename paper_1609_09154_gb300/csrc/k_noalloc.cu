@@ -11,6 +11,8 @@
 // The array is g_gram_scratch below: kNoAllocBlocks partial k x k matrices
 // for k <= kNoAllocKMax, i.e. 256 * 64 * 64 floats = 4 MiB, which every GPU
 // that loads this library holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -25,12 +27,44 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) float g_gram_scratch[kNoAllocBlocks * kNoAllocKMax * kNoAllocKMax];
 
 std::mutex g_scratch_mu;
-float *g_scratch_dev[kMaxDevices] = {};  // device address of g_gram_scratch, per device
+// device address of g_gram_scratch per device, and the id of the CUDA
+// context it was looked up in (a device reset creates a new context, in
+// which the module and its array are loaded again at another address)
+float *g_scratch_dev[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the current context (0 if the driver cannot tell).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 // Device address of the scratch array on the current device.  The symbol's
 // name in host code is only a host-side stand-in; the address a kernel may
-// use comes from cudaGetSymbolAddress, looked up once per device with that
-// device current.
+// use comes from cudaGetSymbolAddress, looked up with that device current
+// once per device and context (again after a device reset).
 float *scratch_for_current_device(int *status) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
@@ -42,8 +76,9 @@ float *scratch_for_current_device(int *status) {
     *status = AUNMF_E_UNSUPPORTED;
     return nullptr;
   }
+  const unsigned long long ctx = current_context_id();  // 0: no context yet
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_dev[dev]) {
+  if (!g_scratch_dev[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_gram_scratch);
     if (e != cudaSuccess || !p) {
@@ -52,6 +87,8 @@ float *scratch_for_current_device(int *status) {
       return nullptr;
     }
     g_scratch_dev[dev] = static_cast<float *>(p);
+    // the lookup has made the runtime's context current if it was not yet
+    g_scratch_ctx[dev] = current_context_id();
   }
   *status = AUNMF_OK;
   return g_scratch_dev[dev];

@@ -40,7 +40,8 @@
 // fixed order, so results do not depend on scheduling.
 //
 // Every mbarrier wait is bounded (clock64); on expiry the kernel raises a
-// device error flag, skips the rest of its work and still frees TMEM.
+// device error flag and skips the rest of its work, then waits (bounded
+// again) for the copies and MMAs it has in flight and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdio.h>
@@ -58,7 +59,6 @@ constexpr int kTileM = 256;          // rows of X per work unit (2 x M=128 MMAs)
 constexpr int kMaxBN = 256;          // MMA N limit; wider products are split by columns
 constexpr int kStageBytesK = 128;    // K extent of one stage in bytes (one 128B swizzle row)
 constexpr int kThreads = 320;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 #ifndef AUNMF_TC_CHUNK_KB
 #define AUNMF_TC_CHUNK_KB 2
 #endif
@@ -109,20 +109,31 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of parity `parity`; false on expiry (or if
-// another thread already raised the error flag).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
+// Bounded wait for the phase of parity `parity`; false on expiry after
+// `limit` SM clocks (or once another thread has raised the error flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err, long long limit) {
   if (mbar_try(b, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t spins = 1;; ++spins) {
     if (mbar_try(b, parity)) return true;
     if ((spins & 1023u) == 0) {
       if (*(volatile int *)err) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         atomicExch(err, 1);
         return false;
       }
     }
+  }
+}
+// The same wait on the way out of the kernel, for work this thread has
+// itself put in flight (it completes on its own): bounded, and not cut short
+// by the error flag.
+__device__ __forceinline__ void mbar_wait_drain(uint64_t *b, uint32_t parity, long long limit) {
+  if (mbar_try(b, parity)) return;
+  const long long t0 = clock64();
+  for (uint32_t spins = 1;; ++spins) {
+    if (mbar_try(b, parity)) return;
+    if ((spins & 1023u) == 0 && clock64() - t0 > limit) return;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -273,6 +284,8 @@ struct GemmLaunch {
   float *scratch;      // without a shared accumulator: per-CTA column-major
   int scr_cols;        // accumulators, scr_cols x 256 floats per CTA (L2-resident)
   int *err;
+  long long wait_cycles;  // limit of every bounded wait (SM clocks)
+  int inject;          // test hook: the first accumulator chunk's ready signal is withheld
 };
 
 // The problem that work unit u belongs to, and the unit's index v within it.
@@ -325,7 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *empty = bars + L.nstages;
   uint64_t *tfull = bars + 2 * L.nstages;
   uint64_t *tempty = tfull + 2;
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+  uint64_t *drain = tempty + 2;  // completion of every MMA issued, before TMEM is freed
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -338,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 256);
     }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!group) {
@@ -360,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int st = 0;
       uint32_t ph = 0;
       bool ok = true;
+      int64_t nissued = 0;
       for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
         int64_t v;
         const GemmProblem *p = find_problem(one, two, group, L, u, &v);
@@ -368,13 +384,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row0 = (int)(tile * kTileM);
         const uint32_t tx = xbytes + (uint32_t)p->BN * kStageBytesK;
         for (int64_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(&empty[st], ph ^ 1u, L.err)) { ok = false; break; }
+          if (!mbar_wait(&empty[st], ph ^ 1u, L.err, L.wait_cycles)) { ok = false; break; }
           uint8_t *xs = smem + (size_t)st * sbytes;
           mbar_expect_tx(&full[st], tx);
           tma_load_2d(xs, &p->mapX, &full[st], (int)(kb * BKE), row0, pol_x);
           tma_load_2d(xs + xbytes, &p->mapY, &full[st], (int)(kb * BKE), 0, pol_y);
+          ++nissued;
           if (++st == L.nstages) { st = 0; ph ^= 1u; }
         }
+      }
+      // Every copy issued must land before the CTA exits (one still in
+      // flight would write shared memory the CTA no longer owns).  The c-th
+      // load into stage s completes phase c of full[s]; on the normal path
+      // the MMA warp has waited for all of them, so these return at once.
+      const int64_t rounds = nissued / L.nstages, rem = nissued % L.nstages;
+      for (int s = 0; s < L.nstages; ++s) {
+        const int64_t cnt = rounds + (s < rem ? 1 : 0);
+        if (cnt > 0) mbar_wait_drain(&full[s], (uint32_t)((cnt - 1) & 1), L.wait_cycles);
       }
     }
   } else if (warp == 1) {
@@ -383,6 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int st = 0, buf = 0;
       uint32_t ph = 0, tph = 0;
       bool ok = true;
+      bool withheld = false;
       for (int64_t u = blockIdx.x; u < L.units && ok; u += gridDim.x) {
         int64_t v;
         const GemmProblem *p = find_problem(one, two, group, L, u, &v);
@@ -391,12 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t id = idesc(BF16, 128, p->BN);
         for (int64_t cb0 = kb0; cb0 < kb1 && ok; cb0 += L.chunk_kb) {
           const int64_t cb1 = min(kb1, cb0 + (int64_t)L.chunk_kb);
-          if (!mbar_wait(&tempty[buf], tph ^ 1u, L.err)) { ok = false; break; }
+          if (!mbar_wait(&tempty[buf], tph ^ 1u, L.err, L.wait_cycles)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d0 = tbase + (uint32_t)(buf * 2 * L.BNmax);
           const uint32_t d1 = d0 + (uint32_t)L.BNmax;
           for (int64_t kb = cb0; kb < cb1; ++kb) {
-            if (!mbar_wait(&full[st], ph, L.err)) { ok = false; break; }
+            if (!mbar_wait(&full[st], ph, L.err, L.wait_cycles)) { ok = false; break; }
             tc_fence_after();
             const uint32_t xs = su32(smem + (size_t)st * sbytes);
             const uint32_t ys = xs + xbytes;
@@ -412,7 +439,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (++st == L.nstages) { st = 0; ph ^= 1u; }
           }
           if (!ok) break;
-          mma_commit(&tfull[buf]);
+          if (L.inject && !withheld)
+            withheld = true;  // test hook: the epilogue's wait for this chunk runs out
+          else
+            mma_commit(&tfull[buf]);
           if (++buf == L.nbuf) { buf = 0; tph ^= 1u; }
         }
       }
@@ -447,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 64; ++j) acc[j] = 0.f;
         for (int64_t cb0 = kb0; cb0 < kb1; cb0 += L.chunk_kb) {
-          if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
+          if (!mbar_wait(&tfull[buf], tph, L.err, L.wait_cycles)) { ok = false; break; }
           tc_fence_after();
           const uint32_t taddr =
               tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
@@ -497,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int jj = 0; jj < 32; ++jj) nx[jj] = ld_keep(scol + (size_t)jj * kTileM, pol_s);
           }
         }
-        if (!mbar_wait(&tfull[buf], tph, L.err)) { ok = false; break; }
+        if (!mbar_wait(&tfull[buf], tph, L.err, L.wait_cycles)) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr =
             tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * L.BNmax + half * L.BNmax);
@@ -578,6 +608,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   if (warp == 1) {
+    // every MMA this CTA issued has finished before TMEM is freed: on the
+    // normal path the epilogue has already seen the last one complete; after
+    // a wait ran out, some may still be running
+    if (lane == 0) {
+      mma_commit(drain);
+      mbar_wait_drain(drain, 0u, L.wait_cycles);
+    }
+    __syncwarp();
     tc_fence_after();
     tmem_dealloc(tbase, L.tmem_cols);
   }
@@ -1047,6 +1085,8 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units,
   L->scratch = nullptr;
   L->scr_cols = 0;
   L->err = err;
+  L->wait_cycles = fault::wait_cycles();
+  L->inject = fault::site() == AUNMF_INJECT_TC_WAIT ? 1 : 0;
   return L->nstages >= 2;
 }
 

@@ -38,6 +38,25 @@ def dense_lowrank(m: int, n: int, r: int, seed: int, sigma: float = 0.01, noise:
     return A, Ws, Hs
 
 
+def dense_lowrank_blocked(m: int, n: int, r: int, seed: int, sigma: float = 0.01,
+                          block_rows: int = 4096):
+    """The dense recipe in float64 for sizes whose one-shot draw would need
+    several times A's memory: W* and H* drawn first, then A filled row block
+    by row block (W* H* + |N(0, sigma^2)| per block) from the same
+    generator, so the extra memory is one block.  The numbers differ from
+    ``dense_lowrank``'s for the same seed; the distribution is the same."""
+    g = _rng(seed)
+    Ws = g.random((m, r))
+    Hs = g.random((r, n))
+    A = np.empty((m, n))
+    for r0 in range(0, m, block_rows):
+        r1 = min(m, r0 + block_rows)
+        np.matmul(Ws[r0:r1], Hs, out=A[r0:r1])
+        if sigma > 0:
+            A[r0:r1] += np.abs(g.normal(0.0, sigma, size=(r1 - r0, n)))
+    return A, Ws, Hs
+
+
 def init_factors(m: int, n: int, k: int, seed: int):
     """(W0, H0) uniform on [0, 1), float64; H0 is drawn first so that it does not
     depend on m."""

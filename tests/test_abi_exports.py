@@ -62,3 +62,18 @@ def test_library_loads_without_gpu(libpath):
     L.aunmf_strerror.argtypes = [ctypes.c_int]
     assert L.aunmf_strerror(-1) == b"invalid argument"
     assert L.aunmf_strerror(0) == b"ok"
+
+
+def test_fault_hook_validates_its_arguments_without_a_gpu(libpath):
+    """aunmf_test_inject rejects unknown sites and out-of-range limits and
+    sets nothing then; setting it back to normal needs no device."""
+    import ctypes
+
+    L = ctypes.CDLL(libpath)
+    L.aunmf_test_inject.argtypes = [ctypes.c_int, ctypes.c_double]
+    L.aunmf_test_inject.restype = ctypes.c_int
+    assert L.aunmf_test_inject(4, 0.0) == -1
+    assert L.aunmf_test_inject(-1, 0.0) == -1
+    assert L.aunmf_test_inject(1, float("nan")) == -1
+    assert L.aunmf_test_inject(1, 1e9) == -1
+    assert L.aunmf_test_inject(0, 0.0) == 0

@@ -111,6 +111,41 @@ def test_stop_rule_matches_oracle(ax, small, algo, variant):
     assert info["pgrad_last"] == pytest.approx(full["pgrad"][j], rel=1e-3)
 
 
+def _pgrad_state(A, W, H):
+    return orc.pgrad(W, H, H @ H.T, A @ H.T, W.T @ W, W.T @ A)
+
+
+def test_projected_gradient_at_zero_entries(ax):
+    """The device measure keeps a negative gradient at a zero entry and drops
+    a positive one (reading R10).  info["pgrad_first"] is the measure of
+    (W0, H0).  First the hand case of the oracle pin (sqrt(12), exact in
+    FP32) in both orientations, then a random state with ~40 % of the entries
+    of W0 and H0 zeroed, where the zero entries' negative gradients carry a
+    large share of the measure (checked against the variant that drops
+    them, so the case can tell the two apart)."""
+    H = np.array([[1.0, 0.0], [1.0, 1.0]])
+    A = np.array([[3.0, 0.0], [0.0, 0.0]])
+    W = np.array([[0.0, 1.0], [1.0, 0.0]])
+    for a, w, h in ((A, W, H), (A.T, H.T, W.T)):
+        _, _, _, info = ax.run(dev(a), 2, "mu", 1, dev(w), dev(h), stop_tol=1.0)
+        assert info["pgrad_first"] == pytest.approx(np.sqrt(12.0), rel=1e-6)
+    A, W0, H0 = problem(300, 200, 10, 6, seed=31)
+    g = np.random.default_rng(31)
+    W0[g.random(W0.shape) < 0.4] = 0.0
+    H0[g.random(H0.shape) < 0.4] = 0.0
+    want = _pgrad_state(A, W0, H0)
+    gW = W0 @ (H0 @ H0.T) - A @ H0.T
+    gH = (W0.T @ W0) @ H0 - W0.T @ A
+    dropped = np.sqrt(np.sum(np.where(W0 > 0, gW, 0.0) ** 2) +
+                      np.sum(np.where(H0 > 0, gH, 0.0) ** 2))
+    assert dropped < 0.9 * want
+    # ABPP ignores W0 and starts from W = 0 (Alg. 1 initialises only H)
+    want_abpp = _pgrad_state(A, np.zeros_like(W0), H0)
+    for algo, w in (("mu", want), ("hals", want), ("abpp", want_abpp)):
+        _, _, _, info = ax.run(dev(A), 10, algo, 1, dev(W0), dev(H0), stop_tol=1.0)
+        assert info["pgrad_first"] == pytest.approx(w, rel=1e-4), algo
+
+
 def test_stop_rule_graph_and_eager_agree(ax, small):
     A, W0, H0 = small
     full = orc.nmf_run(A, 10, "hals", 30, W0, H0, track_pgrad=True)

@@ -102,6 +102,35 @@ def test_autograd_function(ax):
     assert (np.abs(host(Hd.grad) - 3.0 * dH_ref) <= 3.0 * th).all()
 
 
+def test_autograd_function_on_a_side_stream(ax):
+    """nmf_loss called under another torch stream runs its kernels on that
+    stream (the handle is rebound to torch's current stream at every call):
+    inputs made on the side stream, loss and gradients read after it, equal
+    bit for bit to the same call on the default stream."""
+    from paper_1609_09154_gb300.autograd import nmf_loss
+
+    A, W, H = problem(2000, 1500, 32, seed=13)
+
+    def grads():
+        Ad = dev(A)
+        Wd = dev(W).requires_grad_(True)
+        Hd = dev(H).requires_grad_(True)
+        loss = nmf_loss(Ad, Wd, Hd)
+        loss.backward()
+        return loss.detach().clone(), Wd.grad.clone(), Hd.grad.clone()
+
+    ref = grads()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        got = grads()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
 def test_loss_mixed_precision(ax, prec):
     A, W, H = problem(700, 520, 50, seed=9)

@@ -11,6 +11,8 @@ Tolerances (from the arithmetic):
   * whole runs in mixed precision: relative residual within 1e-3 of the
     oracle's after 30 iterations from the same start.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -63,6 +65,14 @@ SHAPES = [(300, 200, 10), (517, 389, 50), (1031, 129, 33), (64, 48, 1), (700, 26
           (600, 520, 300), (1500, 1300, 512), (700, 9000, 384)]
 
 
+@functools.lru_cache(maxsize=None)
+def oracle_products(m, n, k):
+    """The oracle's A H^T and W^T A (FP64) for the shape's problem, shared by
+    the TF32 and BF16 cases."""
+    A, W, H = problem(m, n, k, seed=m + n + k)
+    return orc.aht(A, H), orc.wta(A, W)
+
+
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_products_tensor_cores(ax, m, n, k, prec):
@@ -70,8 +80,9 @@ def test_products_tensor_cores(ax, m, n, k, prec):
     Ad = dev(A)
     PW = host(ax.aht(Ad, dev(H), prec=prec))
     PH = host(ax.wta(Ad, dev(W), prec=prec))
-    check(PW, A @ H.T, np.abs(A) @ np.abs(H).T, n, prec)
-    check(PH, W.T @ A, np.abs(W).T @ np.abs(A), m, prec)
+    ref_aht, ref_wta = oracle_products(m, n, k)
+    check(PW, ref_aht, np.abs(A) @ np.abs(H).T, n, prec)
+    check(PH, ref_wta, np.abs(W).T @ np.abs(A), m, prec)
 
 
 @pytest.mark.parametrize("algo,prec", [("hals", "tf32"), ("mu", "bf16"), ("hals", "fp32")])
@@ -104,7 +115,7 @@ def test_products_tensor_cores_padded_lda(ax):
 
     M = aunmf.Matrix(333, 201, Av.data_ptr(), 203, None, None, None, 0)
     PW = host(ax.aht(M, dev(H), prec="tf32"))
-    check(PW, A @ H.T, np.abs(A) @ np.abs(H).T, 201, "tf32")
+    check(PW, orc.aht(A, H), np.abs(A) @ np.abs(H).T, 201, "tf32")
 
 
 def test_tensor_core_products_deterministic(ax):

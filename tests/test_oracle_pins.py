@@ -502,6 +502,34 @@ def test_pgrad_vanishes_at_an_nnls_solution():
     assert np.abs(g[W == 0]).max() > 1e-3
 
 
+def test_pgrad_hand_case_with_zero_entries_of_both_signs():
+    """Hand-derived 2 x 2 case, k = 2, whose factors have zero entries with a
+    negative and with a positive gradient (reading R10: min(0, g) where the
+    entry is 0, g where it is > 0).
+
+    H = [[1, 0], [1, 1]], A = [[3, 0], [0, 0]], W = [[0, 1], [1, 0]]:
+      H H^T = [[1, 1], [1, 2]], A H^T = [[3, 3], [0, 0]],
+      W^T W = I,                 W^T A = [[0, 0], [3, 0]].
+      grad_W = W H H^T - A H^T = [[-2, -1], [1, 1]]
+        W_00 = 0, g = -2 -> -2 (kept: negative at a zero entry)
+        W_01 = 1, g = -1 -> -1;  W_10 = 1, g = 1 -> 1
+        W_11 = 0, g = +1 ->  0 (projected away)           sum of squares 6
+      grad_H = W^T W H - W^T A = [[1, 0], [-2, 1]]
+        H_00 = 1 -> 1, H_01 = 0 with g = 0 -> 0, H_10 = 1 -> -2, H_11 = 1 -> 1
+                                                          sum of squares 6
+    so the measure is sqrt(12).  Dropping the negative gradient at a zero
+    entry (keeping g only where x > 0) gives sqrt(8); keeping max(0, g)
+    there gives sqrt(9); no projection gives sqrt(13).  The transposed
+    problem (A^T, H^T, W^T) has the same measure and sends the W entries
+    through the loop over H, so both loops see both kinds of zero entry."""
+    H = np.array([[1.0, 0.0], [1.0, 1.0]])
+    A = np.array([[3.0, 0.0], [0.0, 0.0]])
+    W = np.array([[0.0, 1.0], [1.0, 0.0]])
+    assert orc.pgrad(W, H, *_products(A, W, H)) == pytest.approx(np.sqrt(12.0), rel=1e-15)
+    assert orc.pgrad(H.T, W.T, *_products(A.T, H.T, W.T)) == pytest.approx(np.sqrt(12.0),
+                                                                           rel=1e-15)
+
+
 def test_stop_rule_stops_at_the_first_iteration_below_tolerance():
     """stop_tol: the run ends after the first iteration whose starting state
     has a projected gradient <= stop_tol times the initial one (reading R10);
