@@ -152,7 +152,12 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
 
 /* Same as aunmf_run with every array in HOST memory (A dense only): copies A,
  * W0, H0 to the device, runs, copies W, H back.  The device copies live in
- * the handle's workspace.  Host buffers registered as pinned transfer faster. */
+ * the handle's workspace.  With opt->prec TF32 or BF16 and A in page-locked
+ * host memory (cudaHostAlloc / cudaHostRegister, e.g. torch's pin_memory),
+ * A is not copied: the run's one-off layout pass reads it over the host link
+ * and writes the rounded device copies that the products stream, so A's
+ * device footprint and staging copy disappear (A must stay valid and
+ * unchanged until the call returns).  Otherwise A is copied first. */
 int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_t lda, int k,
                    int algo, int iters, const float *W0, const float *H0, float *W, float *H,
                    double *relres, const aunmf_options *opt, aunmf_info *info);
@@ -236,6 +241,23 @@ int aunmf_loss_fwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
  * may be NULL to skip that gradient.  All pointers [device]; enqueues only. */
 int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, const float *H,
                    int prec, const float *WtA, const float *grad_out, float *dW, float *dH);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* The gather roof of the sparse products (Sec. 5.2.1 products with a sparse
+ * A): each nonzero of A H^T (W^T A) reads the k-vector of row idx[e] of H^T
+ * (W), a row at a data-dependent address, so the products are bound by how
+ * fast such rows can be gathered, not by their algorithmic HBM bytes.  This
+ * call times nothing itself: it enqueues a kernel that loads row idx[e] of X
+ * for every e < n (the same index stream a product walks: its column or row
+ * indices) with the widest loads and does nothing else; the caller times it
+ * with events on `stream`.  Not a step of the method.
+ *   idx    n indices in [0, rows) [device]; X rows x k, leading dimension ld
+ *          floats (ld % 4 == 0, 16-byte aligned base) [device]
+ *   k      1..64; sink: one float [device] (never written in practice)
+ * Returns AUNMF_OK, AUNMF_E_INVAL or AUNMF_E_CUDA. */
+int aunmf_probe_gather(const int32_t *idx, int64_t n, const float *X, int64_t rows, int k,
+                       int64_t ld, float *sink, void *stream);
 
 /* ---- fault injection for tests ---------------------------------------------- */
 

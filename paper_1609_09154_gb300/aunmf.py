@@ -93,6 +93,7 @@ SIGNATURES = {
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
     "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
     "aunmf_test_inject": [_I, _D],
+    "aunmf_probe_gather": [_P, _I64, _P, _I64, _I, _I64, _P, _P],
     "aunmf_loss_fwd": [_P, _MP, _I, _P, _P, _I, _P, _P],
     "aunmf_run_batched": [_P, _I, _MP, _P, _I, _I, _P, _P, _P, _P, _P, _OP, _IP],
     "aunmf_loss_bwd": [_P, _MP, _I, _P, _P, _I, _P, _P, _P, _P],
@@ -127,6 +128,20 @@ def load(build_if_missing: bool = True):
 
 def strerror(code: int) -> str:
     return load().aunmf_strerror(code).decode()
+
+
+def probe_gather(idx, X, k, sink, stream=None):
+    """aunmf_probe_gather (a measurement, not a step of the method): enqueue
+    the gather-roof kernel that loads row idx[e] of X for every e, on
+    `stream` (default: torch's current stream).  idx: int32 CUDA tensor; X:
+    rows x ld float32 CUDA tensor (ld % 4 == 0) whose first k columns are the
+    factor; sink: one float32 on the device."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().aunmf_probe_gather(_ptr(idx), idx.numel(), _ptr(X), X.shape[0], k, X.stride(0),
+                                   _ptr(sink), ctypes.c_void_p(s.cuda_stream))
+    if rc != OK:
+        raise AunmfError(rc, strerror(rc))
 
 
 def test_inject(site: int, wait_ms: float = 0.0) -> int:

@@ -724,20 +724,46 @@ int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_
                    double *relres, const aunmf_options *opt, aunmf_info *info) {
   if (!h || !A || m < 1 || n < 1 || lda < n || !H0 || !W || !H) return AUNMF_E_INVAL;
   if (algo != AUNMF_ABPP && !W0) return AUNMF_E_INVAL;
+  if (k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   cudaStream_t s = h->stream;
-  ENS(h, h->hA, sizeof(float) * m * n);
+  const int prec = opt ? opt->prec : AUNMF_FP32;
+  // The tensor-core forms read A only in the one-off layout pass, which
+  // writes the rounded device copies the products stream.  When A is in
+  // page-locked host memory that pass reads it over the host link directly
+  // (no staging copy, no device buffer for A); otherwise, and for the FP32
+  // form (whose products read A every iteration), A is copied first.
+  const float *Ad = nullptr;
+  int64_t ldd = n;
+  if (prec == AUNMF_TF32 || prec == AUNMF_BF16) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, A) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr) {
+      Ad = static_cast<const float *>(at.devicePointer);
+      ldd = lda;
+    } else {
+      cudaGetLastError();
+    }
+  }
   ENS(h, h->hW, sizeof(float) * m * k);
   ENS(h, h->hH, sizeof(float) * k * n);
-  float *dA = P<float>(h->hA), *dW = P<float>(h->hW), *dH = P<float>(h->hH);
-  CK(h, cudaMemcpy2DAsync(dA, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
-                          cudaMemcpyHostToDevice, s));
+  float *dW = P<float>(h->hW), *dH = P<float>(h->hH);
+  if (!Ad) {
+    ENS(h, h->hA, sizeof(float) * m * n);
+    float *dA = P<float>(h->hA);
+    if (lda == n)
+      CK(h, cudaMemcpyAsync(dA, A, sizeof(float) * m * n, cudaMemcpyHostToDevice, s));
+    else
+      CK(h, cudaMemcpy2DAsync(dA, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
+                              cudaMemcpyHostToDevice, s));
+    Ad = dA;
+  }
   if (algo != AUNMF_ABPP) CK(h, cudaMemcpyAsync(dW, W0, sizeof(float) * m * k, cudaMemcpyHostToDevice, s));
   CK(h, cudaMemcpyAsync(dH, H0, sizeof(float) * k * n, cudaMemcpyHostToDevice, s));
   aunmf_matrix M{};
   M.m = m;
   M.n = n;
-  M.dense = dA;
-  M.lda = n;
+  M.dense = Ad;
+  M.lda = ldd;
   int rc = aunmf_run(h, &M, k, algo, iters, dW, dH, dW, dH, relres, opt, info);
   if (rc != AUNMF_OK && rc != AUNMF_E_NOCONVERGE) return rc;
   CK(h, cudaMemcpyAsync(W, dW, sizeof(float) * m * k, cudaMemcpyDeviceToHost, s));

@@ -182,3 +182,27 @@ def test_sparse_long_rows_are_split(ax):
     W2, H2, r2, _ = ax.run(M, k, "hals", 10, dev(W0), dev(H0))
     assert np.all(np.abs(r1 - ref["relres"]) <= 1e-6), np.abs(r1 - ref["relres"]).max()
     assert torch.equal(W1, W2) and torch.equal(H1, H2) and np.array_equal(r1, r2)
+
+
+def test_gather_probe_runs_and_checks_its_arguments():
+    """The gather-roof kernel (a measurement, not a step of the method) runs
+    on a product's index stream and rejects a leading dimension that is not
+    a multiple of 4 or a rank above 64, launching nothing then."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1609_09154_gb300 import aunmf
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    idx = torch.randint(0, 5000, (100_003,), device="cuda", dtype=torch.int32, generator=g)
+    X = torch.rand((5000, 52), device="cuda", generator=g)
+    sink = torch.zeros(1, device="cuda")
+    aunmf.probe_gather(idx, X, 50, sink)
+    torch.cuda.synchronize()
+    assert float(sink) == 0.0
+    with pytest.raises(aunmf.AunmfError) as e:
+        aunmf.probe_gather(idx, torch.rand((5000, 50), device="cuda"), 50, sink)
+    assert e.value.code == aunmf.E_INVAL
+    with pytest.raises(aunmf.AunmfError) as e:
+        aunmf.probe_gather(idx, torch.rand((5000, 68), device="cuda"), 65, sink)
+    assert e.value.code == aunmf.E_INVAL

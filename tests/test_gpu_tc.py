@@ -176,3 +176,23 @@ def test_mixed_reported_residual_matches_direct(ax, prec):
     W, H, rel, _ = ax.run(dev(A), k, "hals", 5, dev(W0), dev(H0), prec=prec)
     direct = orc.relres_direct(A, host(W), host(H))
     assert abs(rel[-1] - direct) <= 1e-4, (rel[-1], direct)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_run_host_reads_pinned_a_directly(ax, config_small, prec):
+    """aunmf_run_host with A in page-locked host memory and a tensor-core
+    form: the layout pass reads A over the host link (no staging copy); the
+    result equals the device-buffer run bit for bit (same rounded copies,
+    same kernels), and so does a pageable A (copied first) and a pinned A
+    with padded rows (lda > n)."""
+    A, W0, H0 = config_small
+    f = lambda x: np.ascontiguousarray(x, dtype=np.float32)  # noqa: E731
+    Wd, Hd, rel_d, _ = ax.run(dev(A), 10, "hals", 8, dev(W0), dev(H0), prec=prec)
+    pinned = torch.from_numpy(f(A)).pin_memory()
+    wide = torch.zeros((A.shape[0], A.shape[1] + 4), dtype=torch.float32).pin_memory()
+    wide[:, :A.shape[1]] = pinned
+    for Ah in (pinned.numpy(), f(A), wide.numpy()[:, :A.shape[1]]):
+        Wh, Hh, rel_h, _ = ax.run_host(Ah, 10, "hals", 8, f(W0), f(H0), prec=prec)
+        np.testing.assert_array_equal(rel_h, rel_d)
+        np.testing.assert_array_equal(Wh, Wd.cpu().numpy())
+        np.testing.assert_array_equal(Hh, Hd.cpu().numpy())
