@@ -163,11 +163,16 @@ def dist_setup():
     import torch
     import torch.distributed as dist
 
+    import datetime
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # a replica that dies or never arrives ends the others' next barrier
+        # or reduction with an error after this long, instead of a hang
+        timeout = datetime.timedelta(seconds=float(os.environ.get("AUNMF_PG_TIMEOUT_S", "600")))
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo", timeout=timeout)
     return world, rank, local
 
 

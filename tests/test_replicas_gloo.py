@@ -61,3 +61,45 @@ def test_single_process_needs_no_process_group():
         for k, v in env.items():
             if v is not None:
                 os.environ[k] = v
+
+
+FAILING_WORKER = r"""
+import os, sys, time
+sys.path.insert(0, {root!r})
+import bench
+world, rank, local = bench.dist_setup()
+bench.barrier(world)  # both ranks get here
+if rank == 1:
+    if {mode!r} == "raise":
+        raise RuntimeError("replica 1 fails between steps")
+    time.sleep(60)  # "stall": never reaches the next barrier in time
+t0 = time.time()
+try:
+    bench.barrier(world)
+    print("RESULT no-error", flush=True)
+except Exception as e:
+    print("RESULT peer-failure %.1f %s" % (time.time() - t0, type(e).__name__), flush=True)
+"""
+
+
+def test_a_failed_replica_ends_the_others_barrier_with_an_error():
+    """A replica that raises between steps, or stalls past the process-group
+    timeout, does not leave the others waiting forever: rank 0's next
+    barrier fails with an error well within the test's limit (failure made
+    on the host, as two gloo processes on the CPU)."""
+    for mode in ("raise", "stall"):
+        port = _free_port()
+        procs = []
+        for r in range(2):
+            env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r),
+                       MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="",
+                       AUNMF_PG_TIMEOUT_S="5")
+            procs.append(subprocess.Popen(
+                [sys.executable, "-c", FAILING_WORKER.format(root=ROOT, mode=mode)], env=env,
+                stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+        out0, err0 = procs[0].communicate(timeout=120)
+        procs[1].kill()
+        procs[1].communicate(timeout=30)
+        line = [x for x in out0.splitlines() if x.startswith("RESULT")]
+        assert line and line[0].startswith("RESULT peer-failure"), (mode, out0, err0[-2000:])
+        assert float(line[0].split()[2]) < 60.0
