@@ -60,7 +60,7 @@ struct aunmf_handle {
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   Buf aux;         // printed HALS sweep / projected gradient: partials, barrier, values
   Buf spl, splpart;  // sparse: long-row lists of the CSR and the CSC; their chunk partials
-  int max_gram_blocks = 4 * 152;
+  int max_gram_blocks = 2 * 152;
   int n_dparts = 2 * 152;
 };
 
@@ -493,7 +493,9 @@ int aunmf_create(aunmf_handle **out, void *stream) {
   if (e != cudaSuccess) { int rc = fail_cuda(h, e, "cudaStreamCreate"); delete h; return rc; }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  h->max_gram_blocks = 4 * sms;
+  // Gram partials: one per block of a single resident wave (two 256-thread
+  // blocks per SM); fewer partials also shorten the FP64 reduction
+  h->max_gram_blocks = 2 * sms;
   h->n_dparts = 2 * sms;
   *out = h;
   return AUNMF_OK;

@@ -578,19 +578,20 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
             if (j < k) rsf[j] = rho;
           }
           __syncwarp();
+          // z' = Q rho in plain FP32 with Q's high half: z' only corrects an
+          // error of ~cond u_pair in x, so its own relative error (~2^-24 per
+          // term) leaves the refined x far below FP32 resolution, at a quarter
+          // of the pair form's instructions (the residual rho above is the
+          // part that needs the pairs)
           float zrh[KT], zrl[KT];
 #pragma unroll
           for (int t = 0; t < KT; ++t) {
             const int j = lane + 32 * t;
-            float hi = 0.f, lo = 0.f;
+            float hi = 0.f;
             if (j < k)
-              for (int l = 0; l < k; ++l) {
-                const float rl = rsf[l];
-                two_fma_acc(Qh[l * k + j], rl, hi, lo);
-                lo = fmaf(Ql[l * k + j], rl, lo);
-              }
-            zrh[t] = __fadd_rn(hi, lo);
-            zrl[t] = __fsub_rn(lo, __fsub_rn(zrh[t], hi));
+              for (int l = 0; l < k; ++l) hi = fmaf(Qh[l * k + j], rsf[l], hi);
+            zrh[t] = hi;
+            zrl[t] = 0.f;
           }
 #pragma unroll
           for (int t = 0; t < KT; ++t)

@@ -330,7 +330,11 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
     float *X = side ? b.Ht : b.W;
     for (int64_t row = I.r0 + wib; row < I.r1; row += nwb) {
       bool fnum, fcap;
-      const int n_ex = bpp::bpp_row_fast<KT>(w, R, row, k, X, 1, max_piv, &fnum, &fcap);
+      // problems with k <= 32 take the one-index-per-lane form even in a
+      // launch sized for larger ranks (fewer instructions per exchange)
+      const int n_ex = (KT > 1 && k <= 32)
+                           ? bpp::bpp_row_fast<1>(w, R, row, k, X, 1, max_piv, &fnum, &fcap)
+                           : bpp::bpp_row_fast<KT>(w, R, row, k, X, 1, max_piv, &fnum, &fcap);
       if (lane == 0) b.redo[row] = fnum ? 1 : 0;
       if (!fnum) {
         piv_total += n_ex;

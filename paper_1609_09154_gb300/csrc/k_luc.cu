@@ -282,11 +282,21 @@ __global__ void __launch_bounds__(kTprThreads)
   constexpr int LDT = KP + 1;
   extern __shared__ __align__(16) float smt[];
   float *sGt = smt;  // KP x KP: sGt[i][j] = G[j][i], zero outside k x k
+  // HALS: 1 / G_ii; 0 where G_ii <= 0 (the coordinate is left as it is), -1
+  // where the reciprocal overflows (a subnormal G_ii: divided by it instead)
+  float *sInv = smt + KP * KP;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float *tile = smt + KP * KP + wib * 32 * LDT;
+  float *tile = sInv + KP + wib * 32 * LDT;
   for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) {
     const int i = e / KP, j = e % KP;
     sGt[e] = (i < k && j < k) ? G[j * k + i] : 0.f;
+  }
+  // the HALS step divides by G_ii for every row: one reciprocal per block
+  // instead (the product differs from the quotient by at most an ulp)
+  for (int i = threadIdx.x; i < KP; i += blockDim.x) {
+    const float gii = i < k ? G[i * k + i] : 0.f;
+    const float r = gii > 0.f ? 1.f / gii : 0.f;
+    sInv[i] = isfinite(r) ? r : -1.f;
   }
   __syncthreads();
   const float g = (OP == kOpGrad && gscale) ? *gscale : 1.f;
@@ -309,15 +319,18 @@ __global__ void __launch_bounds__(kTprThreads)
       // kOpHalsUnit: Eq. halsupdate as printed, without the division.
 #pragma unroll
       for (int i = 0; i < KP; ++i) {
-        const float gii = sGt[i * KP + i];
         if (OP == kOpHalsUnit) {
           if (i < k) {
             const float v = x[i] + (t[i] - xg<KP>(x, sGt, i));
             x[i] = v > 0.f ? v : 0.f;
           }
-        } else if (gii > 0.f) {
-          const float v = x[i] + (t[i] - xg<KP>(x, sGt, i)) / gii;
-          x[i] = v > 0.f ? v : 0.f;
+        } else {
+          const float inv = sInv[i];
+          if (inv != 0.f) {
+            const float d = t[i] - xg<KP>(x, sGt, i);
+            const float v = x[i] + (inv > 0.f ? d * inv : d / sGt[i * KP + i]);
+            x[i] = v > 0.f ? v : 0.f;
+          }
         }
       }
 #pragma unroll
@@ -339,7 +352,7 @@ __global__ void __launch_bounds__(kTprThreads)
 template <int KP, int OP>
 cudaError_t launch_tpr(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
                        const float *gscale, float *out, cudaStream_t s) {
-  const size_t smem = sizeof(float) * ((size_t)KP * KP + (size_t)kTprWarps * 32 * (KP + 1));
+  const size_t smem = sizeof(float) * ((size_t)KP * KP + KP + (size_t)kTprWarps * 32 * (KP + 1));
   cudaFuncSetAttribute(k_luc_tpr<KP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // one wave of resident blocks (a second, partial wave would leave most
   // SMs idle for its whole length), each walking its share of row groups

@@ -96,6 +96,24 @@ def test_products_fp32_long_contraction(ax, m, n, k):
     assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
 
 
+def test_products_fp32_padded_rows(ax):
+    """A in a buffer with padded rows (lda = 204 > n = 201): both products
+    take the float4 tile loads (16-byte aligned rows), with K tails (201 and
+    333 are not multiples of the 16-deep K step) and, for W^T A, an output
+    edge (M = 201) whose last group of four rows is partly outside A."""
+    A, W, H = problem(333, 201, 24, seed=5)
+    big = np.zeros((333, 204))
+    big[:, :201] = A
+    Abig = dev(big)
+    from paper_1609_09154_gb300 import aunmf
+
+    M = aunmf.Matrix(333, 201, Abig.data_ptr(), 204, None, None, None, 0)
+    PW = host(ax.aht(M, dev(H)))
+    PH = host(ax.wta(M, dev(W)))
+    assert_product(PW, orc.aht(A, H), np.abs(A) @ np.abs(H).T, 201)
+    assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), 333)
+
+
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_mu_updates(ax, m, n, k):
     A, W, H = problem(m, n, k, seed=m + 2)
