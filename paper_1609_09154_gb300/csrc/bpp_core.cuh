@@ -403,8 +403,12 @@ __device__ __forceinline__ bool solve_mixed(const float *Mh, const float *Ml, in
   return false;
 }
 
-// Solves row `row` of R (rows x k) into X (warm: start from the support of
-// X's row); returns the exchanges, *failed_numeric / *failed_cap.  Each
+// Solves row `row` of R (rows x k) into X (warm 1: start from the support of
+// X's row; warm 2: from the positive entries of the unconstrained solution
+// z = G^{-1} r when G^{-1} is usable (else as warm 1) -- for a first update,
+// whose X (zero, or a random start) says nothing about the solution; warm 0:
+// from the empty passive set); returns the exchanges, *failed_numeric /
+// *failed_cap.  Each
 // lane keeps its entries of r (FP32), x and y (FP32 pairs) and the
 // tolerances (FP32): the exchange rule needs only their signs and
 // magnitudes, and FP64 instructions -- conversions and compares included --
@@ -446,9 +450,38 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
   }
   __syncwarp();
   // z = G^{-1} r (a pair), shared by every exchange of this right-hand side
-  // that takes the Q route; formed on the first such exchange
+  // that takes the Q route; formed on the first such exchange (or first of
+  // all, for warm 2)
   float zh[KT], zl[KT];
   bool have_z = false;
+  auto form_z = [&]() {
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      // z_j = sum_l (Qh + Ql)_lj r_l, r_l an FP32 value
+      const int j = lane + 32 * t;
+      float hi = 0.f, lo = 0.f;
+      if (j < k)
+        for (int l = 0; l < k; ++l) {
+          const float rl = rsf[l];
+          two_fma_acc(Qh[l * k + j], rl, hi, lo);
+          lo = fmaf(Ql[l * k + j], rl, lo);
+        }
+      zh[t] = __fadd_rn(hi, lo);
+      zl[t] = __fsub_rn(lo, __fsub_rn(zh[t], hi));
+    }
+    have_z = true;
+  };
+  if (warm == 2 && have_q) {
+    // the solution is unique (G positive definite), so the starting set
+    // changes only the number of exchanges
+    form_z();
+    any = false;
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      pas[t] = !dead[t] && lane + 32 * t < k && zh[t] > 0.f;
+      any |= pas[t];
+    }
+  }
   int alpha = 3, beta = k + 1, it = 0;
   bool failed_numeric = false, failed_cap = false;
   bool need_solve = __any_sync(0xffffffffu, any);
@@ -500,23 +533,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
       } else {
         // ---- through Q = G^{-1} and z = Q r: the constrained solution has
         // Q_BB y_B = -z_B and x_F = z_F + Q_FB y_B (y_F = 0, x_B = 0)
-        if (!have_z) {
-#pragma unroll
-          for (int t = 0; t < KT; ++t) {
-            // z_j = sum_l (Qh + Ql)_lj r_l, r_l an FP32 value
-            const int j = lane + 32 * t;
-            float hi = 0.f, lo = 0.f;
-            if (j < k)
-              for (int l = 0; l < k; ++l) {
-                const float rl = rsf[l];
-                two_fma_acc(Qh[l * k + j], rl, hi, lo);
-                lo = fmaf(Ql[l * k + j], rl, lo);
-              }
-            zh[t] = __fadd_rn(hi, lo);
-            zl[t] = __fsub_rn(lo, __fsub_rn(zh[t], hi));
-          }
-          have_z = true;
-        }
+        if (!have_z) form_z();
 #pragma unroll
         for (int t = 0; t < KT; ++t)
           if (!pas[t] && lane + 32 * t < k) {

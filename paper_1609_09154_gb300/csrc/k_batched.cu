@@ -318,6 +318,10 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
   long long piv_total = 0, nonconv = 0;
+  // the first iteration starts each solve from the signs of the unconstrained
+  // solution (W = 0 and the random H0 say nothing about the solution), later
+  // ones from the previous iterate's support
+  const int warm = ctr->iter == 0 ? 2 : 1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item I = items[it];
     const BInst &b = P[I.p];
@@ -333,8 +337,8 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
       // problems with k <= 32 take the one-index-per-lane form even in a
       // launch sized for larger ranks (fewer instructions per exchange)
       const int n_ex = (KT > 1 && k <= 32)
-                           ? bpp::bpp_row_fast<1>(w, R, row, k, X, 1, max_piv, &fnum, &fcap)
-                           : bpp::bpp_row_fast<KT>(w, R, row, k, X, 1, max_piv, &fnum, &fcap);
+                           ? bpp::bpp_row_fast<1>(w, R, row, k, X, warm, max_piv, &fnum, &fcap)
+                           : bpp::bpp_row_fast<KT>(w, R, row, k, X, warm, max_piv, &fnum, &fcap);
       if (lane == 0) b.redo[row] = fnum ? 1 : 0;
       if (!fnum) {
         piv_total += n_ex;

@@ -55,6 +55,10 @@ __global__ void __launch_bounds__(32 * kBppWarps, 1)
   const int nwb = blockDim.x >> 5;
   const BppWarp w = bpp_stage(Gd, Qg, q_ok, k, sm, wib);
   __syncthreads();
+  // a run's first iteration (no relres written yet): the previous iterate is
+  // the random start (or W = 0), so the solves start from the signs of the
+  // unconstrained solution instead of its support
+  if (warm == 1 && ctr->iter == 0) warm = 2;
   long long piv_total = 0, nonconv = 0;
   for (int64_t row = (int64_t)blockIdx.x * nwb + wib; row < rows;
        row += (int64_t)gridDim.x * nwb) {
