@@ -448,7 +448,7 @@ def run_ksweep(args):
     clocks = Clocks(local)
     clocks.start()
     rows, launches = [], 0
-    for k in WORKLOADS["ksweep"]["ks"]:
+    for k in (args.ks or WORKLOADS["ksweep"]["ks"]):
         W0, H0 = synth.init_factors_torch(m, n, k, seed=SEED + rank, device=dev)
         W, H = torch.empty_like(W0), torch.empty_like(H0)
         for prec in ("tf32", "bf16"):
@@ -486,7 +486,7 @@ def run_ksweep(args):
             "ms_per_step": world * 1e3 / top["iters_per_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": top["prec"], "data": "synthetic",
             "config": {"workload": f"k sweep: dense {m}x{n} FP32, planted rank {args.rank} + "
-                                   f"|N(0,0.01^2)|, HALS at k in {WORKLOADS['ksweep']['ks']}, "
+                                   f"|N(0,0.01^2)|, HALS at k in {args.ks or WORKLOADS['ksweep']['ks']}, "
                                    f"TF32 and BF16 products; value at k={top['k']} "
                                    f"{top['prec'].upper()}",
                        "m": m, "n": n, "k": top["k"], "algo": "hals", "prec": top["prec"],
@@ -817,6 +817,8 @@ def main():
                     help="skip the MU / HALS / ABPP runs on the same input")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the comparison with the FP64 oracle on the small configuration")
+    ap.add_argument("--ks", type=lambda v: [int(x) for x in v.split(",")], default=None,
+                    help="--workload ksweep: ranks to run (comma-separated; default: the full sweep)")
     ap.add_argument("--oracle-full", action="store_true",
                     help="--impl reference: time the oracle on the whole workload, unscaled")
     args = ap.parse_args()

@@ -32,7 +32,7 @@
 // drain shorter than a chunk.
 // Without the hi/lo split (k > 64) each output has one TMEM column; the
 // first 64 sums of a row stay in registers and the rest go to shared memory
-// or, when they do not fit beside two pipeline stages (BN > ~160), to a
+// or, when they do not fit beside three pipeline stages (BN > 128), to a
 // per-CTA column-major accumulator in global memory that stays in L2.  MMA N
 // is at most 256: a wider product (k <= 512) runs as two column blocks in
 // one launch.
@@ -1043,8 +1043,8 @@ bool all_pair(const GemmProblem &p) { return p.pair && p.BN <= 128; }
 // Shape of a launch whose problems have at most BNmax MMA columns and whose
 // shared accumulator rows need at most accw floats.  The FP32 accumulator
 // (256 x (accw | 1) floats, odd stride so that the 32 rows a warp touches
-// fall in 32 banks) goes to shared memory when two pipeline stages still fit
-// beside it; otherwise chunks are added into P in global memory
+// fall in 32 banks) goes to shared memory when three pipeline stages still
+// fit beside it; otherwise chunks are added into P in global memory
 // (L2-resident), with longer chunks.  TMEM holds nbuf chunk accumulators of
 // 2 x BNmax columns; the drain reads up to BN rounded up to 64 columns past
 // the start of the last half, which must stay inside the allocation.
@@ -1069,7 +1069,10 @@ bool launch_shape(GemmLaunch *L, int BNmax, int accw, bool pairs, int64_t units,
     L->acc_ld = 0;
     L->nstages = (int)(budget / sbytes);
     L->chunk_kb = kChunkKBReg;
-  } else if (acc + 2 * sbytes <= budget) {
+  } else if (acc + 3 * sbytes <= budget) {
+    // the shared accumulator only with at least three pipeline stages beside
+    // it: with two, each stage's TMA latency stalls the MMAs (k = 320, two
+    // blocks of 160: 8.34 -> 6.11 ms per TF32 product on the L2 scratch path)
     L->acc_ld = ld;
     L->nstages = (int)((budget - acc) / sbytes);
     L->chunk_kb = kChunkKB;
