@@ -1,7 +1,7 @@
 // k_luc.cu -- local update computations (LUC) for MU and HALS.
 //
 // Both factors are held as row-major "rows x k" matrices (W, and H^T for H),
-// so one kernel serves both updates.  For k <= 64 one thread owns one row
+// so one kernel serves both updates.  For k <= 64 two threads share one row
 // (k_luc_tpr).  Above, one warp owns one row; lane l holds the entries
 // j = l, l + 32, ... (KT = ceil(k / 32) per lane, rounded up to 12 or 16
 // above 256; k <= 512), and the k x k
@@ -16,7 +16,7 @@ namespace {
 constexpr int kLucThreads = 256;
 constexpr int kLucWarps = kLucThreads / kWarp;
 constexpr int kSmemGramMaxK = 108;  // 108*108*4 B < 48 KB default dynamic limit
-constexpr int kTprMaxK = 64;        // thread-per-row forms up to this k
+constexpr int kTprMaxK = 64;        // two-threads-per-row forms up to this k
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -208,17 +208,21 @@ __global__ void k_hals_scale_gram(float *__restrict__ GW, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Thread-per-row forms for k <= 64 (the same three updates).  A warp takes 32
-// consecutive rows, copies them into a shared tile (row stride KP + 1, odd:
-// the lanes' rows fall in 32 banks) with asynchronous 4-byte copies, all in
-// flight at once, and each thread then keeps its row in registers and walks
-// the k coordinates itself: no shuffle per coordinate.  The k x k matrix is
-// staged transposed and zero-padded to KP, so (x G)_i = sum_j x_j G_ji reads
-// row i of the staged copy with 16-byte broadcast loads; padded coordinates
-// have G_ii = 0 and stay 0.
+// Two-threads-per-row forms for k <= 64 (the same three updates).  A warp
+// takes 16 consecutive rows, copies them into a shared tile (row stride KP +
+// 1, odd) with asynchronous 4-byte copies, all in flight at once; lanes 2r
+// and 2r + 1 then share row r, each keeping one half of it (KH = KP / 2
+// entries) in registers.  For coordinate i each thread forms its half of (x
+// G)_i, one shuffle adds the halves, and the thread that holds x_i updates
+// it: no shuffle per entry, half the dependent FMA chain per coordinate and
+// half the registers of a thread per row, so twice the warps stay resident.
+// The k x k matrix is staged transposed and zero-padded to KP, so (x G)_i =
+// sum_j x_j G_ji reads row i of the staged copy with 16-byte loads; padded
+// coordinates have G_ii = 0 and stay 0.
 enum LucOp { kOpMu = 0, kOpHals = 1, kOpGrad = 2, kOpHalsUnit = 3 };
 constexpr int kTprThreads = 256;
 constexpr int kTprWarps = kTprThreads / kWarp;
+constexpr int kTprRows = 16;  // rows per warp
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -231,14 +235,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// tile rows 0..31 = src rows 0..nr-1 (row length k, contiguous), zeros
+// tile rows 0..kTprRows-1 = src rows 0..nr-1 (row length k, contiguous), zeros
 // elsewhere; the warp's copies complete before it returns.
 template <int KP>
 __device__ __forceinline__ void tile_in(const float *__restrict__ src, int nr, int k, float *tile,
                                         int lane) {
   constexpr int LDT = KP + 1;
-#pragma unroll 8
-  for (int rr = 0; rr < 32; ++rr)
+#pragma unroll 4
+  for (int rr = 0; rr < kTprRows; ++rr)
 #pragma unroll
     for (int c = lane; c < KP; c += 32) {
       const bool v = rr < nr && c < k;
@@ -258,13 +262,14 @@ __device__ __forceinline__ void tile_out(float *__restrict__ dst, int nr, int k,
   __syncwarp();
 }
 
-// (x G)_i for the thread's row x (KP registers) and the staged G^T.
-template <int KP>
-__device__ __forceinline__ float xg(const float (&x)[KP], const float *sGt, int i) {
-  const float4 *g4 = reinterpret_cast<const float4 *>(sGt + i * KP);
+// This thread's half of (x G)_i: x its KH entries (columns h*KH ...), the
+// staged G^T row i from the same column.
+template <int KH>
+__device__ __forceinline__ float xg_half(const float (&x)[KH], const float *gi) {
+  const float4 *g4 = reinterpret_cast<const float4 *>(gi);
   float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
 #pragma unroll
-  for (int q = 0; q < KP / 4; ++q) {
+  for (int q = 0; q < KH / 4; ++q) {
     const float4 g = g4[q];
     d0 = fmaf(x[4 * q], g.x, d0);
     d1 = fmaf(x[4 * q + 1], g.y, d1);
@@ -280,13 +285,16 @@ __global__ void __launch_bounds__(kTprThreads)
               int64_t rows, int k, float eps, const float *__restrict__ gscale,
               float *__restrict__ out) {
   constexpr int LDT = KP + 1;
+  constexpr int KH = KP / 2;
+  static_assert(KH % 4 == 0, "half rows of whole 16-byte groups");
   extern __shared__ __align__(16) float smt[];
   float *sGt = smt;  // KP x KP: sGt[i][j] = G[j][i], zero outside k x k
   // HALS: 1 / G_ii; 0 where G_ii <= 0 (the coordinate is left as it is), -1
   // where the reciprocal overflows (a subnormal G_ii: divided by it instead)
   float *sInv = smt + KP * KP;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float *tile = sInv + KP + wib * 32 * LDT;
+  const int h = lane & 1, rw = lane >> 1;  // half of row rw of the warp's rows
+  float *tile = sInv + KP + wib * kTprRows * LDT;
   for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) {
     const int i = e / KP, j = e % KP;
     sGt[e] = (i < k && j < k) ? G[j * k + i] : 0.f;
@@ -301,16 +309,16 @@ __global__ void __launch_bounds__(kTprThreads)
   __syncthreads();
   const float g = (OP == kOpGrad && gscale) ? *gscale : 1.f;
   float *dst = OP == kOpGrad ? out : X;
-  const int64_t groups = (rows + 31) / 32;
+  const int64_t groups = (rows + kTprRows - 1) / kTprRows;
   for (int64_t grp = (int64_t)blockIdx.x * kTprWarps + wib; grp < groups;
        grp += (int64_t)gridDim.x * kTprWarps) {
-    const int64_t r0 = grp * 32;
-    const int nr = (int)min((int64_t)32, rows - r0);
+    const int64_t r0 = grp * kTprRows;
+    const int nr = (int)min((int64_t)kTprRows, rows - r0);
     tile_in<KP>(X + r0 * k, nr, k, tile, lane);
-    float x[KP];
-    float *t = tile + lane * LDT;
+    float x[KH];
+    float *t = tile + rw * LDT + h * KH;  // this thread's half of its row
 #pragma unroll
-    for (int j = 0; j < KP; ++j) x[j] = t[j];
+    for (int j = 0; j < KH; ++j) x[j] = t[j];
     __syncwarp();
     tile_in<KP>(P + r0 * k, nr, k, tile, lane);
     if constexpr (OP == kOpHals || OP == kOpHalsUnit) {
@@ -319,30 +327,31 @@ __global__ void __launch_bounds__(kTprThreads)
       // kOpHalsUnit: Eq. halsupdate as printed, without the division.
 #pragma unroll
       for (int i = 0; i < KP; ++i) {
-        if (OP == kOpHalsUnit) {
-          if (i < k) {
-            const float v = x[i] + (t[i] - xg<KP>(x, sGt, i));
-            x[i] = v > 0.f ? v : 0.f;
-          }
-        } else {
-          const float inv = sInv[i];
-          if (inv != 0.f) {
-            const float d = t[i] - xg<KP>(x, sGt, i);
-            const float v = x[i] + (inv > 0.f ? d * inv : d / sGt[i * KP + i]);
-            x[i] = v > 0.f ? v : 0.f;
+        const int own = i / KH, il = i % KH;  // the half that holds x_i
+        const float inv = sInv[i];
+        if (OP == kOpHalsUnit ? i < k : inv != 0.f) {
+          float d = xg_half<KH>(x, sGt + i * KP + h * KH);
+          d += __shfl_xor_sync(0xffffffffu, d, 1);
+          if (h == own) {
+            const float c = t[il] - d;
+            const float v = x[il] + (OP == kOpHalsUnit ? c
+                                                        : (inv > 0.f ? c * inv : c / sGt[i * KP + i]));
+            x[il] = v > 0.f ? v : 0.f;
           }
         }
       }
 #pragma unroll
-      for (int j = 0; j < KP; ++j) t[j] = x[j];
+      for (int j = 0; j < KH; ++j) t[j] = x[j];
     } else {
       // every entry from the old x: MU x_j p_j / ((x G)_j + eps), gradient
       // g ((x G)_j - p_j); the result replaces p_j in the tile
 #pragma unroll
       for (int j = 0; j < KP; ++j) {
         if (j >= k) break;
-        const float d = xg<KP>(x, sGt, j);
-        t[j] = OP == kOpMu ? x[j] * t[j] / (d + eps) : g * (d - t[j]);
+        float d = xg_half<KH>(x, sGt + j * KP + h * KH);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        const int own = j / KH, jl = j % KH;
+        if (h == own) t[jl] = OP == kOpMu ? x[jl] * t[jl] / (d + eps) : g * (d - t[jl]);
       }
     }
     tile_out<KP>(dst + r0 * k, nr, k, tile, lane);
@@ -352,7 +361,8 @@ __global__ void __launch_bounds__(kTprThreads)
 template <int KP, int OP>
 cudaError_t launch_tpr(float *X, const float *P, const float *G, int64_t rows, int k, float eps,
                        const float *gscale, float *out, cudaStream_t s) {
-  const size_t smem = sizeof(float) * ((size_t)KP * KP + KP + (size_t)kTprWarps * 32 * (KP + 1));
+  const size_t smem =
+      sizeof(float) * ((size_t)KP * KP + KP + (size_t)kTprWarps * kTprRows * (KP + 1));
   cudaFuncSetAttribute(k_luc_tpr<KP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // one wave of resident blocks (a second, partial wave would leave most
   // SMs idle for its whole length), each walking its share of row groups
@@ -364,7 +374,7 @@ cudaError_t launch_tpr(float *X, const float *P, const float *G, int64_t rows, i
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_luc_tpr<KP, OP>, kTprThreads, smem);
     resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 152);
   }
-  const int64_t groups = (rows + 31) / 32;
+  const int64_t groups = (rows + kTprRows - 1) / kTprRows;
   int64_t nb = (groups + kTprWarps - 1) / kTprWarps;
   if (nb > resident) nb = resident;
   k_luc_tpr<KP, OP><<<(unsigned)nb, kTprThreads, smem, s>>>(X, P, G, rows, k, eps, gscale, out);
