@@ -218,7 +218,8 @@ int aunmf_nls_bpp(aunmf_handle *h, const float *G, const float *R, int64_t nrhs,
                   int max_pivots, int64_t *pivots, int64_t *nonconv);
 
 /* ||A - W H||_F / ||A||_F (Sec. 6.2) by the trace expansion with FP64
- * reductions; W m x k, H k x n [device]; *relres [host].  Synchronises. */
+ * reductions; W m x k, H k x n [device]; *relres [host].  Synchronises.
+ * Returns AUNMF_E_TIMEOUT if a bounded device wait of the product gave up. */
 int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const float *H, int k,
                  double *relres);
 
@@ -262,11 +263,13 @@ int aunmf_probe_gather(const int32_t *idx, int64_t n, const float *X, int64_t ro
 /* ---- fault injection for tests ---------------------------------------------- */
 
 /* Every wait of a kernel on another thread, warp or block of the same launch
- * (the tensor-core products' mbarrier waits, the printed HALS sweep's grid
- * barrier) is bounded: after ~2 s it raises the call's device error flag,
- * the kernel drains the copies and tensor-core operations it has in flight,
- * frees its tensor memory and returns, and the call returns AUNMF_E_TIMEOUT
- * with the device context still usable.  aunmf_test_inject() makes those
+ * (the tensor-core products' and the FP32 products' mbarrier waits, the
+ * printed HALS sweep's grid barrier) is bounded: after ~2 s it raises the
+ * call's device error flag, the kernel drains the copies and tensor-core
+ * operations it has in flight, frees its tensor memory and returns, and the
+ * call returns AUNMF_E_TIMEOUT with the device context still usable (the
+ * step-level entry points, which do not synchronise, leave their output
+ * unwritten and report nothing).  aunmf_test_inject() makes those
  * paths run on purpose, for tests, without faulting or hanging the GPU: it
  * withholds one signal so that a bounded wait runs out.  The setting is
  * process-wide and applies to every launch made after the call, until it is
@@ -282,6 +285,10 @@ int aunmf_probe_gather(const int32_t *idx, int64_t n, const float *X, int64_t ro
  *            AUNMF_INJECT_NOMEM         every workspace allocation fails with
  *              AUNMF_E_NOMEM (cudaMalloc is not called); buffers a handle
  *              already holds stay usable
+ *            AUNMF_INJECT_SIMT_WAIT     FP32 dense products with k > 32
+ *              (aunmf_run, aunmf_relres, aunmf_aht / aunmf_wta in FP32): the
+ *              producer warp never signals that the first stage of A is in
+ *              shared memory, so the consumer warps' wait runs out
  *   wait_ms  limit of the bounded waits while `site` is set, in milliseconds
  *            of the device's maximum SM clock (<= 0: the default ~2 s);
  *            ignored for AUNMF_INJECT_NONE, which restores the default.
@@ -291,6 +298,7 @@ int aunmf_probe_gather(const int32_t *idx, int64_t n, const float *X, int64_t ro
 #define AUNMF_INJECT_TC_WAIT 1
 #define AUNMF_INJECT_GRID_BARRIER 2
 #define AUNMF_INJECT_NOMEM 3
+#define AUNMF_INJECT_SIMT_WAIT 4
 int aunmf_test_inject(int site, double wait_ms);
 
 /* ---- fixed-memory variant ------------------------------------------------ */

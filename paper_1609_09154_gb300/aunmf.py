@@ -23,7 +23,7 @@ K_MAX, BPP_K_MAX = 512, 64
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_NOCONVERGE, E_TIMEOUT, E_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6, -7)
-INJECT_NONE, INJECT_TC_WAIT, INJECT_GRID_BARRIER, INJECT_NOMEM = 0, 1, 2, 3
+INJECT_NONE, INJECT_TC_WAIT, INJECT_GRID_BARRIER, INJECT_NOMEM, INJECT_SIMT_WAIT = 0, 1, 2, 3, 4
 
 
 class AunmfError(RuntimeError):

@@ -223,7 +223,7 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhAht);
-    return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, c.parts, s);
+    return launch_aht_simt(A->dense, A->m, A->n, A->lda, c.Ht, c.k, c.PW, c.parts, c.err, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
   const bool split = use_split(c.k);
@@ -257,7 +257,7 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhWta);
-    return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, c.parts, s);
+    return launch_wta_simt(A->dense, A->m, A->n, A->lda, c.W, c.k, c.PHt, c.parts, c.err, s);
   }
   const bool bf = c.prec == AUNMF_BF16;
   const bool split = use_split(c.k);
@@ -524,7 +524,7 @@ int aunmf_destroy(aunmf_handle *h) {
 const char *aunmf_last_cuda_error(aunmf_handle *h) { return h ? h->cuda_err.c_str() : ""; }
 
 int aunmf_test_inject(int site, double wait_ms) {
-  if (site < AUNMF_INJECT_NONE || site > AUNMF_INJECT_NOMEM) return AUNMF_E_INVAL;
+  if (site < AUNMF_INJECT_NONE || site > AUNMF_INJECT_SIMT_WAIT) return AUNMF_E_INVAL;
   if (!(wait_ms <= 60000.0)) return AUNMF_E_INVAL;  // also rejects NaN
   long long cycles = fault::kDefaultWaitCycles;
   if (site != AUNMF_INJECT_NONE && wait_ms > 0.0) {
@@ -636,6 +636,9 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   } else if (A->dense) {
     ENS(h, h->parts, simt_parts_bytes(m > n ? m : n, k));
     c.parts = P<float>(h->parts);
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), s));
   }
   if (!A->dense) {
     int prc = prepare_sparse(h, c, s);
@@ -812,8 +815,11 @@ int aunmf_aht(aunmf_handle *h, const aunmf_matrix *A, const float *H, int k, int
     int rc = prepare_tc(h, c, h->stream);
     if (rc != AUNMF_OK) return rc;
   } else if (A->dense) {
-    ENS(h, h->parts, simt_parts_bytes(A->m, k));
+    ENS(h, h->parts, simt_parts_bytes(A->m > A->n ? A->m : A->n, k));
     c.parts = P<float>(h->parts);
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), h->stream));
   }
   CK(h, product_aht(h, c, h->stream));
   return AUNMF_OK;
@@ -839,8 +845,11 @@ int aunmf_wta(aunmf_handle *h, const aunmf_matrix *A, const float *W, int k, int
     int rc = prepare_tc(h, c, h->stream);
     if (rc != AUNMF_OK) return rc;
   } else if (A->dense) {
-    ENS(h, h->parts, simt_parts_bytes(n, k));
+    ENS(h, h->parts, simt_parts_bytes(A->m > n ? A->m : n, k));
     c.parts = P<float>(h->parts);
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), h->stream));
   }
   if (!A->dense) {
     int rc = prepare_sparse(h, c, h->stream);
@@ -982,8 +991,11 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   CK(h, launch_transpose(H, k, n, Ht, s));
   if (A->dense) {
     CK(h, launch_norm2(A->dense, m, n, A->lda, dp, h->n_dparts, P<double>(h->n2a), s));
-    ENS(h, h->parts, simt_parts_bytes(n, k));
-    CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, P<float>(h->parts), s));
+    ENS(h, h->parts, simt_parts_bytes(A->m > n ? A->m : n, k));
+    ENS(h, h->err, sizeof(int));
+    CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
+    CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, P<float>(h->parts), P<int>(h->err),
+                          s));
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, dp, h->n_dparts, P<double>(h->n2a), s));
     RunCtx c{};
@@ -997,9 +1009,11 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   CK(h, launch_relres(PHt, Ht, n * (int64_t)k, P<float>(h->GW), P<float>(h->GH), k,
                       P<double>(h->n2a), dp, h->n_dparts, nullptr, P<DevCounters>(h->ctr),
                       P<double>(h->last), s));
+  int herr = 0;
+  if (A->dense) CK(h, cudaMemcpyAsync(&herr, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaMemcpyAsync(relres, h->last.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
-  return AUNMF_OK;
+  return herr ? AUNMF_E_TIMEOUT : AUNMF_OK;
 }
 
 // ------------------------------------------------------------ loss / gradient
@@ -1043,6 +1057,9 @@ int loss_setup(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W, co
     CK(h, launch_norm2(A->dense, m, n, A->lda, c.dpart, h->n_dparts, c.n2a, s));
     ENS(h, h->parts, simt_parts_bytes(m > n ? m : n, k));
     c.parts = P<float>(h->parts);
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), s));
   } else {
     CK(h, launch_norm2_vec(A->val, A->nnz, c.dpart, h->n_dparts, c.n2a, s));
   }

@@ -70,13 +70,15 @@ cudaError_t launch_widen(const float *G32, int k, double *G64, cudaStream_t s);
 // SIMT FP32 products.
 //   aht: P_W (m x k, ld k) = A (m x n, lda) * Ht (n x k, ld k)
 //   wta: P_Ht (n x k, ld k) = A^T (n x m) * W (m x k, ld k)
-// parts: simt_parts_bytes(rows of the output, k) bytes for K-split partials
-// (null: no split).
+// parts: simt_parts_bytes(max(m, n), k) bytes for the K-split partials and a
+// copy of the factor with rows padded to 4 floats (null: no split, and the
+// TMA-fed form is not used).  err: the device error flag that the TMA-fed
+// form's bounded waits raise (null: that form is not used).
 size_t simt_parts_bytes(int64_t rows, int k);
 cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *Ht,
-                            int k, float *P, float *parts, cudaStream_t s);
+                            int k, float *P, float *parts, int *err, cudaStream_t s);
 cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
-                            int k, float *P, float *parts, cudaStream_t s);
+                            int k, float *P, float *parts, int *err, cudaStream_t s);
 
 // Sparse products (FP32).  P_W (m x k) = A Ht from CSR; P_Ht (n x k) = A^T W
 // from the CSC form (colptr[n+1], rowidx[nnz], cval[nnz]) built by

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace aunmf {
 
@@ -505,18 +506,254 @@ __global__ void __launch_bounds__(256, AUNMF_SIMT_MINB)
   }
 }
 
+// ---------------------------------------------------------------- TMA-fed form
+// k_gemm_simt_tma: the same product and the same compensated summation as
+// k_gemm_simt, for N > 32 (column tiles of 64) when A's rows are 16-byte
+// aligned.  A's tiles and the fixed factor's 16 x 64 tiles arrive by TMA in
+// a seven-stage shared-memory ring with mbarriers (full: one arrival + the
+// copies' bytes; empty: all 256 threads).  The factor is read from a copy
+// whose rows are padded to a multiple of 4 floats (TMA needs 16-byte row
+// strides; N = 50 floats is not one); staging its tiles with 4-byte
+// asynchronous copies instead measured 3x slower than the whole product
+// should take (11.5 ms for the copies alone at 96,000 x 64,000).  Eight warps compute, 8 x 8 outputs per thread (256 x 64 per
+// block, one block per SM), four 16-byte fragment loads per 64 FFMAs, with
+// the running sums in registers (two warps per SM sub-partition may hold
+// up to 255 registers each; a ninth, producer-only warp would cap them at
+// 168).  Thread 0 also fills the ring: steps 0 .. 6 first, then at the top
+// of step s it waits until every thread has released the stage read at
+// step s - 1 (warp 0 trails the others, so the wait is short) and issues
+// the two copies of step s + 6 into it.
+//   Thread (ty, tx), ty = 0..31, tx = 0..7 (a warp: 4 ty x 8 tx): columns
+//   tx*4 + {0..3} and 32 + tx*4 + {0..3}; rows ty + 32 i (AK) or
+//   ty*4 + {0..3} and 128 + ty*4 + {0..3} (!AK).
+// AK (A K-contiguous): the tile is 256 rows of 16 K (64 bytes), copied with
+// the 64-byte swizzle (16-byte chunk c of row r lands at chunk
+// c ^ ((r >> 1) & 3)), so the four rows a warp reads at once (ty .. ty+3)
+// sit in four different bank groups.  !AK: 16 K-rows of 256 (one kilobyte):
+// a warp's four row fragments are consecutive.  Either way a warp's 16-byte
+// loads of the factor tile read 8 consecutive chunks, with no bank conflict.
+// Slab sums are folded every 128 K into the running sums with Kahan's
+// corrections, which sit in shared memory (one row per thread).  Every wait
+// is bounded; on expiry the kernel raises *err, writes nothing and returns
+// (thread 0 first waits, bounded, for the copies it has in flight).  The K
+// steps of a split are whole (its length is a multiple of 128); rows and
+// columns past either matrix are zero-filled by the copies.
+constexpr int kTBM = 256, kTBN = 64, kTBK = 16, kTStages = 7;
+constexpr int kTThreads = 256;
+constexpr int kTSlabSteps = 8;  // K steps per compensated slab (128 K, as k_gemm_simt)
+constexpr int kTLdc = 68;       // floats per thread row of corrections (64 + pad)
+constexpr size_t kTStageA = (size_t)kTBM * kTBK * 4, kTStageB = (size_t)kTBK * kTBN * 4;
+constexpr size_t kTSmem = 1024 + kTStages * (kTStageA + kTStageB) +
+                          (size_t)kTThreads * kTLdc * 4 + 2 * kTStages * 8;
+
+template <bool AK>
+__global__ void __launch_bounds__(kTThreads, 1)
+    k_gemm_simt_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    int64_t M, int64_t K, int N, float *__restrict__ C, int ldc, int64_t kchunk,
+                    int *err, long long limit, int inject) {
+  // inject (test hook): thread 0 never arrives on the first stage's barrier,
+  // so every thread's bounded wait runs out
+  using namespace aunmf::ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  float *sA = reinterpret_cast<float *>(smem);
+  float *sB = reinterpret_cast<float *>(smem + kTStages * kTStageA);
+  float *corr = reinterpret_cast<float *>(smem + kTStages * (kTStageA + kTStageB));
+  uint64_t *full = reinterpret_cast<uint64_t *>(corr + kTThreads * kTLdc);
+  uint64_t *empty = full + kTStages;
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.x * kTBM;
+  const int n0 = blockIdx.y * kTBN;
+  const int64_t kz0 = (int64_t)blockIdx.z * kchunk, kz1 = min(K, kz0 + kchunk);
+  const int nsteps = kz1 > kz0 ? (int)((kz1 - kz0 + kTBK - 1) / kTBK) : 0;
+  const bool producer = tid < 32;
+  if (tid == 0) {
+    for (int st = 0; st < kTStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kTThreads);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // thread 0: fill stage st with step s
+  const uint64_t pol_a = policy_evict_first(), pol_b = policy_evict_last();  // A streams once
+  int issued = 0;
+  auto fill = [&](int s) {
+    const int st = s % kTStages;
+    const int k0 = (int)(kz0 + (int64_t)s * kTBK);
+    const uint32_t bytes = (uint32_t)(kTStageA + kTStageB);
+    if (inject && s == 0)
+      mbar_expect_tx_only(&full[st], bytes);
+    else
+      mbar_expect_tx(&full[st], bytes);
+    if (AK)
+      tma_load_2d(sA + (size_t)st * kTBM * kTBK, &mapA, &full[st], k0, (int)m0, pol_a);
+    else
+      tma_load_2d(sA + (size_t)st * kTBM * kTBK, &mapA, &full[st], (int)m0, k0, pol_a);
+    tma_load_2d(sB + (size_t)st * kTBK * kTBN, &mapB, &full[st], n0, k0, pol_b);
+    ++issued;
+  };
+  if (tid == 0)  // every stage starts empty: steps 0 .. kTStages - 1
+    for (int s = 0; s < kTStages && s < nsteps; ++s) fill(s);
+
+  const int w = tid >> 5, l = tid & 31, tx = l & 7, ty = w * 4 + (l >> 3);
+  float *kc = corr + (size_t)tid * kTLdc;  // Kahan corrections of the 64 sums
+#pragma unroll
+  for (int e = 0; e < 64; e += 4) *reinterpret_cast<float4 *>(kc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+  float acc[8][8], hi[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = hi[i][j] = 0.f;
+  auto fold = [&]() {  // hi += acc with Kahan's compensation; acc = 0
+#pragma unroll
+    for (int e4 = 0; e4 < 64; e4 += 4) {
+      float4 cv = *reinterpret_cast<const float4 *>(kc + e4);
+      float *c = &cv.x;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e4 + u, i = e >> 3, j = e & 7;
+        const float y = acc[i][j] - c[u];
+        const float t = hi[i][j] + y;
+        c[u] = (t - hi[i][j]) - y;
+        hi[i][j] = t;
+        acc[i][j] = 0.f;
+      }
+      *reinterpret_cast<float4 *>(kc + e4) = cv;
+    }
+  };
+  auto fma8x8 = [&](const float (&a)[8], const float4 b0, const float4 b1) {
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  };
+  // AK: rows ty + 32 i share their swizzle (r >> 1) & 3 (32 i leaves those bits alone)
+  const int sw = (ty >> 1) & 3;
+
+  bool ok = true;
+  int slab = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    const int st = s % kTStages;
+    if (producer && s >= 1 && s - 1 + kTStages < nsteps) {
+      // refill the stage read at step s - 1 (use (s - 1) / kTStages of it)
+      const int sp = s - 1;
+      int okp = 1;
+      if (tid == 0)
+        okp = mbar_wait(&empty[sp % kTStages], (uint32_t)(sp / kTStages) & 1u, err, limit) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, okp, 0)) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) fill(sp + kTStages);
+    }
+    if (!mbar_wait(&full[st], (uint32_t)(s / kTStages) & 1u, err, limit)) {
+      ok = false;
+      break;
+    }
+    const float *a = sA + (size_t)st * kTBM * kTBK;
+    const float *b = sB + (size_t)st * kTBK * kTBN + tx * 4;
+    if (AK) {  // a: [256 rows][16 K], 64-byte swizzle
+#pragma unroll
+      for (int kq = 0; kq < kTBK / 4; ++kq) {
+        float4 av[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          av[i] = *reinterpret_cast<const float4 *>(a + (ty + 32 * i) * kTBK + ((kq ^ sw) << 2));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float *br = b + (kq * 4 + u) * kTBN;
+          const float4 b0 = *reinterpret_cast<const float4 *>(br);
+          const float4 b1 = *reinterpret_cast<const float4 *>(br + 32);
+          float af[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) af[i] = (&av[i].x)[u];
+          fma8x8(af, b0, b1);
+        }
+      }
+    } else {  // a: [16 K][256 rows]
+#pragma unroll
+      for (int kk = 0; kk < kTBK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(a + kk * kTBM + ty * 4);
+        const float4 a1 = *reinterpret_cast<const float4 *>(a + kk * kTBM + 128 + ty * 4);
+        const float *br = b + kk * kTBN;
+        const float4 b0 = *reinterpret_cast<const float4 *>(br);
+        const float4 b1 = *reinterpret_cast<const float4 *>(br + 32);
+        const float af[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        fma8x8(af, b0, b1);
+      }
+    }
+    mbar_arrive(&empty[st]);
+    if (++slab == kTSlabSteps || s + 1 == nsteps) {
+      fold();
+      slab = 0;
+    }
+  }
+  if (tid == 0) {
+    // the copies thread 0 has put in flight land before the block exits
+    for (int st = 0; st < kTStages && st < issued; ++st) {
+      const int cnt = (issued - st + kTStages - 1) / kTStages;
+      mbar_wait_drain(&full[st], (uint32_t)(cnt - 1) & 1u, limit);
+    }
+  }
+  if (!ok) return;
+  C += (int64_t)blockIdx.z * M * ldc;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gm = m0 + (AK ? ty + 32 * i : (i < 4 ? ty * 4 + i : 128 + ty * 4 + i - 4));
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 32 + tx * 4 + j - 4);
+      if (gn < N) C[gm * ldc + gn] = hi[i][j] - kc[i * 8 + j];
+    }
+  }
+}
+
+// Tensor map of A's tiles for k_gemm_simt_tma: AK, a box of 16 K x 256 rows
+// over A (M x K, ld lda), 64-byte swizzle; !AK, 256 rows x 16 K over A
+// stored K x M, no swizzle.  FP32, zero fill outside the matrix.
+// Tensor map of the factor's tiles: 64 columns x 16 K rows over the padded
+// copy (K x N, ld ldp), no swizzle, zero fill past N and K.
+bool simt_factor_map(CUtensorMap *map, const float *Bp, int64_t K, int N, int ldp) {
+  ptx::EncodeTiledFn fn = ptx::encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)K};
+  cuuint64_t strides[1] = {(cuuint64_t)ldp * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kTBN, (cuuint32_t)kTBK};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(Bp), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool simt_map(CUtensorMap *map, const float *A, int64_t lda, int64_t M, int64_t K, bool AK) {
+  ptx::EncodeTiledFn fn = ptx::encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(AK ? K : M), (cuuint64_t)(AK ? M : K)};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)(AK ? kTBK : kTBM), (cuuint32_t)(AK ? kTBM : kTBK)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(A), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            AK ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BM, int BN>
 constexpr size_t simt_kahan_bytes() {
   return sizeof(float) * 256 * 2 * ((BM / 16) * (BN / 16) + 1);
 }
 
 // K splits: the smallest S in 1..4 whose block count fills the resident
-// slots (2 blocks per SM) most evenly, each split at least 8 slabs long.
-int simt_splits(int64_t tiles, int64_t K) {
+// slots (`per_sm` blocks per SM) most evenly, each split at least 8 slabs long.
+int simt_splits(int64_t tiles, int64_t K, int per_sm) {
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t slots = 2LL * (sms > 0 ? sms : 148);
+  const int64_t slots = (int64_t)per_sm * (sms > 0 ? sms : 148);
   int best = 1;
   double best_eff = 0.0;
   for (int S = 1; S <= 4; ++S) {
@@ -540,16 +777,43 @@ __global__ void k_sum_parts(const float *__restrict__ parts, int S, int64_t len,
 
 template <bool AK>
 cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const float *B, int N,
-                      float *C, float *parts, cudaStream_t s) {
+                      float *C, float *parts, int *err, cudaStream_t s) {
   constexpr int BM = AUNMF_SIMT_BM, BK = 16, SLAB = 128;
+  const int vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
+  // TMA-fed form: N > 32, 16-byte aligned rows, coordinates within int32
+  // (parts holds the split partials, then the factor's padded copy)
+  CUtensorMap mapA, mapB;
+  const int ldp = (N + 3) & ~3;
+  float *Bp = parts ? parts + ((4 * M * (int64_t)N + 63) & ~63LL) : nullptr;
+  if (N > 32 && vec && err && parts && M < (1LL << 31) && K < (1LL << 31) &&
+      simt_map(&mapA, A, lda, M, K, AK) && simt_factor_map(&mapB, Bp, K, N, ldp)) {
+    const unsigned gx = (unsigned)((M + kTBM - 1) / kTBM), gy = (unsigned)((N + kTBN - 1) / kTBN);
+    const int S = simt_splits((int64_t)gx * gy, K, 1);
+    const int64_t kchunk = ((K + S - 1) / S + SLAB - 1) / SLAB * SLAB;
+    cudaError_t e = launch_copy2d(B, N, Bp, ldp, K, N, s);
+    if (e != cudaSuccess) return e;
+    auto kern = k_gemm_simt_tma<AK>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    kern<<<dim3(gx, gy, (unsigned)S), kTThreads, kTSmem, s>>>(
+        mapA, mapB, M, K, N, S > 1 ? parts : C, N, kchunk, err, fault::wait_cycles(),
+        fault::site() == AUNMF_INJECT_SIMT_WAIT ? 1 : 0);
+    g_launches += 1;
+    if (S > 1) {
+      const int64_t len = M * (int64_t)N;
+      int64_t nb = (len + 255) / 256;
+      if (nb > 152 * 16) nb = 152 * 16;
+      k_sum_parts<<<(unsigned)nb, 256, 0, s>>>(parts, S, len, C);
+      g_launches += 1;
+    }
+    return cudaGetLastError();
+  }
   const unsigned gx = (unsigned)((M + BM - 1) / BM);
   const int BN = N <= 16 ? 16 : (N <= 32 ? 32 : 64);
   const unsigned gy = (unsigned)((N + BN - 1) / BN);
-  const int S = parts ? simt_splits((int64_t)gx * gy, K) : 1;
+  const int S = parts ? simt_splits((int64_t)gx * gy, K, 2) : 1;
   const int64_t kchunk = ((K + S - 1) / S + SLAB - 1) / SLAB * SLAB;
   float *out = S > 1 ? parts : C;
   const dim3 grid(gx, gy, (unsigned)S);
-  const int vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
   auto go = [&](auto kern, size_t sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<grid, 256, sm, s>>>(A, lda, M, K, B, N, N, out, N, kchunk, vec);
@@ -572,16 +836,18 @@ cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const f
 }  // namespace
 
 cudaError_t launch_aht_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *Ht,
-                            int k, float *P, float *parts, cudaStream_t s) {
-  return gemm_simt<true>(A, lda, m, n, Ht, k, P, parts, s);
+                            int k, float *P, float *parts, int *err, cudaStream_t s) {
+  return gemm_simt<true>(A, lda, m, n, Ht, k, P, parts, err, s);
 }
 
 cudaError_t launch_wta_simt(const float *A, int64_t m, int64_t n, int64_t lda, const float *W,
-                            int k, float *P, float *parts, cudaStream_t s) {
-  return gemm_simt<false>(A, lda, n, m, W, k, P, parts, s);
+                            int k, float *P, float *parts, int *err, cudaStream_t s) {
+  return gemm_simt<false>(A, lda, n, m, W, k, P, parts, err, s);
 }
 
-size_t simt_parts_bytes(int64_t rows, int k) { return sizeof(float) * 4 * (size_t)rows * k; }
+size_t simt_parts_bytes(int64_t rows, int k) {
+  return sizeof(float) * (((4 * (size_t)rows * k + 63) & ~(size_t)63) + (size_t)rows * ((k + 3) & ~3));
+}
 
 // ------------------------------------------------------------------ transpose
 namespace {

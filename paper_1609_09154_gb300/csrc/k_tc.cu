@@ -49,6 +49,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 #include "tc.cuh"
 
 namespace aunmf {
@@ -85,75 +86,8 @@ constexpr int kChunkKBLong = 8 * AUNMF_TC_CHUNK_KB;
 constexpr int kChunkKBScratch = 16 * AUNMF_TC_CHUNK_KB;
 
 // ------------------------------------------------------------------ PTX
-__device__ __forceinline__ uint32_t su32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase of parity `parity`; false on expiry after
-// `limit` SM clocks (or once another thread has raised the error flag).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err, long long limit) {
-  if (mbar_try(b, parity)) return true;
-  const long long t0 = clock64();
-  for (uint32_t spins = 1;; ++spins) {
-    if (mbar_try(b, parity)) return true;
-    if ((spins & 1023u) == 0) {
-      if (*(volatile int *)err) return false;
-      if (clock64() - t0 > limit) {
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-// The same wait on the way out of the kernel, for work this thread has
-// itself put in flight (it completes on its own): bounded, and not cut short
-// by the error flag.
-__device__ __forceinline__ void mbar_wait_drain(uint64_t *b, uint32_t parity, long long limit) {
-  if (mbar_try(b, parity)) return;
-  const long long t0 = clock64();
-  for (uint32_t spins = 1;; ++spins) {
-    if (mbar_try(b, parity)) return;
-    if ((spins & 1023u) == 0 && clock64() - t0 > limit) return;
-  }
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
-      "l"(map), "r"(su32(bar)), "r"(c0), "r"(c1), "l"(policy)
-      : "memory");
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_normal() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
+using namespace aunmf::ptx;
+
 // Scratch sums: kept in L2 (evict last) against the stream of X tiles.
 __device__ __forceinline__ float ld_keep(const float *p, uint64_t pol) {
   float v;
@@ -162,11 +96,6 @@ __device__ __forceinline__ float ld_keep(const float *p, uint64_t pol) {
 }
 __device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -851,24 +780,6 @@ __global__ void k_round_copy(const float *__restrict__ in, int64_t rows, int64_t
 }
 
 // ------------------------------------------------------------------ host
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 // 2-D tensor map over a row-major rows x cols matrix (leading dimension ld,
 // elements) with a box of box_cols (128 bytes) x box_rows, 128 B swizzle.
 bool make_map(CUtensorMap *map, const void *base, bool bf16, int64_t rows, int64_t cols,

@@ -72,7 +72,7 @@ def test_fault_hook_validates_its_arguments_without_a_gpu(libpath):
     L = ctypes.CDLL(libpath)
     L.aunmf_test_inject.argtypes = [ctypes.c_int, ctypes.c_double]
     L.aunmf_test_inject.restype = ctypes.c_int
-    assert L.aunmf_test_inject(4, 0.0) == -1
+    assert L.aunmf_test_inject(5, 0.0) == -1
     assert L.aunmf_test_inject(-1, 0.0) == -1
     assert L.aunmf_test_inject(1, float("nan")) == -1
     assert L.aunmf_test_inject(1, 1e9) == -1

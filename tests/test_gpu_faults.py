@@ -7,6 +7,9 @@ aunmf_test_inject withholds one signal so that a bounded device wait runs out
     kernel waits for its own copies and MMAs in flight, frees its tensor
     memory and returns, and aunmf_run / aunmf_run_batched return
     AUNMF_E_TIMEOUT;
+  * the FP32 product's producer warp never signals that the first stage of A
+    is in shared memory, so the consumer warps' mbarrier wait runs out;
+    aunmf_run and aunmf_relres return AUNMF_E_TIMEOUT;
   * block 0 of the printed HALS sweep never arrives at the first grid
     barrier, and every block's bounded wait gives up;
   * workspace allocations fail (cudaMalloc is not called): AUNMF_E_NOMEM.
@@ -75,6 +78,23 @@ def test_tensor_core_wait_runs_out_then_handle_recovers(lib, small, use_graph):
         assert lib.test_inject(lib.INJECT_NONE) == lib.OK
     W, H, rel, _ = h.run(Ad, 10, "hals", 6, dev(W0), dev(H0), prec="tf32", use_graph=use_graph)
     assert np.abs(rel - ref["hals"]).max() <= 1e-3
+    h.close()
+
+
+def test_fp32_product_wait_runs_out_then_handle_recovers(lib):
+    # k = 40 > 32: the FP32 products take the TMA-fed form
+    A, W0, H0 = problem(1200, 900, 40, seed=77)
+    ref = orc.nmf_run(A, 40, "hals", 3, W0, H0)["relres"]
+    h = lib.Handle()
+    Ad = dev(A)
+    assert lib.test_inject(lib.INJECT_SIMT_WAIT, WAIT_MS) == lib.OK
+    try:
+        _expect(lib, lib.E_TIMEOUT, lambda: h.run(Ad, 40, "hals", 3, dev(W0), dev(H0)))
+        _expect(lib, lib.E_TIMEOUT, lambda: h.relres(Ad, dev(W0), dev(H0)))
+    finally:
+        assert lib.test_inject(lib.INJECT_NONE) == lib.OK
+    W, H, rel, _ = h.run(Ad, 40, "hals", 3, dev(W0), dev(H0))
+    assert np.abs(rel - ref).max() <= 1e-6
     h.close()
 
 

@@ -96,12 +96,15 @@ def test_products_fp32_long_contraction(ax, m, n, k):
     assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
 
 
-def test_products_fp32_padded_rows(ax):
-    """A in a buffer with padded rows (lda = 204 > n = 201): both products
-    take the float4 tile loads (16-byte aligned rows), with K tails (201 and
-    333 are not multiples of the 16-deep K step) and, for W^T A, an output
-    edge (M = 201) whose last group of four rows is partly outside A."""
-    A, W, H = problem(333, 201, 24, seed=5)
+@pytest.mark.parametrize("k", [24, 50])
+def test_products_fp32_padded_rows(ax, k):
+    """A in a buffer with padded rows (lda = 204 > n = 201), with K tails (201
+    and 333 are not multiples of the 16-deep K step).  k = 24: the register-
+    staged form takes the float4 tile loads (16-byte aligned rows), and for
+    W^T A an output edge (M = 201) whose last group of four rows is partly
+    outside A.  k = 50: the TMA-fed form, whose tensor map strides by lda and
+    zero-fills past the matrix's n (not lda) columns and m rows."""
+    A, W, H = problem(333, 201, k, seed=5)
     big = np.zeros((333, 204))
     big[:, :201] = A
     Abig = dev(big)
