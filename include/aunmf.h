@@ -83,6 +83,18 @@ typedef struct {
   int hals_variant;   /* HALS: 0 = exact coordinate steps, normalisation compensated in H;
                          1 = Eq. halsupdate as printed (see aunmf_run) */
   double stop_tol;    /* > 0: stop on the projected gradient (see aunmf_run); 0 = off */
+  int validate;       /* 1: before the run, check that A >= 0 and finite (Sec. 2 poses NMF
+                         for a nonnegative A), that a CSR A is well formed (rowptr from 0
+                         to nnz and nondecreasing; column indices in [0, n) and increasing
+                         within a row), and that W0 (MU, HALS) and H0 are >= 0 and finite;
+                         any violation returns AUNMF_E_INVAL before other kernels read the
+                         input.  Costs one pass over A (over the host link for a pinned
+                         host A); 0 = the caller vouches for its input. */
+  int bpp_cold_start; /* ABPP: 1 = every BPP solve starts from x = 0 (all indices active);
+                         0 = from the previous iterate's support, the first iteration from
+                         the signs of the unconstrained solution.  Each subproblem has one
+                         solution when its Gram is positive definite, so both reach the
+                         same x (to rounding); warm starts take fewer exchanges. */
 } aunmf_options;
 
 /* Per-call report, filled when the pointer is non-NULL. */

@@ -51,6 +51,7 @@ class Options(ctypes.Structure):
         ("prec", ctypes.c_int), ("mu_eps", ctypes.c_double), ("bpp_max_pivots", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
         ("hals_variant", ctypes.c_int), ("stop_tol", ctypes.c_double),
+        ("validate", ctypes.c_int), ("bpp_cold_start", ctypes.c_int),
     ]
 
 
@@ -221,11 +222,13 @@ class Handle:
     # ---------------------------------------------------------- whole runs
     def run(self, A, k, algo, iters, W0, H0, *, prec="fp32", mu_eps=0.0, bpp_max_pivots=0,
             use_graph=True, profile=False, out=None, allow_noconverge=False, hals_variant=0,
-            stop_tol=0.0):
+            stop_tol=0.0, validate=False, bpp_cold_start=False):
         """Alg. 1 on device tensors.  A: dense (m x n) tensor or a Matrix
         (e.g. from csr_matrix).  hals_variant 1: Eq. halsupdate as printed;
-        stop_tol > 0: stop on the projected gradient.  Returns (W, H, relres
-        ndarray of info["iters_done"] entries, info dict)."""
+        stop_tol > 0: stop on the projected gradient; validate: check A, W0,
+        H0 (and a CSR's structure) first; bpp_cold_start: every BPP solve
+        from x = 0.  Returns (W, H, relres ndarray of info["iters_done"]
+        entries, info dict)."""
         torch = _torch()
         M = A if isinstance(A, Matrix) else dense_matrix(A)
         algo = ALGOS[algo] if isinstance(algo, str) else algo
@@ -239,7 +242,7 @@ class Handle:
             W, H = out
         rel = np.zeros(max(iters, 1), dtype=np.float64)
         opt = Options(prec, mu_eps, bpp_max_pivots, int(use_graph), int(profile),
-                      int(hals_variant), float(stop_tol))
+                      int(hals_variant), float(stop_tol), int(validate), int(bpp_cold_start))
         info = Info()
         rc = self._lib.aunmf_run(self._h, ctypes.byref(M), k, algo, iters, _ptr(W0), _ptr(H0),
                                  _ptr(W), _ptr(H), rel.ctypes.data_as(ctypes.c_void_p),
@@ -250,7 +253,7 @@ class Handle:
         return result
 
     def run_batched(self, As, ks, iters, H0s, *, prec="tf32", use_graph=True, bpp_max_pivots=0,
-                    allow_noconverge=False):
+                    allow_noconverge=False, validate=False, bpp_cold_start=False):
         """ABPP on many problems at once (lists of dense CUDA tensors A_p, ranks
         k_p, initial H0_p).  Returns (Ws, Hs, relres ndarray count x iters, info)."""
         torch = _torch()
@@ -265,7 +268,8 @@ class Handle:
         parr = lambda ts: (ctypes.c_void_p * count)(*[t.data_ptr() for t in ts])  # noqa: E731
         rel = np.zeros((count, max(iters, 1)), dtype=np.float64)
         prec = PRECS[prec] if isinstance(prec, str) else prec
-        opt = Options(prec, 0.0, bpp_max_pivots, int(use_graph), 0)
+        opt = Options(prec, 0.0, bpp_max_pivots, int(use_graph), 0, 0, 0.0, int(validate),
+                      int(bpp_cold_start))
         info = Info()
         rc = self._lib.aunmf_run_batched(self._h, count, mats, karr, ABPP, iters, None,
                                          parr(H0s), parr(Ws), parr(Hs),
@@ -276,7 +280,7 @@ class Handle:
         return result
 
     def run_host(self, A, k, algo, iters, W0, H0, *, prec="fp32", use_graph=True,
-                 profile=False, W=None, H=None):
+                 profile=False, W=None, H=None, validate=False):
         """Alg. 1 with host (numpy float32) arrays; copies happen inside."""
         A = np.ascontiguousarray(A, dtype=np.float32) if not isinstance(A, np.ndarray) else A
         m, n = A.shape
@@ -285,7 +289,7 @@ class Handle:
         W = np.empty((m, k), np.float32) if W is None else W
         H = np.empty((k, n), np.float32) if H is None else H
         rel = np.zeros(max(iters, 1), dtype=np.float64)
-        opt = Options(prec, 0.0, 0, int(use_graph), int(profile))
+        opt = Options(prec, 0.0, 0, int(use_graph), int(profile), 0, 0.0, int(validate))
         info = Info()
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None  # noqa: E731
         rc = self._lib.aunmf_run_host(self._h, vp(A), m, n, A.strides[0] // 4, k, algo, iters,

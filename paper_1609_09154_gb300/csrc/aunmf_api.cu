@@ -543,6 +543,27 @@ int aunmf_test_inject(int site, double wait_ms) {
   return AUNMF_OK;
 }
 
+// aunmf_options.validate: A >= 0 and finite (and, for a CSR, a well-formed
+// structure), W0 and H0 >= 0 and finite, checked before any other kernel
+// reads them (Sec. 2 poses NMF for A >= 0; the updates of Sec. 4 keep the
+// factors nonnegative only from a nonnegative start).  W0 may be null.
+static int validate_inputs(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W0,
+                           const float *H0, cudaStream_t s) {
+  ENS(h, h->err, sizeof(int));
+  int *flag = P<int>(h->err);
+  CK(h, cudaMemsetAsync(flag, 0, sizeof(int), s));
+  if (A->dense)
+    CK(h, launch_validate_dense(A->dense, A->m, A->n, A->lda, flag, s));
+  else
+    CK(h, launch_validate_csr(A->rowptr, A->colidx, A->val, A->m, A->n, A->nnz, flag, s));
+  if (W0) CK(h, launch_validate_vec(W0, A->m * (int64_t)k, kValidateFactors, flag, s));
+  if (H0) CK(h, launch_validate_vec(H0, (int64_t)k * A->n, kValidateFactors, flag, s));
+  int hf = 0;
+  CK(h, cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  return hf ? AUNMF_E_INVAL : AUNMF_OK;
+}
+
 int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
               const float *W0, const float *H0, float *W, float *H, double *relres,
               const aunmf_options *opt, aunmf_info *info) {
@@ -553,6 +574,10 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
   if (opt) o = *opt;
   const int64_t m = A->m, n = A->n;
   cudaStream_t s = h->stream;
+  if (o.validate) {
+    rc = validate_inputs(h, A, k, algo == AUNMF_ABPP ? nullptr : W0, H0, s);
+    if (rc != AUNMF_OK) return rc;
+  }
 
   ENS(h, h->Ht, sizeof(float) * n * k);
   ENS(h, h->PW, sizeof(float) * m * k);
@@ -570,7 +595,7 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
 
   RunCtx c{};
   c.A = A;
-  c.warm = 1;
+  c.warm = o.bpp_cold_start ? 0 : 1;
   c.bppq = h->bppq.p;
   c.k = k;
   c.algo = algo;
@@ -1198,7 +1223,14 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
   }
   if (tc::check(1, 1, 1, 1, o.prec, nullptr) != AUNMF_OK) return AUNMF_E_UNSUPPORTED;
   cudaStream_t s = h->stream;
+  if (o.validate) {
+    for (int p = 0; p < count; ++p) {
+      const int rc = validate_inputs(h, &A[p], k[p], nullptr, H0[p], s);
+      if (rc != AUNMF_OK) return rc;
+    }
+  }
   const int max_piv_opt = o.bpp_max_pivots;
+  const int bpp_cold = o.bpp_cold_start ? 1 : 0;
   constexpr int64_t kGramChunk = 256, kDotChunk = 16384;
 
   // ---- arena layout
@@ -1387,7 +1419,8 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     if ((e = tc::launch_gemm_group(D(pl.o_pa), pl.probs_aht.data(), count, pl.units_aht,
                                    pl.bn_aht, bf, err, st)) != cudaSuccess)
       return e;
-    return batched::launch_bpp(I, rw, nrw, count, 0, pl.kmax, max_piv, ctr, tile.first, st);
+    return batched::launch_bpp(I, rw, nrw, count, 0, pl.kmax, max_piv, bpp_cold, ctr, tile.first,
+                               st);
   };
   auto h_half = [&](cudaStream_t st, const batched::BInst *I, const batched::Item *rh, int nrh) {
     cudaError_t e;
@@ -1400,7 +1433,8 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     if ((e = tc::launch_gemm_group(D(pl.o_pw), pl.probs_wta.data(), count, pl.units_wta,
                                    pl.bn_wta, bf, err, st)) != cudaSuccess)
       return e;
-    if ((e = batched::launch_bpp(I, rh, nrh, count, 1, pl.kmax, max_piv, ctr, tile.first, st)) !=
+    if ((e = batched::launch_bpp(I, rh, nrh, count, 1, pl.kmax, max_piv, bpp_cold, ctr, tile.first,
+                                 st)) !=
         cudaSuccess)
       return e;
     if ((e = batched::launch_gram(I, reinterpret_cast<const batched::Item *>(D(pl.o_gh)),

@@ -53,8 +53,9 @@ cudaError_t launch_split_transpose(const BInst *P, const int64_t *tile_prefix, i
                                    int64_t tiles, int side, bool bf16, cudaStream_t s);
 cudaError_t launch_gram(const BInst *P, const Item *items, int nitems, int count, int side,
                         cudaStream_t s);
+// cold: every solve starts from x = 0 (aunmf_options.bpp_cold_start)
 cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count, int side,
-                       int kmax, int max_piv, DevCounters *ctr, int wpb, cudaStream_t s);
+                       int kmax, int max_piv, int cold, DevCounters *ctr, int wpb, cudaStream_t s);
 int bpp_max_warps(int kmax);
 cudaError_t launch_relres(const BInst *P, const Item *items, int nitems, int count,
                           DevCounters *ctr, int iters, cudaStream_t s);

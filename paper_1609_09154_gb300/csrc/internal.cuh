@@ -25,6 +25,18 @@ int site();
 long long wait_cycles();
 }  // namespace fault
 
+// Optional input checks (aunmf_options.validate): each ORs its bit into
+// *flag.  Values: an entry of A negative, NaN or infinite; structure: a CSR
+// row pointer out of order or range, or a column index out of [0, n) or not
+// increasing within its row; factors: an entry of W0 or H0 negative, NaN or
+// infinite.
+constexpr int kValidateValues = 1, kValidateStructure = 2, kValidateFactors = 4;
+cudaError_t launch_validate_dense(const float *A, int64_t m, int64_t n, int64_t lda, int *flag,
+                                  cudaStream_t s);
+cudaError_t launch_validate_vec(const float *v, int64_t len, int bit, int *flag, cudaStream_t s);
+cudaError_t launch_validate_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                                int64_t m, int64_t n, int64_t nnz, int *flag, cudaStream_t s);
+
 // Device-side error/diagnostic counters, one block of int64 in the workspace.
 struct DevCounters {
   long long bpp_pivots;

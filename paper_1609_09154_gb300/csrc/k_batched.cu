@@ -313,15 +313,15 @@ __global__ void g_inv_check(const BInst *__restrict__ P, int side) {
 template <int KT>
 __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
     g_bpp(const BInst *__restrict__ P, const Item *__restrict__ items, int nitems, int side,
-          int max_piv, DevCounters *ctr) {
+          int max_piv, int cold, DevCounters *ctr) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
   long long piv_total = 0, nonconv = 0;
   // the first iteration starts each solve from the signs of the unconstrained
   // solution (W = 0 and the random H0 say nothing about the solution), later
-  // ones from the previous iterate's support
-  const int warm = ctr->iter == 0 ? 2 : 1;
+  // ones from the previous iterate's support; cold: every solve from x = 0
+  const int warm = cold ? 0 : (ctr->iter == 0 ? 2 : 1);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item I = items[it];
     const BInst &b = P[I.p];
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
 template <int KT>
 __global__ void __launch_bounds__(256)
     g_bpp_direct(const BInst *__restrict__ P, const Item *__restrict__ items, int nitems,
-                 int side, int max_piv, DevCounters *ctr) {
+                 int side, int max_piv, int cold, DevCounters *ctr) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nwb = blockDim.x >> 5;
@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(256)
     for (int64_t row = I.r0 + wib; row < I.r1; row += nwb) {
       if (!b.redo[row]) continue;
       bool fnum, fcap;
-      const int n_ex = bpp::bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, 1, max_piv, &fnum, &fcap);
+      const int n_ex = bpp::bpp_row_direct<KT>(G, L, v, rs, Fl, R, row, k, X, cold ? 0 : 1, max_piv,
+                                                    &fnum, &fcap);
       piv_total += n_ex;
       nonconv += fcap;
       numeric += fnum;
@@ -511,7 +512,7 @@ cudaError_t launch_gram(const BInst *P, const Item *items, int nitems, int count
 }
 
 cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count, int side,
-                       int kmax, int max_piv, DevCounters *ctr, int wpb, cudaStream_t s) {
+                       int kmax, int max_piv, int cold, DevCounters *ctr, int wpb, cudaStream_t s) {
   const size_t chol_smem = sizeof(double) * (size_t)kmax * kmax;
   cudaFuncSetAttribute(g_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
   g_chol<<<count, 256, chol_smem, s>>>(P, side);
@@ -526,14 +527,14 @@ cudaError_t launch_bpp(const BInst *P, const Item *items, int nitems, int count,
   const size_t fb_smem = sizeof(double) * ((size_t)kmax * kmax + (size_t)fbw * fb_warp);
   if (kmax <= 32) {
     cudaFuncSetAttribute(g_bpp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    g_bpp<1><<<grid, 32 * wpb, smem, s>>>(P, items, nitems, side, max_piv, ctr);
+    g_bpp<1><<<grid, 32 * wpb, smem, s>>>(P, items, nitems, side, max_piv, cold, ctr);
     cudaFuncSetAttribute(g_bpp_direct<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem);
-    g_bpp_direct<1><<<grid, 32 * fbw, fb_smem, s>>>(P, items, nitems, side, max_piv, ctr);
+    g_bpp_direct<1><<<grid, 32 * fbw, fb_smem, s>>>(P, items, nitems, side, max_piv, cold, ctr);
   } else {
     cudaFuncSetAttribute(g_bpp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    g_bpp<2><<<grid, 32 * wpb, smem, s>>>(P, items, nitems, side, max_piv, ctr);
+    g_bpp<2><<<grid, 32 * wpb, smem, s>>>(P, items, nitems, side, max_piv, cold, ctr);
     cudaFuncSetAttribute(g_bpp_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem);
-    g_bpp_direct<2><<<grid, 32 * fbw, fb_smem, s>>>(P, items, nitems, side, max_piv, ctr);
+    g_bpp_direct<2><<<grid, 32 * fbw, fb_smem, s>>>(P, items, nitems, side, max_piv, cold, ctr);
   }
   g_launches += 5;
   return cudaGetLastError();

@@ -77,3 +77,36 @@ def test_fault_hook_validates_its_arguments_without_a_gpu(libpath):
     assert L.aunmf_test_inject(1, float("nan")) == -1
     assert L.aunmf_test_inject(1, 1e9) == -1
     assert L.aunmf_test_inject(0, 0.0) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of aunmf_matrix, aunmf_options and aunmf_info have
+    the C structs' size and field offsets (a C program compiled against
+    include/aunmf.h prints them)."""
+    import ctypes
+    import shutil
+
+    from paper_1609_09154_gb300 import aunmf
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"aunmf_matrix": aunmf.Matrix, "aunmf_options": aunmf.Options, "aunmf_info": aunmf.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "aunmf.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
