@@ -272,6 +272,27 @@ int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
 int aunmf_probe_gather(const int32_t *idx, int64_t n, const float *X, int64_t rows, int k,
                        int64_t ld, float *sink, void *stream);
 
+/* ---- checked build -------------------------------------------------------- */
+
+/* The library also builds as libaunmf_check.so (compiled with -DAUNMF_CHECK;
+ * paper_1609_09154_gb300/build.py, build(check=True)), the stand-in for a
+ * memory checker: device code tests each index it takes from data (CSR /
+ * CSC structure, sorted positions, BPP index lists, batched work items,
+ * TMA coordinates) and, where one is out of range, records the site and
+ * skips the access instead of faulting.  aunmf_check_status() synchronises
+ * the device, stores in *site the first site recorded since the last call
+ * (0 = none, else an AUNMF_CHECK_* code) and clears the record.  The normal
+ * build compiles no checks: *site = -1, and no device call is made.
+ * Returns AUNMF_OK, or AUNMF_E_INVAL for a null site.  The paper has no
+ * counterpart; this is test support of the library. */
+#define AUNMF_CHECK_SPMM_COLUMN 1  /* SpMM: a gathered row index outside the factor */
+#define AUNMF_CHECK_SPMM_RANGE 2   /* SpMM: a row's nonzero range outside [0, nnz] */
+#define AUNMF_CHECK_CSC 3          /* CSR -> CSC: a position or column outside its array */
+#define AUNMF_CHECK_BPP_LIST 4     /* BPP: a passive / active list position outside [0, k) */
+#define AUNMF_CHECK_BATCHED_ITEM 5 /* batched: a work item's rows outside its problem */
+#define AUNMF_CHECK_TMA_COORD 6    /* TMA: a copy coordinate negative or not 16-byte aligned */
+int aunmf_check_status(int *site);
+
 /* ---- fault injection for tests ---------------------------------------------- */
 
 /* Every wait of a kernel on another thread, warp or block of the same launch

@@ -94,6 +94,7 @@ SIGNATURES = {
     "aunmf_relres": [_P, _MP, _P, _P, _I, ctypes.POINTER(_D)],
     "aunmf_gram_w_noalloc": [_P, _I64, _I, _P, _P],
     "aunmf_test_inject": [_I, _D],
+    "aunmf_check_status": [_P],
     "aunmf_probe_gather": [_P, _I64, _P, _I64, _I, _I64, _P, _P],
     "aunmf_loss_fwd": [_P, _MP, _I, _P, _P, _I, _P, _P],
     "aunmf_run_batched": [_P, _I, _MP, _P, _I, _I, _P, _P, _P, _P, _P, _OP, _IP],
@@ -101,21 +102,21 @@ SIGNATURES = {
 }
 _RESTYPE = {"aunmf_strerror": ctypes.c_char_p, "aunmf_last_cuda_error": ctypes.c_char_p}
 
-_lib = None
+_libs = {}
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(checked: bool = False) -> str:
+    return _build.LIB_CHECK if checked else _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load libaunmf.so (building it first if allowed and missing)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load libaunmf.so, or with checked=True the bounds-checked variant
+    libaunmf_check.so (building it first if allowed and missing)."""
+    if checked in _libs:
+        return _libs[checked]
+    path = lib_path(checked)
+    if build_if_missing and not _build.up_to_date(checked):
+        _build.build(check=checked)
     if not os.path.exists(path):
         raise RuntimeError(f"libaunmf not built ({path}); run __graft_entry__.build()")
     L = ctypes.CDLL(path)
@@ -123,8 +124,18 @@ def load(build_if_missing: bool = True):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = _RESTYPE.get(name, ctypes.c_int)
-    _lib = L
+    _libs[checked] = L
     return L
+
+
+def check_status(checked: bool = True) -> int:
+    """aunmf_check_status of the given library: the first bounds-check site
+    recorded since the last call (0 = none; -1 = a build without checks)."""
+    site = ctypes.c_int(0)
+    rc = load(checked=checked).aunmf_check_status(ctypes.byref(site))
+    if rc != OK:
+        raise AunmfError(rc, strerror(rc))
+    return site.value
 
 
 def strerror(code: int) -> str:
@@ -190,9 +201,9 @@ def csr_matrix(rowptr, colidx, val, shape) -> Matrix:
 class Handle:
     """Owns an aunmf_handle bound to torch's current CUDA stream."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, checked=False):
         torch = _torch()
-        self._lib = load()
+        self._lib = load(checked=checked)
         s = stream if stream is not None else torch.cuda.current_stream()
         self._h = ctypes.c_void_p()
         self._check(self._lib.aunmf_create(ctypes.byref(self._h), ctypes.c_void_p(s.cuda_stream)))

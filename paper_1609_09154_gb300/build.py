@@ -1,6 +1,9 @@
 """Build step for the CUDA library: compiles csrc/*.cu for sm_103a with nvcc
 (one process per translation unit, in parallel) and links
-_build/libaunmf.so in-tree.  No cmake, no torch extension machinery."""
+_build/libaunmf.so in-tree.  build(check=True) makes the checked variant,
+_build/libaunmf_check.so (-DAUNMF_CHECK: device bounds checks that record a
+site and skip the access; see aunmf_check_status in include/aunmf.h).  No
+cmake, no torch extension machinery."""
 from __future__ import annotations
 
 import glob
@@ -14,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libaunmf.so")
+LIB_CHECK = os.path.join(OUT_DIR, "libaunmf_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
     "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -37,23 +41,27 @@ def _deps():
         os.path.join(HERE, "..", "include", "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(check: bool = False) -> bool:
+    lib = LIB_CHECK if check else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    lib = LIB_CHECK if check else LIB
+    if not force and up_to_date(check):
+        return lib
+    obj_dir = os.path.join(OUT_DIR, "check") if check else OUT_DIR
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
+    flags = [*NVCC_FLAGS, *(["-DAUNMF_CHECK"] if check else []), *extra]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,14 +71,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

@@ -35,6 +35,14 @@ std::atomic<long long> g_inject_cycles{aunmf::fault::kDefaultWaitCycles};
 }  // namespace
 
 int aunmf::fault::site() { return g_inject_site.load(std::memory_order_relaxed); }
+
+// Readers of the checked build's per-unit site words (registered while the
+// library loads; none in the normal build).
+static std::vector<int (*)()> &check_readers() {
+  static std::vector<int (*)()> readers;
+  return readers;
+}
+void aunmf::register_check_reader(int (*reader)()) { check_readers().push_back(reader); }
 long long aunmf::fault::wait_cycles() { return g_inject_cycles.load(std::memory_order_relaxed); }
 
 struct Buf {
@@ -219,7 +227,8 @@ cudaError_t product_aht(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   (void)h;
   if (!A->dense) {
     PhaseTimer t(c, s, kPhAht);
-    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, c.Ht, c.k, c.PW, &c.csr_long, s);
+    return launch_aht_csr(A->rowptr, A->colidx, A->val, A->m, A->n, A->nnz, c.Ht, c.k, c.PW,
+                          &c.csr_long, s);
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhAht);
@@ -253,7 +262,8 @@ cudaError_t product_wta(aunmf_handle *h, RunCtx &c, cudaStream_t s) {
   (void)h;
   if (!A->dense) {
     PhaseTimer t(c, s, kPhWta);
-    return launch_wta_csc(c.colptr, c.rowidx, c.cval, A->n, c.W, c.k, c.PHt, &c.csc_long, s);
+    return launch_wta_csc(c.colptr, c.rowidx, c.cval, A->n, A->m, A->nnz, c.W, c.k, c.PHt,
+                          &c.csc_long, s);
   }
   if (c.prec == AUNMF_FP32) {
     PhaseTimer t(c, s, kPhWta);
@@ -562,6 +572,22 @@ static int validate_inputs(aunmf_handle *h, const aunmf_matrix *A, int k, const 
   CK(h, cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   return hf ? AUNMF_E_INVAL : AUNMF_OK;
+}
+
+int aunmf_check_status(int *site) {
+  if (!site) return AUNMF_E_INVAL;
+  if (check_readers().empty()) {
+    *site = -1;
+    return AUNMF_OK;
+  }
+  cudaDeviceSynchronize();
+  int first = 0;
+  for (int (*r)() : check_readers()) {
+    const int v = r();
+    if (!first) first = v;
+  }
+  *site = first;
+  return AUNMF_OK;
 }
 
 int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters,
@@ -1027,7 +1053,7 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
     c.A = A;
     int rc = prepare_sparse(h, c, s);
     if (rc != AUNMF_OK) return rc;
-    CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, W, k, PHt, &c.csc_long, s));
+    CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, m, A->nnz, W, k, PHt, &c.csc_long, s));
   }
   CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
   CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s));

@@ -502,7 +502,7 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
         const int j = lane + 32 * t;
-        if (j < k) {
+        if (j < k && AUNMF_BOUND(posf[t] < k && posb[t] < k, AUNMF_CHECK_BPP_LIST)) {
           if (pas[t]) Fl[posf[t]] = j; else Bl[posb[t]] = j;
         }
       }
@@ -781,13 +781,15 @@ __device__ __forceinline__ int bpp_row_direct(const double *__restrict__ G, doub
       }
 #pragma unroll
       for (int t = 0; t < KT; ++t)
-        if (pas[t]) Fl[pos[t]] = lane + 32 * t;
+        if (pas[t] && AUNMF_BOUND(pos[t] < k && lane + 32 * t < k, AUNMF_CHECK_BPP_LIST))
+          Fl[pos[t]] = lane + 32 * t;
       __syncwarp();
       if (!warp_cholesky([G, k](int a, int b) { return G[a * k + b]; }, Fl, nf, L, ldl, lane)) {
         failed_numeric = true;
         break;
       }
-      for (int a = lane; a < nf; a += 32) v[a] = rs[Fl[a]];
+      for (int a = lane; a < nf; a += 32)
+        v[a] = AUNMF_BOUND(Fl[a] >= 0 && Fl[a] < k, AUNMF_CHECK_BPP_LIST) ? rs[Fl[a]] : 0.0;
       __syncwarp();
       warp_chol_solve(L, ldl, nf, v, lane);
 #pragma unroll

@@ -37,6 +37,38 @@ cudaError_t launch_validate_vec(const float *v, int64_t len, int bit, int *flag,
 cudaError_t launch_validate_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
                                 int64_t m, int64_t n, int64_t nnz, int *flag, cudaStream_t s);
 
+// Checked build (-DAUNMF_CHECK, libaunmf_check.so): AUNMF_BOUND(ok, site)
+// tests an index condition in device code.  When it fails it records `site`
+// (an AUNMF_CHECK_* code; the first one per translation unit) in a device
+// word and yields false, so the caller skips the access instead of
+// faulting.  In the normal build it is the constant true, and `ok` is not
+// evaluated.  Each unit registers a reader of its word at load time;
+// aunmf_check_status() calls them (no readers: the normal build).
+void register_check_reader(int (*reader)());
+#ifdef AUNMF_CHECK
+namespace {
+__device__ int g_check_site;
+__device__ __noinline__ bool check_fail(int site) {
+  atomicCAS(&g_check_site, 0, site);
+  return false;
+}
+int read_check_site() {
+  int v = 0;
+  const int z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_check_site, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaMemcpyToSymbol(g_check_site, &z, sizeof(int));
+  return v;
+}
+[[maybe_unused]] const int g_check_registered = (register_check_reader(read_check_site), 0);
+}  // namespace
+#define AUNMF_BOUND(ok, site) ((ok) ? true : check_fail(site))
+#else
+#define AUNMF_BOUND(ok, site) true
+#endif
+
 // Device-side error/diagnostic counters, one block of int64 in the workspace.
 struct DevCounters {
   long long bpp_pivots;
@@ -106,12 +138,13 @@ struct SpLongRows {
   const int64_t *chunk0 = nullptr;
   float *part = nullptr;
 };
+// (n, m and nnz bound the gathered indices in the checked build.)
 cudaError_t launch_aht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, const float *Ht, int k, float *P, const SpLongRows *lr,
-                           cudaStream_t s);
+                           int64_t m, int64_t n, int64_t nnz, const float *Ht, int k, float *P,
+                           const SpLongRows *lr, cudaStream_t s);
 cudaError_t launch_wta_csc(const int64_t *colptr, const int32_t *rowidx, const float *cval,
-                           int64_t n, const float *W, int k, float *P, const SpLongRows *lr,
-                           cudaStream_t s);
+                           int64_t n, int64_t m, int64_t nnz, const float *W, int k, float *P,
+                           const SpLongRows *lr, cudaStream_t s);
 // list: long_rows_capacity(nnz) int64; chunk0: capacity + 1 int64; count: one
 // counter.  Fills lr (its part stays null: the caller allocates nchunks x k
 // floats).  Synchronises the stream.

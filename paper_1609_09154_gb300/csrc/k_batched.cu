@@ -213,6 +213,10 @@ __global__ void __launch_bounds__(256)
     const Item I = items[it];
     const BInst &b = P[I.p];
     const int k = b.k;
+    if (!AUNMF_BOUND(I.r0 >= 0 && I.r0 <= I.r1 && I.r1 <= (side ? b.m : b.n) && k >= 1 &&
+                         k <= kMaxK,
+                     AUNMF_CHECK_BATCHED_ITEM))
+      continue;
     const float *X = side ? b.W : b.Ht;
     double *out = (side ? b.gpart_w : b.gpart_h) + (int64_t)I.chunk * k * k;
     const int kp = (k + 3) & ~3;
@@ -326,6 +330,10 @@ __global__ void __launch_bounds__(32 * bpp::kBppWarps, 1)
     const Item I = items[it];
     const BInst &b = P[I.p];
     const int k = b.k;
+    if (!AUNMF_BOUND(I.r0 >= 0 && I.r0 <= I.r1 && I.r1 <= (side ? b.n : b.m) && k >= 1 &&
+                         k <= kMaxK,
+                     AUNMF_CHECK_BATCHED_ITEM))
+      continue;
     __syncthreads();
     const bpp::BppWarp w =
         bpp::bpp_stage(side ? b.GW : b.GH, reinterpret_cast<const float *>(b.Q), b.q_ok, k, sm, wib);
@@ -367,6 +375,10 @@ __global__ void __launch_bounds__(256)
     const Item I = items[it];
     const BInst &b = P[I.p];
     const int k = b.k;
+    if (!AUNMF_BOUND(I.r0 >= 0 && I.r0 <= I.r1 && I.r1 <= (side ? b.n : b.m) && k >= 1 &&
+                         k <= kMaxK,
+                     AUNMF_CHECK_BATCHED_ITEM))
+      continue;
     bool any = false;
     for (int64_t r = I.r0 + threadIdx.x; r < I.r1; r += blockDim.x) any |= b.redo[r] != 0;
     if (!__syncthreads_or(any)) continue;
@@ -414,6 +426,9 @@ __global__ void g_dot_partial(const BInst *__restrict__ P, const Item *__restric
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item I = items[it];
     const BInst &b = P[I.p];
+    if (!AUNMF_BOUND(I.r0 >= 0 && I.r0 <= I.r1 && I.r1 <= b.n * (int64_t)b.k,
+                     AUNMF_CHECK_BATCHED_ITEM))
+      continue;
     double s = 0.0;
     for (int64_t e = I.r0 + threadIdx.x; e < I.r1; e += blockDim.x)
       s = fma((double)b.PHt[e], (double)b.Ht[e], s);

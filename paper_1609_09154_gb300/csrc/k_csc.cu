@@ -24,12 +24,15 @@ int grid_for(int64_t items, int per_sm) {
 }
 
 // rows[e] = r for the nonzeros e of row r (a warp per row).
-__global__ void k_rows_of(const int64_t *__restrict__ rowptr, int64_t m, int32_t *__restrict__ rows) {
+__global__ void k_rows_of(const int64_t *__restrict__ rowptr, int64_t m, int64_t nnz,
+                          int32_t *__restrict__ rows) {
+  (void)nnz;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w0; r < m; r += ws)
-    for (int64_t e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) rows[e] = (int32_t)r;
+    for (int64_t e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32)
+      if (AUNMF_BOUND(e >= 0 && e < nnz, AUNMF_CHECK_CSC)) rows[e] = (int32_t)r;
 }
 
 __global__ void k_iota(int32_t *__restrict__ p, int64_t nnz) {
@@ -49,9 +52,10 @@ __global__ void k_csc_fill(const int32_t *__restrict__ key, const int32_t *__res
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = pos[q];
+    const int64_t c1 = key[q];
+    if (!AUNMF_BOUND(e >= 0 && e < nnz && c1 >= 0 && c1 < n, AUNMF_CHECK_CSC)) continue;
     rowidx[q] = rows[e];
     cval[q] = val[e];
-    const int64_t c1 = key[q];
     const int64_t c0 = q == 0 ? 0 : (int64_t)key[q - 1] + 1;
     for (int64_t c = c0; c <= c1; ++c) colptr[c] = q;
   }
@@ -105,7 +109,7 @@ cudaError_t launch_csr_to_csc(const int64_t *rowptr, const int32_t *colidx, cons
   size_t temp_bytes = sort_temp_bytes(nnz, n);
   if (nnz > 0) {
     k_iota<<<grid_for(nnz, 16), kCscThreads, 0, s>>>(pos_in, nnz);
-    k_rows_of<<<grid_for(m * 32, 16), kCscThreads, 0, s>>>(rowptr, m, rows);
+    k_rows_of<<<grid_for(m * 32, 16), kCscThreads, 0, s>>>(rowptr, m, nnz, rows);
     cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, temp_bytes, colidx, key, pos_in, pos,
                                                     (int)nnz, 0, key_bits(n), s);
     if (e != cudaSuccess) return e;

@@ -587,6 +587,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
       mbar_expect_tx_only(&full[st], bytes);
     else
       mbar_expect_tx(&full[st], bytes);
+    // x coordinates (k0 for AK and the factor, m0 otherwise) are multiples
+    // of 16 floats; the checked build tests it and skips bad copies
+    if (!AUNMF_BOUND(k0 >= 0 && (k0 & 3) == 0 && (m0 & 3) == 0 && (n0 & 3) == 0,
+                     AUNMF_CHECK_TMA_COORD))
+      return;
     if (AK)
       tma_load_2d(sA + (size_t)st * kTBM * kTBK, &mapA, &full[st], k0, (int)m0, pol_a);
     else

@@ -20,12 +20,14 @@ constexpr int64_t kChunkNz = 2048;  // nonzeros per warp on a long row
 
 // acc[t] (lane's entries j = lane + 32 t) += sum over nonzeros e in [e0, e1)
 // of val[e] X[idx[e], j]: the warp stages 32 nonzeros in registers, then
-// broadcasts them and gathers the k-vectors of X, four at a time.
+// broadcasts them and gathers the k-vectors of X (ncols rows), four at a
+// time.  (ncols is read only by the checked build.)
 template <int KT>
 __device__ __forceinline__ void spmm_range(const int32_t *__restrict__ idx,
                                            const float *__restrict__ val,
-                                           const float *__restrict__ X, int k, int64_t e0,
-                                           int64_t e1, float (&acc)[KT], int lane) {
+                                           const float *__restrict__ X, int64_t ncols, int k,
+                                           int64_t e0, int64_t e1, float (&acc)[KT], int lane) {
+  (void)ncols;
   for (int64_t eb = e0; eb < e1; eb += 32) {
     const int64_t e = eb + lane;
     const int my_c = e < e1 ? __ldg(&idx[e]) : 0;
@@ -46,7 +48,10 @@ __device__ __forceinline__ void spmm_range(const int32_t *__restrict__ idx,
 #pragma unroll
         for (int t = 0; t < KT; ++t) {
           const int col = lane + 32 * t;
-          g[u][t] = col < k ? __ldg(&X[(int64_t)c[u] * k + col]) : 0.f;
+          g[u][t] = (col < k && AUNMF_BOUND((uint64_t)c[u] < (uint64_t)ncols,
+                                            AUNMF_CHECK_SPMM_COLUMN))
+                        ? __ldg(&X[(int64_t)c[u] * k + col])
+                        : 0.f;
         }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -59,30 +64,33 @@ __device__ __forceinline__ void spmm_range(const int32_t *__restrict__ idx,
 #pragma unroll
       for (int t = 0; t < KT; ++t) {
         const int col = lane + 32 * t;
-        if (col < k) acc[t] = fmaf(v, __ldg(&X[(int64_t)c * k + col]), acc[t]);
+        if (col < k && AUNMF_BOUND((uint64_t)c < (uint64_t)ncols, AUNMF_CHECK_SPMM_COLUMN))
+          acc[t] = fmaf(v, __ldg(&X[(int64_t)c * k + col]), acc[t]);
       }
     }
   }
 }
 
-// Y (rows x k) = S (rows x ncols, CSR ptr/idx/val) * X (ncols x k), a warp
-// per row.  Rows longer than `skip_above` (> 0) are left to the chunked
-// kernels below.
+// Y (rows x k) = S (rows x ncols, CSR ptr/idx/val, nnz nonzeros) * X
+// (ncols x k), a warp per row.  Rows longer than `skip_above` (> 0) are left
+// to the chunked kernels below.
 template <int KT>
 __global__ void __launch_bounds__(kSpThreads)
     k_spmm(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-           const float *__restrict__ val, int64_t rows, const float *__restrict__ X, int k,
-           float *__restrict__ Y, int64_t skip_above) {
+           const float *__restrict__ val, int64_t rows, int64_t ncols, int64_t nnz,
+           const float *__restrict__ X, int k, float *__restrict__ Y, int64_t skip_above) {
+  (void)nnz;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (int64_t)blockIdx.x * kSpWarps + (threadIdx.x >> 5);
   const int64_t ws = (int64_t)gridDim.x * kSpWarps;
   for (int64_t r = w0; r < rows; r += ws) {
     const int64_t e0 = ptr[r], e1 = ptr[r + 1];
     if (skip_above > 0 && e1 - e0 > skip_above) continue;
+    if (!AUNMF_BOUND(e0 >= 0 && e0 <= e1 && e1 <= nnz, AUNMF_CHECK_SPMM_RANGE)) continue;
     float acc[KT];
 #pragma unroll
     for (int t = 0; t < KT; ++t) acc[t] = 0.f;
-    spmm_range<KT>(idx, val, X, k, e0, e1, acc, lane);
+    spmm_range<KT>(idx, val, X, ncols, k, e0, e1, acc, lane);
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int col = lane + 32 * t;
@@ -100,9 +108,12 @@ __global__ void __launch_bounds__(kSpThreads)
 template <int KT>
 __global__ void __launch_bounds__(kSpThreads)
     k_spmm_chunks(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                  const float *__restrict__ val, const float *__restrict__ X, int k,
-                  const int64_t *__restrict__ lrow, const int64_t *__restrict__ chunk0,
-                  int64_t nlong, int64_t nchunks, float *__restrict__ part) {
+                  const float *__restrict__ val, int64_t rows, int64_t ncols, int64_t nnz,
+                  const float *__restrict__ X, int k, const int64_t *__restrict__ lrow,
+                  const int64_t *__restrict__ chunk0, int64_t nlong, int64_t nchunks,
+                  float *__restrict__ part) {
+  (void)rows;
+  (void)nnz;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (int64_t)blockIdx.x * kSpWarps + (threadIdx.x >> 5);
   const int64_t ws = (int64_t)gridDim.x * kSpWarps;
@@ -113,12 +124,14 @@ __global__ void __launch_bounds__(kSpThreads)
       if (chunk0[mid] <= c) lo = mid; else hi = mid - 1;
     }
     const int64_t r = lrow[lo];
+    if (!AUNMF_BOUND(r >= 0 && r < rows, AUNMF_CHECK_SPMM_RANGE)) continue;
     const int64_t e0 = ptr[r] + (c - chunk0[lo]) * kChunkNz;
     const int64_t e1 = min(ptr[r + 1], e0 + kChunkNz);
+    if (!AUNMF_BOUND(e0 >= 0 && e0 <= e1 && e1 <= nnz, AUNMF_CHECK_SPMM_RANGE)) continue;
     float acc[KT];
 #pragma unroll
     for (int t = 0; t < KT; ++t) acc[t] = 0.f;
-    spmm_range<KT>(idx, val, X, k, e0, e1, acc, lane);
+    spmm_range<KT>(idx, val, X, ncols, k, e0, e1, acc, lane);
 #pragma unroll
     for (int t = 0; t < KT; ++t) {
       const int col = lane + 32 * t;
@@ -191,21 +204,24 @@ int sp_blocks(int64_t warps) {
   }
 
 cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows,
-                 const float *X, int k, float *Y, const SpLongRows *lr, cudaStream_t s) {
+                 int64_t ncols, int64_t nnz, const float *X, int k, float *Y,
+                 const SpLongRows *lr, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
   const int kt = (k + 31) / 32;
   const bool split = lr && lr->nlong > 0;
   const int64_t skip = split ? kLongRowNz : 0;
   const int nb = sp_blocks(rows);
-#define AUNMF_SP_MAIN(KT) k_spmm<KT><<<nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, X, k, Y, skip)
+#define AUNMF_SP_MAIN(KT) \
+  k_spmm<KT><<<nb, kSpThreads, 0, s>>>(ptr, idx, val, rows, ncols, nnz, X, k, Y, skip)
   AUNMF_SP_SWITCH(kt, AUNMF_SP_MAIN)
 #undef AUNMF_SP_MAIN
   g_launches += 1;
   if (split) {
     const int nbc = sp_blocks(lr->nchunks), nbl = sp_blocks(lr->nlong);
 #define AUNMF_SP_CH(KT)                                                                  \
-  k_spmm_chunks<KT><<<nbc, kSpThreads, 0, s>>>(ptr, idx, val, X, k, lr->row, lr->chunk0, \
-                                               lr->nlong, lr->nchunks, lr->part);        \
+  k_spmm_chunks<KT><<<nbc, kSpThreads, 0, s>>>(ptr, idx, val, rows, ncols, nnz, X, k,      \
+                                               lr->row, lr->chunk0, lr->nlong, lr->nchunks, \
+                                               lr->part);                                \
   k_spmm_long_sum<KT><<<nbl, kSpThreads, 0, s>>>(lr->row, lr->chunk0, lr->nlong, lr->part, k, Y)
     AUNMF_SP_SWITCH(kt, AUNMF_SP_CH)
 #undef AUNMF_SP_CH
@@ -217,15 +233,15 @@ cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64
 }  // namespace
 
 cudaError_t launch_aht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, const float *Ht, int k, float *P, const SpLongRows *lr,
-                           cudaStream_t s) {
-  return spmm(rowptr, colidx, val, m, Ht, k, P, lr, s);
+                           int64_t m, int64_t n, int64_t nnz, const float *Ht, int k, float *P,
+                           const SpLongRows *lr, cudaStream_t s) {
+  return spmm(rowptr, colidx, val, m, n, nnz, Ht, k, P, lr, s);
 }
 
 cudaError_t launch_wta_csc(const int64_t *colptr, const int32_t *rowidx, const float *cval,
-                           int64_t n, const float *W, int k, float *P, const SpLongRows *lr,
-                           cudaStream_t s) {
-  return spmm(colptr, rowidx, cval, n, W, k, P, lr, s);
+                           int64_t n, int64_t m, int64_t nnz, const float *W, int k, float *P,
+                           const SpLongRows *lr, cudaStream_t s) {
+  return spmm(colptr, rowidx, cval, n, m, nnz, W, k, P, lr, s);
 }
 
 int64_t long_rows_capacity(int64_t nnz) { return nnz / kLongRowNz + 1; }

@@ -316,8 +316,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&empty[st], ph ^ 1u, L.err, L.wait_cycles)) { ok = false; break; }
           uint8_t *xs = smem + (size_t)st * sbytes;
           mbar_expect_tx(&full[st], tx);
-          tma_load_2d(xs, &p->mapX, &full[st], (int)(kb * BKE), row0, pol_x);
-          tma_load_2d(xs + xbytes, &p->mapY, &full[st], (int)(kb * BKE), 0, pol_y);
+          // (checked build: a bad coordinate skips the copies; the stage then
+          // never fills and the bounded waits end the launch)
+          if (AUNMF_BOUND(kb >= 0 && kb * BKE <= 0x7fffffffLL &&
+                              ((kb * BKE * ESZ) & 15) == 0 && row0 >= 0,
+                          AUNMF_CHECK_TMA_COORD)) {
+            tma_load_2d(xs, &p->mapX, &full[st], (int)(kb * BKE), row0, pol_x);
+            tma_load_2d(xs + xbytes, &p->mapY, &full[st], (int)(kb * BKE), 0, pol_y);
+          }
           ++nissued;
           if (++st == L.nstages) { st = 0; ph ^= 1u; }
         }

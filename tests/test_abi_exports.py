@@ -110,3 +110,17 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_normal_build_compiles_no_bounds_checks(libpath):
+    """aunmf_check_status of the normal build reports -1 (no checks compiled)
+    without touching a device."""
+    import ctypes
+
+    L = ctypes.CDLL(libpath)
+    L.aunmf_check_status.argtypes = [ctypes.c_void_p]
+    L.aunmf_check_status.restype = ctypes.c_int
+    site = ctypes.c_int(7)
+    assert L.aunmf_check_status(ctypes.byref(site)) == 0
+    assert site.value == -1
+    assert L.aunmf_check_status(None) == -1
