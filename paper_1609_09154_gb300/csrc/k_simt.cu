@@ -181,6 +181,164 @@ __global__ void __launch_bounds__(kGramThreads, 2)
   }
 }
 
+// k_gram8: the FP32 Gram of a factor with contiguous rows (ldx == k, k <= 64,
+// 16-byte aligned), with 8 x 8 register tiles.  A block (one per SM) walks
+// its rows in stages of kG8Rows: each stage is one contiguous span of the
+// factor, copied with 16-byte loads at the span's own offsets into shared
+// memory (no index arithmetic) while the previous stage is consumed.
+// Thread (g, t): tile t = (ti, tj), ti <= tj, of the upper triangle in 8 x 8
+// blocks (28 tiles at k = 50, 36 at 64), row group g of ngrp = 256 / tiles
+// (rows g, g + ngrp, ... of each stage).  Each row costs a thread 16 values
+// (float2 loads for even k) and 64 FFMAs, against 8 values and 16 FFMAs per
+// row in k_gram_part's 4 x 4 tiles.  As there, slabs are summed in fresh
+// registers and folded into Kahan-compensated running sums (~64 rows a
+// slab; the sums in registers, the corrections in shared memory), and the
+// groups' sums are added in group order, so the result does not depend on
+// scheduling.
+constexpr int kG8Threads = 256, kG8Rows = 128, kG8MaxK = 64;
+constexpr int kG8Buf = kG8Rows * kG8MaxK + 8;  // floats per stage buffer (+ tail pad)
+constexpr int kG8Ldc = 68;                     // floats per thread row of corrections
+constexpr int kG8Pre = kG8Rows * kG8MaxK / 4 / kG8Threads;  // float4 prefetch per thread
+constexpr size_t kG8Smem = sizeof(float) * (2 * (size_t)kG8Buf + (size_t)kG8Threads * kG8Ldc);
+
+template <bool EVEN>
+__global__ void __launch_bounds__(kG8Threads, 1)
+    k_gram8(const float *__restrict__ X, int64_t rows, int k, int64_t chunk,
+            float *__restrict__ partials) {
+  extern __shared__ __align__(16) float sg[];
+  float *buf0 = sg, *buf1 = sg + kG8Buf;
+  float *corr = sg + 2 * kG8Buf;
+  const int tid = threadIdx.x;
+  const int nt = (k + 7) >> 3, ntiles = nt * (nt + 1) / 2;
+  const int ngrp = kG8Threads / ntiles;
+  const int g = tid / ntiles, t = tid - g * ntiles;
+  const bool act = g < ngrp;
+  int ti = 0, tj = 0;
+  if (act) {
+    int rem = t;
+    while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+    tj = ti + rem;
+  }
+  // stages per slab: ~64 of the thread's own rows between folds
+  const int fold_every = max(1, (64 * ngrp + kG8Rows / 2) / kG8Rows);
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
+  float *kc = corr + (size_t)tid * kG8Ldc;
+#pragma unroll
+  for (int e = 0; e < 64; e += 4) *reinterpret_cast<float4 *>(kc + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+  float acc[8][8], hi[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = hi[i][j] = 0.f;
+
+  // stage c0: the span X[c0 k, (c0 + nr) k), float4 groups then <= 3 floats
+  float4 pre[kG8Pre];
+  float tailv = 0.f;
+  auto fetch = [&](int64_t c0) {
+    const int nr = (int)min((int64_t)kG8Rows, r1 - c0);
+    const int len = nr * k, n4 = len >> 2;
+    const float4 *src = reinterpret_cast<const float4 *>(X + c0 * k);
+#pragma unroll
+    for (int q = 0; q < kG8Pre; ++q) {
+      const int i4 = tid + q * kG8Threads;
+      pre[q] = i4 < n4 ? __ldcs(src + i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    tailv = tid < (len & 3) ? X[c0 * k + (n4 << 2) + tid] : 0.f;
+  };
+  auto store = [&](float *b, int64_t c0) {
+    const int nr = (int)min((int64_t)kG8Rows, r1 - c0);
+    const int len = nr * k, n4 = len >> 2;
+#pragma unroll
+    for (int q = 0; q < kG8Pre; ++q) {
+      const int i4 = tid + q * kG8Threads;
+      if (i4 < n4) *reinterpret_cast<float4 *>(b + 4 * i4) = pre[q];
+    }
+    if (tid < (len & 3)) b[(n4 << 2) + tid] = tailv;
+  };
+  auto fold = [&]() {
+#pragma unroll
+    for (int e4 = 0; e4 < 64; e4 += 4) {
+      float4 cv = *reinterpret_cast<const float4 *>(kc + e4);
+      float *c = &cv.x;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e4 + u, i = e >> 3, j = e & 7;
+        const float y = acc[i][j] - c[u];
+        const float tt = hi[i][j] + y;
+        c[u] = (tt - hi[i][j]) - y;
+        hi[i][j] = tt;
+        acc[i][j] = 0.f;
+      }
+      *reinterpret_cast<float4 *>(kc + e4) = cv;
+    }
+  };
+  auto load8 = [&](const float *p, float (&v)[8]) {
+    if constexpr (EVEN) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 w = *reinterpret_cast<const float2 *>(p + 2 * u);
+        v[2 * u] = w.x;
+        v[2 * u + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p[u];
+    }
+  };
+
+  if (r0 < r1) {
+    fetch(r0);
+    store(buf0, r0);
+  }
+  __syncthreads();
+  int stage = 0;
+  float *cur = buf0, *nxt = buf1;
+  for (int64_t c0 = r0; c0 < r1; c0 += kG8Rows, ++stage) {
+    const int nr = (int)min((int64_t)kG8Rows, r1 - c0);
+    const bool more = c0 + kG8Rows < r1;
+    if (more) fetch(c0 + kG8Rows);
+    if (act) {
+      for (int rr = g; rr < nr; rr += ngrp) {
+        const float *row = cur + rr * k;
+        float a[8], b[8];
+        load8(row + 8 * ti, a);
+        load8(row + 8 * tj, b);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if ((stage + 1) % fold_every == 0 || !more) fold();
+    }
+    if (more) store(nxt, c0 + kG8Rows);
+    __syncthreads();
+    float *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  // the groups' sums (hi - c), added in group order by group 0
+  float *gs = sg;  // ngrp x ntiles x 64 floats, over the stage buffers
+  __syncthreads();
+  if (act && g > 0) {
+#pragma unroll
+    for (int e = 0; e < 64; ++e) gs[((size_t)g * ntiles + t) * 64 + e] = hi[e >> 3][e & 7] - kc[e];
+  }
+  __syncthreads();
+  if (act && g == 0) {
+    float *out = partials + (int64_t)blockIdx.x * k * k;
+#pragma unroll
+    for (int e = 0; e < 64; ++e) {
+      float v = hi[e >> 3][e & 7] - kc[e];
+      for (int h = 1; h < ngrp; ++h) v += gs[((size_t)h * ntiles + t) * 64 + e];
+      const int i = 8 * ti + (e >> 3), j = 8 * tj + (e & 7);
+      if (i < k && j < k) {
+        out[i * k + j] = v;
+        out[j * k + i] = v;
+      }
+    }
+  }
+}
+
 template <bool FP64>
 size_t gram_smem_bytes(int k) {
   const int kp = (k + 3) & ~3, nt = kp / 4, ntiles = nt * (nt + 1) / 2;
@@ -269,6 +427,30 @@ int gram_partial_blocks(int64_t rows, int max_blocks) {
 
 cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
                         float *partials, int max_blocks, cudaStream_t s) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 148;
+  // k_gram8 needs >= 16 stages per block to repay its fixed costs: on the
+  // sparse workload's 10^6 / 5 10^5 rows it takes the Grams from 0.320 to
+  // 0.242 ms per iteration; on the dense one's 96,000 / 64,000 rows it was
+  // slower (0.109 against 0.077 ms), so those keep k_gram_part
+  if (ldx == k && k <= kG8MaxK && k >= 8 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+      rows >= 16LL * kG8Rows * sms) {
+    // one block per SM (its chunk a whole number of stages, so every span
+    // starts on a 16-byte boundary), partials reduced as for k_gram_part
+    int64_t nb = (rows + kG8Rows - 1) / kG8Rows;
+    const int64_t cap = min((int64_t)max_blocks, (int64_t)sms);
+    if (nb > cap) nb = cap;
+    const int64_t chunk = ((rows + nb - 1) / nb + kG8Rows - 1) / kG8Rows * kG8Rows;
+    nb = (rows + chunk - 1) / chunk;
+    auto kern = (k & 1) ? k_gram8<false> : k_gram8<true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kG8Smem);
+    kern<<<(unsigned)nb, kG8Threads, kG8Smem, s>>>(X, rows, k, chunk, partials);
+    k_gram_reduce<<<(k * k + 31) / 32, 256, 0, s>>>(partials, (int)nb, k, G);
+    g_launches += 2;
+    return cudaGetLastError();
+  }
   const int nb = gram_partial_blocks(rows, max_blocks);
   const int64_t chunk = (rows + nb - 1) / nb;
   const size_t smem = gram_smem_bytes<false>(k);

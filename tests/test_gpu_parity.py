@@ -117,6 +117,27 @@ def test_products_fp32_padded_rows(ax, k):
     assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), 333)
 
 
+@pytest.mark.parametrize("rows,k", [(400_003, 50), (350_001, 33), (320_000, 64), (330_017, 8)])
+def test_gram_many_rows(ax, rows, k):
+    """Factors with >= 16 x 128 rows per SM take the 8 x 8-tile Gram (rows
+    staged as contiguous spans, ~64-row slabs folded into Kahan sums, the
+    row groups' sums added in order).  Its error is at most (L + 2 + ngrp) u
+    |X|^T |X| for slabs of L ~ 64 rows and ngrp = 256 // tiles row groups
+    (FP32 sums of L terms, Kahan's fold, the groups' sum), far inside the
+    generic 2 rows u bar; the ragged row counts end in partial stages."""
+    rng = np.random.default_rng(rows + k)
+    X = rng.random((rows, k)).astype(np.float32).astype(np.float64)
+    G = host(ax.gram_w(dev(X)))
+    ref = orc.gram_w(X)
+    nt = (k + 7) // 8
+    ngrp = 256 // (nt * (nt + 1) // 2)
+    absprod = np.abs(X).T @ np.abs(X)
+    tol = (64 + 2 + ngrp) * U32 * absprod
+    err = np.abs(G - ref)
+    assert (err <= tol).all(), f"max err/tol {np.max(err / tol):.3g}"
+    np.testing.assert_array_equal(G, G.T)
+
+
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_mu_updates(ax, m, n, k):
     A, W, H = problem(m, n, k, seed=m + 2)
