@@ -315,7 +315,7 @@ cudaError_t gram(aunmf_handle *h, RunCtx &c, const float *X, int64_t rows, float
   if (c.algo == AUNMF_ABPP)
     return launch_gram_d(X, rows, c.k, c.k, G64, G32, reinterpret_cast<double *>(c.gpart),
                          h->max_gram_blocks, s);
-  return launch_gram(X, rows, c.k, c.k, G32, c.gpart, h->max_gram_blocks, s);
+  return launch_gram(X, rows, c.k, c.k, G32, c.gpart, h->max_gram_blocks, s, c.err);
 }
 
 // Projected-gradient norm of the current (W, H) into pg_dev[ctr->iter], from
@@ -695,6 +695,11 @@ int aunmf_run(aunmf_handle *h, const aunmf_matrix *A, int k, int algo, int iters
     int prc = prepare_sparse(h, c, s);
     if (prc != AUNMF_OK) return prc;
   }
+  if (!c.err) {  // the bounded waits of the wide-rank Gram report here too
+    ENS(h, h->err, sizeof(int));
+    c.err = P<int>(h->err);
+    CK(h, cudaMemsetAsync(c.err, 0, sizeof(int), s));
+  }
   CK(h, gram(h, c, c.Ht, n, c.GH, c.GH64, s));
   if (c.track_pg) {
     // W^T W and W^T A of the starting W, for the first iteration's measure
@@ -832,7 +837,10 @@ int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_
 int aunmf_gram_w(aunmf_handle *h, const float *W, int64_t m, int k, float *G) {
   if (!h || !W || !G || m < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
-  CK(h, launch_gram(W, m, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream));
+  ENS(h, h->err, sizeof(int));
+  CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), h->stream));
+  CK(h, launch_gram(W, m, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream,
+                    P<int>(h->err)));
   return AUNMF_OK;
 }
 
@@ -840,8 +848,11 @@ int aunmf_gram_h(aunmf_handle *h, const float *H, int k, int64_t n, float *G) {
   if (!h || !H || !G || n < 1 || k < 1 || k > AUNMF_K_MAX) return AUNMF_E_INVAL;
   ENS(h, h->Ht, sizeof(float) * n * k);
   ENS(h, h->gpart, sizeof(float) * (size_t)h->max_gram_blocks * k * k);
+  ENS(h, h->err, sizeof(int));
+  CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), h->stream));
   CK(h, launch_transpose(H, k, n, P<float>(h->Ht), h->stream));
-  CK(h, launch_gram(P<float>(h->Ht), n, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream));
+  CK(h, launch_gram(P<float>(h->Ht), n, k, k, G, P<float>(h->gpart), h->max_gram_blocks, h->stream,
+                    P<int>(h->err)));
   return AUNMF_OK;
 }
 
@@ -1038,13 +1049,13 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
   ENS(h, h->last, sizeof(double));
   float *Ht = P<float>(h->Ht), *PHt = P<float>(h->PHt);
   double *dp = P<double>(h->dpart);
+  ENS(h, h->err, sizeof(int));
   CK(h, cudaMemsetAsync(h->ctr.p, 0, sizeof(DevCounters), s));
+  CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
   CK(h, launch_transpose(H, k, n, Ht, s));
   if (A->dense) {
     CK(h, launch_norm2(A->dense, m, n, A->lda, dp, h->n_dparts, P<double>(h->n2a), s));
     ENS(h, h->parts, simt_parts_bytes(A->m > n ? A->m : n, k));
-    ENS(h, h->err, sizeof(int));
-    CK(h, cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
     CK(h, launch_wta_simt(A->dense, m, n, A->lda, W, k, PHt, P<float>(h->parts), P<int>(h->err),
                           s));
   } else {
@@ -1055,13 +1066,15 @@ int aunmf_relres(aunmf_handle *h, const aunmf_matrix *A, const float *W, const f
     if (rc != AUNMF_OK) return rc;
     CK(h, launch_wta_csc(c.colptr, c.rowidx, c.cval, n, m, A->nnz, W, k, PHt, &c.csc_long, s));
   }
-  CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s));
-  CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s));
+  CK(h, launch_gram(W, m, k, k, P<float>(h->GW), P<float>(h->gpart), h->max_gram_blocks, s,
+                    P<int>(h->err)));
+  CK(h, launch_gram(Ht, n, k, k, P<float>(h->GH), P<float>(h->gpart), h->max_gram_blocks, s,
+                    P<int>(h->err)));
   CK(h, launch_relres(PHt, Ht, n * (int64_t)k, P<float>(h->GW), P<float>(h->GH), k,
                       P<double>(h->n2a), dp, h->n_dparts, nullptr, P<DevCounters>(h->ctr),
                       P<double>(h->last), s));
   int herr = 0;
-  if (A->dense) CK(h, cudaMemcpyAsync(&herr, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(&herr, h->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaMemcpyAsync(relres, h->last.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   return herr ? AUNMF_E_TIMEOUT : AUNMF_OK;
@@ -1131,8 +1144,8 @@ int aunmf_loss_fwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
   cudaStream_t s = h->stream;
   const int64_t m = A->m, n = A->n;
   CK(h, product_wta(h, c, s));
-  CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s));
-  CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+  CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s, c.err));
+  CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s, c.err));
   CK(h, launch_loss(c.PHt, c.Ht, n * (int64_t)k, c.GW, c.GH, k, c.n2a, c.dpart, h->n_dparts, loss,
                     s));
   if (WtA) CK(h, launch_transpose(c.PHt, n, k, WtA, s));
@@ -1148,13 +1161,13 @@ int aunmf_loss_bwd(aunmf_handle *h, const aunmf_matrix *A, int k, const float *W
   cudaStream_t s = h->stream;
   const int64_t m = A->m, n = A->n;
   if (dW) {  // dL/dW = W (H H^T) - A H^T
-    CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s));
+    CK(h, launch_gram(c.Ht, n, k, k, c.GH, c.gpart, h->max_gram_blocks, s, c.err));
     CK(h, product_aht(h, c, s));
     CK(h, launch_xg_minus_p(c.W, c.PW, c.GH, m, k, grad_out, dW, s));
   }
   if (dH) {  // dL/dH = (W^T W) H - W^T A, formed transposed
     ENS(h, h->dHt, sizeof(float) * n * k);
-    CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s));
+    CK(h, launch_gram(c.W, m, k, k, c.GW, c.gpart, h->max_gram_blocks, s, c.err));
     if (WtA) {
       CK(h, launch_transpose(WtA, k, n, c.PHt, s));
     } else {

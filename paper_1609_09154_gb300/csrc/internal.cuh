@@ -100,8 +100,11 @@ __device__ __forceinline__ void two_fma_acc(float a, float b, float &hi, float &
 
 // Gram: partial[b] = sum over rows of block b of X^T X (X rows x k, row-major,
 // leading dimension ldx); then G = sum_b partial[b] in FP64, fixed order.
+// err: the device error flag for the bounded waits of the wide-rank form
+// (k >= 96, which runs the TMA-fed product kernel on X^T X); null keeps the
+// k_gram_part form.
 cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
-                        float *partials, int max_blocks, cudaStream_t s);
+                        float *partials, int max_blocks, cudaStream_t s, int *err = nullptr);
 int gram_partial_blocks(int64_t rows, int max_blocks);
 // The same Gram with every product formed exactly in FP64 (FP32 x FP32 fits a
 // double) and summed in FP64: G64 (k x k, FP64) for the BPP solves, and G32 =

@@ -425,8 +425,18 @@ int gram_partial_blocks(int64_t rows, int max_blocks) {
   return (int)nb;
 }
 
+namespace {
+bool gram_via_gemm(const float *X, int64_t rows, int k, float *G, float *partials, int max_blocks,
+                   int *err, cudaStream_t s, cudaError_t *status);
+}  // namespace
+
 cudaError_t launch_gram(const float *X, int64_t rows, int k, int64_t ldx, float *G,
-                        float *partials, int max_blocks, cudaStream_t s) {
+                        float *partials, int max_blocks, cudaStream_t s, int *err) {
+  // wide ranks: the TMA-fed FP32 product kernel on X^T X (below)
+  if (ldx == k && err) {
+    cudaError_t st = cudaSuccess;
+    if (gram_via_gemm(X, rows, k, G, partials, max_blocks, err, s, &st)) return st;
+  }
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1027,6 +1037,43 @@ cudaError_t gemm_simt(const float *A, int64_t lda, int64_t M, int64_t K, const f
     g_launches += 1;
   }
   return cudaGetLastError();
+}
+// G = X^T X for X (rows x k, contiguous rows, k >= 96 and a multiple of 4,
+// 16-byte aligned) with the TMA-fed FP32 product kernel: C (k x k) = Aop
+// (k x rows) B (rows x k) with Aop(i, r) = X[r][i] (A stored K x M) and B =
+// X.  The whole square is formed (twice the flops of the upper triangle), in
+// Kahan-compensated slabs like every product, over S K splits chosen to fill
+// the SMs, whose partials (S x k x k in `partials`) are added in FP64 in
+// split order.  At k = 512 on 96,000 / 64,000 rows this replaces k_gram_part,
+// whose 4 x 4 tiles need 8,256 tiles per row and so re-stage every row 33
+// times.  Returns false (nothing launched) when the shape does not qualify.
+bool gram_via_gemm(const float *X, int64_t rows, int k, float *G, float *partials, int max_blocks,
+                   int *err, cudaStream_t s, cudaError_t *status) {
+  if (k < 96 || (k & 3) || (reinterpret_cast<uintptr_t>(X) & 15) || rows < 1024 ||
+      rows >= (1LL << 31))
+    return false;
+  CUtensorMap mapA, mapB;
+  if (!simt_map(&mapA, X, k, k, rows, false) || !simt_factor_map(&mapB, X, rows, k, k)) return false;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 148;
+  const unsigned gx = (unsigned)((k + kTBM - 1) / kTBM), gy = (unsigned)((k + kTBN - 1) / kTBN);
+  int64_t S = (sms + (int64_t)gx * gy - 1) / ((int64_t)gx * gy);
+  S = min(S, (int64_t)max_blocks);
+  S = min(S, rows / 512);
+  if (S < 1) S = 1;
+  const int64_t kchunk = ((rows + S - 1) / S + 127) / 128 * 128;
+  S = (rows + kchunk - 1) / kchunk;
+  auto kern = k_gemm_simt_tma<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+  kern<<<dim3(gx, gy, (unsigned)S), kTThreads, kTSmem, s>>>(
+      mapA, mapB, k, rows, k, partials, k, kchunk, err, fault::wait_cycles(),
+      fault::site() == AUNMF_INJECT_SIMT_WAIT ? 1 : 0);
+  k_gram_reduce<<<(k * k + 31) / 32, 256, 0, s>>>(partials, (int)S, k, G);
+  g_launches += 2;
+  *status = cudaGetLastError();
+  return true;
 }
 }  // namespace
 

@@ -138,6 +138,24 @@ def test_gram_many_rows(ax, rows, k):
     np.testing.assert_array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("rows,k", [(5003, 128), (3001, 300), (2100, 512), (1500, 96)])
+def test_gram_wide_ranks(ax, rows, k):
+    """k >= 96 (a multiple of 4) on >= 1024 rows: X^T X on the TMA-fed FP32
+    product kernel, the whole square in Kahan-compensated slabs of 128 rows
+    over K splits whose partials are added in FP64.  Error at most (128 + 4)
+    u |X|^T |X| (slab sums, Kahan's fold, the splits); the square comes out
+    exactly symmetric (entries (i, j) and (j, i) take the same FMAs in the
+    same order)."""
+    rng = np.random.default_rng(rows + k)
+    X = rng.random((rows, k)).astype(np.float32).astype(np.float64)
+    G = host(ax.gram_w(dev(X)))
+    ref = orc.gram_w(X)
+    tol = (128 + 4) * U32 * (np.abs(X).T @ np.abs(X))
+    err = np.abs(G - ref)
+    assert (err <= tol).all(), f"max err/tol {np.max(err / tol):.3g}"
+    np.testing.assert_array_equal(G, G.T)
+
+
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_mu_updates(ax, m, n, k):
     A, W, H = problem(m, n, k, seed=m + 2)
