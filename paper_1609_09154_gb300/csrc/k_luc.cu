@@ -124,6 +124,83 @@ __global__ void __launch_bounds__(kLucThreads)
   }
 }
 
+// The same sweep for wide ranks (k > 108 with k % 4 == 0, the Gram read
+// through L1): lane l holds the entries j = 128 t + 4 l + u (t < KT4, u < 4)
+// of R rows, so a coordinate's row of G arrives as KT4 16-byte loads shared
+// by the R rows, instead of 32 KT4 / 8 scalar loads per row (the scalar form
+// spent ~95 instructions per row and coordinate at k = 512, most of them
+// load issue and 64-bit address arithmetic, at 41 % issue).
+template <int KT4, int R>
+__global__ void __launch_bounds__(kLucThreads)
+    k_hals4(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
+            int64_t rows, int k, int unit) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
+  const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
+  const int k4 = k >> 2;
+  const float4 *G4 = reinterpret_cast<const float4 *>(G);
+  for (int64_t rb = w0 * R; rb < rows; rb += wstride * R) {
+    float4 x[R][KT4], p[R][KT4];
+#pragma unroll
+    for (int rho = 0; rho < R; ++rho) {
+      const int64_t r = rb + rho;
+#pragma unroll
+      for (int t = 0; t < KT4; ++t) {
+        const int j4 = 32 * t + lane;  // float4 group of entries 4 j4 .. 4 j4 + 3
+        const bool in = r < rows && j4 < k4;
+        x[rho][t] = in ? reinterpret_cast<const float4 *>(X + r * k)[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        p[rho][t] = in ? reinterpret_cast<const float4 *>(P + r * k)[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KT4; ++t) {
+      for (int l = 0; l < 32; ++l) {
+        const int i0 = 128 * t + 4 * l;
+        if (i0 >= k) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u;
+          const float4 *Gi = G4 + (size_t)i * k4;  // G is symmetric: row i = column i
+          float4 g[KT4];
+#pragma unroll
+          for (int tt = 0; tt < KT4; ++tt) {
+            const int j4 = 32 * tt + lane;
+            g[tt] = j4 < k4 ? Gi[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          const float gii = G[(size_t)i * k + i];
+#pragma unroll
+          for (int rho = 0; rho < R; ++rho) {
+            float part = 0.f;
+#pragma unroll
+            for (int tt = 0; tt < KT4; ++tt) {
+              part = fmaf(x[rho][tt].x, g[tt].x, part);
+              part = fmaf(x[rho][tt].y, g[tt].y, part);
+              part = fmaf(x[rho][tt].z, g[tt].z, part);
+              part = fmaf(x[rho][tt].w, g[tt].w, part);
+            }
+            const float dot = warp_sum(part);
+            if (lane == l && (unit || gii > 0.f)) {
+              float *xe = &x[rho][t].x + u;
+              const float pe = (&p[rho][t].x)[u];
+              const float v = *xe + (unit ? pe - dot : (pe - dot) / gii);
+              *xe = v > 0.f ? v : 0.f;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int rho = 0; rho < R; ++rho) {
+      const int64_t r = rb + rho;
+#pragma unroll
+      for (int t = 0; t < KT4; ++t) {
+        const int j4 = 32 * t + lane;
+        if (r < rows && j4 < k4) reinterpret_cast<float4 *>(X + r * k)[j4] = x[rho][t];
+      }
+    }
+  }
+}
+
 // Gradient rows of 0.5 ||A - W H||_F^2: out = g (X G - P) for X rows x k,
 // G k x k, P rows x k (X = W, G = H H^T, P = A H^T gives dL/dW; X = H^T,
 // G = W^T W, P = (W^T A)^T gives (dL/dH)^T).  g is read from device memory
@@ -193,17 +270,19 @@ __global__ void k_hals_scale_rows(float *__restrict__ X, int64_t rows, int k,
   }
 }
 
-__global__ void k_hals_scale_gram(float *__restrict__ GW, int k) {
-  // one block: read the diagonal first, then rescale
+__global__ void __launch_bounds__(512) k_hals_scale_gram(float *__restrict__ GW, int k) {
+  // one block: read the diagonal first, then rescale row by row (no index
+  // division per entry: with one it took 0.58 ms at k = 512)
   __shared__ float sd[AUNMF_K_MAX];
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const float g = GW[i * k + i];
     sd[i] = g > 0.f ? sqrtf(g) : 1.f;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e / k, j = e % k;
-    GW[e] = GW[e] / (sd[i] * sd[j]);
+  for (int i = 0; i < k; ++i) {
+    const float si = sd[i];
+    float *row = GW + (size_t)i * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) row[j] = row[j] / (si * sd[j]);
   }
 }
 
@@ -655,6 +734,23 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
   const bool sm = k <= kSmemGramMaxK;
   const size_t smem = sm ? sizeof(float) * k * k : 0;
   const int u = unit ? 1 : 0;
+  if (!sm && (k & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(P) |
+                               reinterpret_cast<uintptr_t>(G)) & 15) == 0) {
+    // two rows per warp while the registers allow 2+ blocks per SM; one row
+    // above k = 256 (two rows at k = 512 took 136 registers, one block per
+    // SM, and ran the update at 20.3 against 13.6 ms of the scalar form)
+    const int kt4 = (k + 127) / 128, R = kt4 <= 2 ? 2 : 1;
+    int64_t nbw = (rows + kLucWarps * R - 1) / (kLucWarps * R);
+    if (nbw > 152 * 8) nbw = 152 * 8;
+    switch (kt4) {
+      case 1: k_hals4<1, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 2: k_hals4<2, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 3: k_hals4<3, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      default: k_hals4<4, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+    }
+    g_launches += 1;
+    return cudaGetLastError();
+  }
 #define AUNMF_CALL_HALS(KT)                                                       \
   if (sm) k_hals<KT, true><<<nb, kLucThreads, smem, s>>>(X, P, G, rows, k, u);    \
   else k_hals<KT, false><<<nb, kLucThreads, 0, s>>>(X, P, G, rows, k, u);
@@ -693,7 +789,7 @@ cudaError_t launch_hals_normalise(float *X, int64_t rows_x, float *Y, int64_t ro
   };
   if (rows_x > 0) scale(X, rows_x, true);
   if (Y && rows_y > 0) scale(Y, rows_y, false);
-  k_hals_scale_gram<<<1, 256, 0, s>>>(GW, k);
+  k_hals_scale_gram<<<1, 512, 0, s>>>(GW, k);
   g_launches += 1 + (rows_x > 0) + (Y && rows_y > 0);
   return cudaGetLastError();
 }

@@ -1251,16 +1251,32 @@ __global__ void k_dot_partial(const float *__restrict__ P, const float *__restri
 // with the fit residual.  Without d, the mean of the rounding errors (not
 // zero on real value distributions: -8e-6 relative for BF16 on uniform
 // low-rank data) would bias the reported residual by ~1e-3 at relres ~1e-2.
-__global__ void k_relres_final(const double *__restrict__ partials, int nparts,
+// <GW, GH> in FP64 by one block: four interleaved chains per thread keep
+// loads in flight (a single chain waited on L2 for every element: 0.58 ms at
+// k = 512), combined in a fixed order.
+__device__ double gram_dot_block(const float *__restrict__ GW, const float *__restrict__ GH,
+                                 int kk) {
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+  const int step = blockDim.x;
+  int e = threadIdx.x;
+  for (; e + 3 * step < kk; e += 4 * step) {
+    q0 = fma((double)GW[e], (double)GH[e], q0);
+    q1 = fma((double)GW[e + step], (double)GH[e + step], q1);
+    q2 = fma((double)GW[e + 2 * step], (double)GH[e + 2 * step], q2);
+    q3 = fma((double)GW[e + 3 * step], (double)GH[e + 3 * step], q3);
+  }
+  for (; e < kk; e += step) q0 = fma((double)GW[e], (double)GH[e], q0);
+  return block_sum_d((q0 + q1) + (q2 + q3));
+}
+
+__global__ void __launch_bounds__(1024) k_relres_final(const double *__restrict__ partials, int nparts,
                                const float *__restrict__ GW, const float *__restrict__ GH, int k,
                                const double *__restrict__ n2a, double *__restrict__ relres,
                                DevCounters *ctr, double *last) {
   double cross = 0.0;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) cross += partials[b];
   cross = block_sum_d(cross);
-  double quad = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
-  quad = block_sum_d(quad);
+  const double quad = gram_dot_block(GW, GH, k * k);
   if (threadIdx.x == 0) {
     const double a2 = n2a[0];
     double r2 = (a2 + n2a[1]) - 2.0 * cross + quad;
@@ -1274,15 +1290,13 @@ __global__ void k_relres_final(const double *__restrict__ partials, int nparts,
 }
 // loss = 0.5 (||A||^2 + d - 2 <P, Ht> + <GW, GH>), FP64 (not clamped); d as
 // for the residual.
-__global__ void k_loss_final(const double *__restrict__ partials, int nparts,
+__global__ void __launch_bounds__(1024) k_loss_final(const double *__restrict__ partials, int nparts,
                              const float *__restrict__ GW, const float *__restrict__ GH, int k,
                              const double *__restrict__ n2a, double *__restrict__ loss) {
   double cross = 0.0;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) cross += partials[b];
   cross = block_sum_d(cross);
-  double quad = 0.0;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) quad = fma((double)GW[e], (double)GH[e], quad);
-  quad = block_sum_d(quad);
+  const double quad = gram_dot_block(GW, GH, k * k);
   if (threadIdx.x == 0) *loss = 0.5 * ((n2a[0] + n2a[1]) - 2.0 * cross + quad);
 }
 }  // namespace
@@ -1291,7 +1305,7 @@ cudaError_t launch_loss(const float *P, const float *Ht, int64_t len, const floa
                         const float *GH, int k, const double *n2a, double *partials, int nparts,
                         double *loss, cudaStream_t s) {
   k_dot_partial<<<nparts, 256, 0, s>>>(P, Ht, len, partials);
-  k_loss_final<<<1, 256, 0, s>>>(partials, nparts, GW, GH, k, n2a, loss);
+  k_loss_final<<<1, 1024, 0, s>>>(partials, nparts, GW, GH, k, n2a, loss);
   g_launches += 2;
   return cudaGetLastError();
 }
@@ -1317,7 +1331,7 @@ cudaError_t launch_relres(const float *P, const float *Ht, int64_t len, const fl
                           int nparts, double *relres_dev, DevCounters *ctr, double *last,
                           cudaStream_t s) {
   k_dot_partial<<<nparts, 256, 0, s>>>(P, Ht, len, partials);
-  k_relres_final<<<1, 256, 0, s>>>(partials, nparts, GW, GH, k, n2a, relres_dev, ctr, last);
+  k_relres_final<<<1, 1024, 0, s>>>(partials, nparts, GW, GH, k, n2a, relres_dev, ctr, last);
   g_launches += 2;
   return cudaGetLastError();
 }
