@@ -66,11 +66,12 @@ def test_printed_run_matches_oracle(ax, small, prec):
 
 
 @pytest.mark.parametrize("m,n,k", [(2000, 1500, 10), (3000, 700, 150), (40000, 3000, 16),
-                                   (257, 300, 64)])
+                                   (257, 300, 64), (1500, 900, 200)])
 def test_printed_sweep_one_iteration_elementwise(ax, m, n, k):
     """One iteration (printed W sweep, then the printed H rows), factors entry
     by entry: k = 150 reads G from global memory in the sweep and takes the
-    warp-per-row H step; m = 40000 spreads the sweep over many blocks, each
+    warp-per-row H step; k = 200 (a multiple of 4) takes the H step with
+    16-byte Gram row loads; m = 40000 spreads the sweep over many blocks, each
     column's norm crossing the grid barrier."""
     A, W0, H0 = problem(m, n, k, min(k, 12), seed=m + k)
     W, H, _, _ = ax.run(dev(A), k, "hals", 1, dev(W0), dev(H0), hals_variant=1)
