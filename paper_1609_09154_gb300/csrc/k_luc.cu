@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(kLucThreads)
 // by the R rows, instead of 32 KT4 / 8 scalar loads per row (the scalar form
 // spent ~95 instructions per row and coordinate at k = 512, most of them
 // load issue and 64-bit address arithmetic, at 41 % issue).
-template <int KT4, int R>
-__global__ void __launch_bounds__(kLucThreads)
+template <int KT4, int R, int MINB>
+__global__ void __launch_bounds__(kLucThreads, MINB)
     k_hals4(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
             int64_t rows, int k, int unit) {
   const int lane = threadIdx.x & 31;
@@ -738,17 +738,19 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
   const int u = unit ? 1 : 0;
   if (!sm && (k & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(P) |
                                reinterpret_cast<uintptr_t>(G)) & 15) == 0) {
-    // two rows per warp while the registers allow 2+ blocks per SM; one row
-    // above k = 256 (two rows at k = 512 took 136 registers, one block per
-    // SM, and ran the update at 20.3 against 13.6 ms of the scalar form)
-    const int kt4 = (k + 127) / 128, R = kt4 <= 2 ? 2 : 1;
+    // rows per warp and the register cap, measured (update phase per
+    // iteration at 96000 x 64000): k <= 256 two rows; 257..384 one row (two
+    // rows: 7.27 against 6.34 ms at k = 384); above, two rows capped at 128
+    // registers for two blocks per SM (10.3 ms at k = 512; one row 12.4 ms;
+    // two rows uncapped took 136 registers, one block per SM: 20.3 ms)
+    const int kt4 = (k + 127) / 128, R = kt4 == 3 ? 1 : 2;
     int64_t nbw = (rows + kLucWarps * R - 1) / (kLucWarps * R);
     if (nbw > 152 * 8) nbw = 152 * 8;
     switch (kt4) {
-      case 1: k_hals4<1, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      case 2: k_hals4<2, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      case 3: k_hals4<3, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      default: k_hals4<4, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 1: k_hals4<1, 2, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 2: k_hals4<2, 2, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 3: k_hals4<3, 1, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      default: k_hals4<4, 2, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
     }
     g_launches += 1;
     return cudaGetLastError();
