@@ -420,6 +420,7 @@ def run_batched(args):
                                  "latency-bound), so this fraction is the products' share of the step"},
             "relres_median_last": float(np.median(rel[:, -1])), "bpp_pivots": info["bpp_pivots"],
             "tuned_bpp_tile": [info["tuned_bpp_warps"], info["tuned_bpp_rows"]],
+            "tuned_gemm_stages": [info["tuned_gemm_stages_aht"], info["tuned_gemm_stages_wta"]],
             "gpu_launches": int(info["launches"]), "clocks": clk,
         }
         print(json.dumps(line))

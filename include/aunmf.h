@@ -114,6 +114,8 @@ typedef struct {
                             /*   (cold-start, full-size Cholesky) fallback                  */
   double pgrad_first;       /* stop_tol > 0: projected-gradient norm of (W0, H0) ...        */
   double pgrad_last;        /*   ... and of the state the last iteration started from       */
+  int tuned_gemm_stages_aht; /* aunmf_run_batched: autotuned pipeline stages of the grouped */
+  int tuned_gemm_stages_wta; /*   A H^T and W^T A products (0: as many as fit)              */
 } aunmf_info;
 
 /* ---- handle -------------------------------------------------------------- */
@@ -182,8 +184,10 @@ int aunmf_run_host(aunmf_handle *h, const float *A, int64_t m, int64_t n, int64_
  * Every phase of an iteration -- both tensor-core products, the Gram
  * matrices, G^{-1}, the BPP solves, the residual -- is one launch covering
  * all problems; one iteration is captured as a CUDA graph (use_graph) and
- * replayed.  The BPP work tile is autotuned on the first call for a batch
- * signature (count, sum m, sum n, max k, precision) and cached in the handle.
+ * replayed.  The BPP work tile and the grouped products' pipeline depth are
+ * autotuned on the first call for a batch signature (count, sum m, sum n,
+ * max k, precision), each candidate timed on the device, and cached in the
+ * handle; info reports the choices.
  * Requires algo == AUNMF_ABPP and opt->prec TF32 or BF16.
  * relres [host] count x iters, row p = problem p (may be NULL).  Synchronises. */
 int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const int *k, int algo,

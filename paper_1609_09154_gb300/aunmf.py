@@ -66,6 +66,7 @@ class Info(ctypes.Structure):
         ("tuned_bpp_warps", ctypes.c_int), ("tuned_bpp_rows", ctypes.c_int),
         ("bpp_redone", ctypes.c_int64),
         ("pgrad_first", ctypes.c_double), ("pgrad_last", ctypes.c_double),
+        ("tuned_gemm_stages_aht", ctypes.c_int), ("tuned_gemm_stages_wta", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -65,6 +65,9 @@ struct aunmf_handle {
   Buf batch, batch_meta;               // batched runs: arena, descriptors
   // autotuned BPP work tile per batch signature: (warps per block, rows per warp)
   std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> bpp_tuned;
+  // autotuned pipeline stages of the grouped products per batch signature:
+  // (A H^T, W^T A)
+  std::map<std::tuple<int, int64_t, int64_t, int, int>, std::pair<int, int>> gemm_tuned;
   Buf hA, hW, hH;  // device copies for aunmf_run_host
   Buf aux;         // printed HALS sweep / projected gradient: partials, barrier, values
   Buf spl, splpart;  // sparse: long-row lists of the CSR and the CSC; their chunk partials
@@ -1382,6 +1385,9 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
   auto tune_it = h->bpp_tuned.find(sig);
   std::pair<int, int> tile = tune_it != h->bpp_tuned.end() ? tune_it->second
                                                            : std::make_pair(wmax, 4);
+  auto gtune_it = h->gemm_tuned.find(sig);
+  std::pair<int, int> gstages =
+      gtune_it != h->gemm_tuned.end() ? gtune_it->second : std::make_pair(0, 0);
 
   // ---- descriptors to the device: one staging copy
   auto stage_meta = [&](std::vector<uint8_t> &buf) {
@@ -1456,7 +1462,7 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
                                              count, pl.tiles_fh[count], 0, bf, st)) != cudaSuccess)
       return e;
     if ((e = tc::launch_gemm_group(D(pl.o_pa), pl.probs_aht.data(), count, pl.units_aht,
-                                   pl.bn_aht, bf, err, st)) != cudaSuccess)
+                                   pl.bn_aht, bf, err, st, gstages.first)) != cudaSuccess)
       return e;
     return batched::launch_bpp(I, rw, nrw, count, 0, pl.kmax, max_piv, bpp_cold, ctr, tile.first,
                                st);
@@ -1470,7 +1476,7 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
                                              count, pl.tiles_fw[count], 1, bf, st)) != cudaSuccess)
       return e;
     if ((e = tc::launch_gemm_group(D(pl.o_pw), pl.probs_wta.data(), count, pl.units_wta,
-                                   pl.bn_wta, bf, err, st)) != cudaSuccess)
+                                   pl.bn_wta, bf, err, st, gstages.second)) != cudaSuccess)
       return e;
     if ((e = batched::launch_bpp(I, rh, nrh, count, 1, pl.kmax, max_piv, bpp_cold, ctr, tile.first,
                                  st)) !=
@@ -1483,6 +1489,51 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
                                   (int)pl.dot.size(), count, ctr, iters, st);
   };
 
+  // timing events of the autotuners (freed with the call's resources)
+  auto tune_events = [&]() -> int {
+    if (R.ev.size() >= 2) return AUNMF_OK;
+    R.ev.assign(2, nullptr);
+    CK(h, cudaEventCreate(&R.ev[0]));
+    CK(h, cudaEventCreate(&R.ev[1]));
+    return AUNMF_OK;
+  };
+
+  // ---- autotune the grouped products' pipeline depth: every stage count
+  // from 2 to as many as fit, each product timed twice (their inputs are the
+  // split copies of H^T and of W = 0; only P is written, and every iteration
+  // forms it again)
+  if (gtune_it == h->gemm_tuned.end() && iters > 0) {
+    int rc = tune_events();
+    if (rc != AUNMF_OK) return rc;
+    cudaEvent_t a0 = R.ev[0], a1 = R.ev[1];
+    CK(h, batched::launch_split_transpose(inst_d(), reinterpret_cast<const int64_t *>(D(pl.o_tfh)),
+                                          count, pl.tiles_fh[count], 0, bf, s));
+    CK(h, batched::launch_split_transpose(inst_d(), reinterpret_cast<const int64_t *>(D(pl.o_tfw)),
+                                          count, pl.tiles_fw[count], 1, bf, s));
+    auto tune = [&](const void *dp, DescBytes &probs, int64_t units, int bn,
+                    int *chosen) -> int {
+      const int smax = tc::group_max_stages(probs.data(), count, units, bn);
+      float best = 1e30f;
+      *chosen = 0;
+      for (int st = 2; st <= smax; ++st) {
+        CK(h, cudaEventRecord(a0, s));
+        for (int rep = 0; rep < 2; ++rep)
+          CK(h, tc::launch_gemm_group(dp, probs.data(), count, units, bn, bf, err, s, st));
+        CK(h, cudaEventRecord(a1, s));
+        CK(h, cudaEventSynchronize(a1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a0, a1);
+        if (ms < best) { best = ms; *chosen = st; }
+      }
+      return AUNMF_OK;
+    };
+    rc = tune(D(pl.o_pa), pl.probs_aht, pl.units_aht, pl.bn_aht, &gstages.first);
+    if (rc != AUNMF_OK) return rc;
+    rc = tune(D(pl.o_pw), pl.probs_wta, pl.units_wta, pl.bn_wta, &gstages.second);
+    if (rc != AUNMF_OK) return rc;
+    h->gemm_tuned[sig] = gstages;
+  }
+
   // ---- autotune the BPP work tile on the first W update (factors restored)
   if (tune_it == h->bpp_tuned.end() && iters > 0) {
     std::vector<std::pair<int, int>> cand;
@@ -1492,9 +1543,8 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     if (cand.empty()) cand.push_back({wmax, 4});
     float best = 1e30f;
     std::pair<int, int> best_tile = cand[0];
-    R.ev.assign(2, nullptr);
-    CK(h, cudaEventCreate(&R.ev[0]));
-    CK(h, cudaEventCreate(&R.ev[1]));
+    int rc = tune_events();
+    if (rc != AUNMF_OK) return rc;
     cudaEvent_t a0 = R.ev[0], a1 = R.ev[1];
     for (const auto &c : cand) {
       tile = c;
@@ -1566,6 +1616,8 @@ int aunmf_run_batched(aunmf_handle *h, int count, const aunmf_matrix *A, const i
     info->launches = g_launches - launches0 + graph_launches;
     info->tuned_bpp_warps = tile.first;
     info->tuned_bpp_rows = tile.second;
+    info->tuned_gemm_stages_aht = gstages.first;
+    info->tuned_gemm_stages_wta = gstages.second;
   }
   if (herr) return AUNMF_E_TIMEOUT;
   if (hc.bpp_numeric) return AUNMF_E_NUMERIC;

@@ -1085,8 +1085,9 @@ bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int
   return true;
 }
 
-cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
-                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s) {
+namespace {
+bool group_shape(GemmLaunch *L, const void *host_first, int nprob, int64_t units, int BNmax,
+                 int *err) {
   const GemmProblem *hp = reinterpret_cast<const GemmProblem *>(host_first);
   int accw = 0;
   bool pairs = true;
@@ -1095,8 +1096,21 @@ cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, 
     accw = w > accw ? w : accw;
     pairs = pairs && all_pair(hp[i]);
   }
+  return launch_shape(L, BNmax, accw, pairs, units, nprob, err);
+}
+}  // namespace
+
+int group_max_stages(const void *host_first, int nprob, int64_t units, int BNmax) {
   GemmLaunch L;
-  if (!launch_shape(&L, BNmax, accw, pairs, units, nprob, err)) return cudaErrorInvalidValue;
+  return group_shape(&L, host_first, nprob, units, BNmax, nullptr) ? L.nstages : 0;
+}
+
+cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
+                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s,
+                              int nstages) {
+  GemmLaunch L;
+  if (!group_shape(&L, host_first, nprob, units, BNmax, err)) return cudaErrorInvalidValue;
+  if (nstages >= 2 && nstages < L.nstages) L.nstages = nstages;
   const GemmProblem &h0 = *reinterpret_cast<const GemmProblem *>(host_first);
   return launch_kernel(h0, h0, reinterpret_cast<const GemmProblem *>(dev_problems), L, bf16, s);
 }

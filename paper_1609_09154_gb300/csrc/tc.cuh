@@ -58,8 +58,13 @@ size_t problem_bytes();
 bool fill_group_problem(void *host_dst, const void *X, int64_t M, int64_t K, int64_t ldx,
                         const void *Y, int k, int64_t ldy, bool split, bool bf16, float *C,
                         int64_t unit0, int64_t *units, int *BN);
+// nstages: pipeline stages of the shared-memory ring (>= 2; 0 or above the
+// most that fit: as many as fit, the default).  group_max_stages: that most
+// (0 if the group cannot launch).
 cudaError_t launch_gemm_group(const void *dev_problems, const void *host_first, int nprob,
-                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s);
+                              int64_t units, int BNmax, bool bf16, int *err, cudaStream_t s,
+                              int nstages = 0);
+int group_max_stages(const void *host_first, int nprob, int64_t units, int BNmax);
 // P = sum over s of parts[s] (len elements each), s ascending.
 cudaError_t launch_sum_splits(const float *parts, int S, int64_t len, float *P, cudaStream_t s);
 

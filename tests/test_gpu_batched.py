@@ -89,6 +89,8 @@ def test_batched_matches_single_and_oracle(ax, prec):
     Ws, Hs, rel, info = ax.run_batched(As, ks, iters, H0s, prec=prec)
     assert info["bpp_nonconverged"] == 0 and info["bpp_numeric"] == 0
     assert info["tuned_bpp_warps"] > 0 and info["tuned_bpp_rows"] > 0
+    # the grouped products' pipeline depth, autotuned on the first call
+    assert info["tuned_gemm_stages_aht"] >= 2 and info["tuned_gemm_stages_wta"] >= 2
     host = lambda t: t.cpu().numpy().astype(np.float64)  # noqa: E731
     for p, (A, H0, k) in enumerate(probs):
         W1, H1, r1, _ = ax.run(As[p], k, "abpp", iters, dev(np.zeros((A.shape[0], k))), H0s[p],
