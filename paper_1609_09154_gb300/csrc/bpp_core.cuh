@@ -712,14 +712,14 @@ __device__ __forceinline__ int bpp_row_fast(const BppWarp &w, const float *__res
     }
     need_solve = true;
   }
-  // a row handed to the fallback keeps its previous iterate, whose support
-  // the fallback starts from
-  if (!failed_numeric) {
+  // a row handed to the fallback gets the passive set it had reached (1 on
+  // it, 0 elsewhere), which the fallback starts from: in the first
+  // iteration, whose previous iterate is the random start, that saves the
+  // fallback most of its exchanges (the fallback always overwrites the row)
 #pragma unroll
-    for (int t = 0; t < KT; ++t) {
-      const int j = lane + 32 * t;
-      if (j < k) X[row * k + j] = __fadd_rn(xh[t], xl[t]);
-    }
+  for (int t = 0; t < KT; ++t) {
+    const int j = lane + 32 * t;
+    if (j < k) X[row * k + j] = failed_numeric ? (pas[t] ? 1.f : 0.f) : __fadd_rn(xh[t], xl[t]);
   }
   *failed_numeric_out = failed_numeric;
   *failed_cap_out = failed_cap;
