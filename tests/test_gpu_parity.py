@@ -96,6 +96,21 @@ def test_products_fp32_long_contraction(ax, m, n, k):
     assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
 
 
+@pytest.mark.parametrize("m,n,k", [(40, 1000, 33), (1000, 40, 33), (513, 260, 64), (256, 256, 65),
+                                   (2048, 4, 40)])
+def test_products_fp32_tma_edges(ax, m, n, k):
+    """The TMA-fed FP32 form (k > 32, rows 16-byte aligned) at its edges: an
+    output tile mostly past M (40 rows of 256), a contraction shorter than
+    one 16-deep step or one 128-long slab (K = 40, K = 4), exactly one tile
+    (256 x 256), N = 33 (one column past 32) and 65 (a second column tile of
+    one column), and M = 513 (one row into a third tile)."""
+    A, W, H = problem(m, n, k, seed=m * 7 + n + k)
+    PW = host(ax.aht(dev(A), dev(H)))
+    PH = host(ax.wta(dev(A), dev(W)))
+    assert_product(PW, orc.aht(A, H), np.abs(A) @ np.abs(H).T, n)
+    assert_product(PH, orc.wta(A, W), np.abs(W).T @ np.abs(A), m)
+
+
 @pytest.mark.parametrize("k", [24, 50])
 def test_products_fp32_padded_rows(ax, k):
     """A in a buffer with padded rows (lda = 204 > n = 201), with K tails (201
