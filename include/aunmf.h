@@ -322,10 +322,12 @@ int aunmf_check_status(int *site);
  *            AUNMF_INJECT_NOMEM         every workspace allocation fails with
  *              AUNMF_E_NOMEM (cudaMalloc is not called); buffers a handle
  *              already holds stay usable
- *            AUNMF_INJECT_SIMT_WAIT     FP32 dense products with k > 32
- *              (aunmf_run, aunmf_relres, aunmf_aht / aunmf_wta in FP32): the
- *              producer warp never signals that the first stage of A is in
- *              shared memory, so the consumer warps' wait runs out
+ *            AUNMF_INJECT_SIMT_WAIT     the TMA-fed FP32 kernel: dense FP32
+ *              products with k > 32 (aunmf_run, aunmf_relres, aunmf_aht /
+ *              aunmf_wta in FP32) and the Gram matrices at k >= 96 (a
+ *              multiple of 4, >= 1024 rows) in every precision: thread 0
+ *              never arrives on the first stage's barrier, so every thread's
+ *              wait for that stage runs out
  *   wait_ms  limit of the bounded waits while `site` is set, in milliseconds
  *            of the device's maximum SM clock (<= 0: the default ~2 s);
  *            ignored for AUNMF_INJECT_NONE, which restores the default.
