@@ -130,10 +130,10 @@ __global__ void __launch_bounds__(kLucThreads)
 // by the R rows, instead of 32 KT4 / 8 scalar loads per row (the scalar form
 // spent ~95 instructions per row and coordinate at k = 512, most of them
 // load issue and 64-bit address arithmetic, at 41 % issue).
-template <int KT4, int R, int MINB>
-__global__ void __launch_bounds__(kLucThreads, MINB)
-    k_hals4(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
-            int64_t rows, int k, int unit) {
+template <int KT4, int R>
+__device__ __forceinline__ void hals4_rows(float *__restrict__ X, const float *__restrict__ P,
+                                           const float *__restrict__ G, int64_t rows, int k,
+                                           int unit) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (int64_t)blockIdx.x * kLucWarps + (threadIdx.x >> 5);
   const int64_t wstride = (int64_t)gridDim.x * kLucWarps;
@@ -199,6 +199,22 @@ __global__ void __launch_bounds__(kLucThreads, MINB)
       }
     }
   }
+}
+
+// The sweep with the compiler's own register choice, and with registers
+// capped at 128 for two blocks per SM (a launch bound with a minimum of one
+// block already changes the choice: 79 against 62 registers at KT4 = 3).
+template <int KT4, int R>
+__global__ void __launch_bounds__(kLucThreads)
+    k_hals4(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
+            int64_t rows, int k, int unit) {
+  hals4_rows<KT4, R>(X, P, G, rows, k, unit);
+}
+template <int KT4, int R>
+__global__ void __launch_bounds__(kLucThreads, 2)
+    k_hals4_capped(float *__restrict__ X, const float *__restrict__ P, const float *__restrict__ G,
+                   int64_t rows, int k, int unit) {
+  hals4_rows<KT4, R>(X, P, G, rows, k, unit);
 }
 
 // Gradient rows of 0.5 ||A - W H||_F^2: out = g (X G - P) for X rows x k,
@@ -761,10 +777,10 @@ cudaError_t launch_hals(float *X, const float *P, const float *G, int64_t rows, 
     int64_t nbw = (rows + kLucWarps * R - 1) / (kLucWarps * R);
     if (nbw > 152 * 8) nbw = 152 * 8;
     switch (kt4) {
-      case 1: k_hals4<1, 2, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      case 2: k_hals4<2, 2, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      case 3: k_hals4<3, 1, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
-      default: k_hals4<4, 2, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 1: k_hals4<1, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 2: k_hals4<2, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      case 3: k_hals4<3, 1><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
+      default: k_hals4_capped<4, 2><<<(unsigned)nbw, kLucThreads, 0, s>>>(X, P, G, rows, k, u); break;
     }
     g_launches += 1;
     return cudaGetLastError();
