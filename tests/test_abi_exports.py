@@ -124,3 +124,19 @@ def test_normal_build_compiles_no_bounds_checks(libpath):
     assert L.aunmf_check_status(ctypes.byref(site)) == 0
     assert site.value == -1
     assert L.aunmf_check_status(None) == -1
+
+
+def test_checked_build_compiles_and_exports_the_boundary():
+    """The bounds-checked variant (-DAUNMF_CHECK) builds for sm_103a and
+    exports the same symbols, aunmf_check_status included (nothing called)."""
+    from paper_1609_09154_gb300 import build
+
+    if shutil_which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    path = build.build(check=True)
+    assert path.endswith("libaunmf_check.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(aunmf_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, f"declared but not exported: {missing}"
